@@ -163,7 +163,7 @@ def clock_factor(q: int, beta: float):
     if q % 2 == 0:
         cols.append(np.cos(math.pi * np.arange(q)) / math.sqrt(q))
     F = np.stack(cols, axis=1)
-    lam = np.einsum("ki,kl,lj->ij", F, B, F).diagonal().copy()
+    lam = np.einsum("ki,kl,lj->ij", F, B, F, optimize=True).diagonal().copy()
     if np.any(lam < -1e-12 * np.abs(lam).max()):
         raise ValueError("clock bond matrix not positive semidefinite")
     W = F * np.sqrt(np.clip(lam, 0.0, None))[None, :]
@@ -387,7 +387,7 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None):
 
     # (d) triads, eqs. E-L
     E = np.einsum("tbcda,bck->tkda", A, U["A"])
-    F = np.einsum("abcdg,bck,g->akdg", X, U["X"], sig)
+    F = np.einsum("abcdg,bck,g->akdg", X, U["X"], sig, optimize=True)
     G = np.einsum("bPQRg,PQk->bkRg", Y, U["Y"])
     H = np.einsum("wPQRb,PQk->wkRb", Dm, U["D"])
     I_, J_, K_, L_ = U["A"], U["X"], U["Y"], U["D"]
@@ -397,23 +397,23 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None):
     Jg = np.einsum("bck,bcl->kl", J_, J_)
     Kg = np.einsum("bck,bcl->kl", K_, K_)
     Lg = np.einsum("bck,bcl->kl", L_, L_)
-    EEI = np.einsum("tkda,tlde,kl->ae", E, E, Ig)
-    O = np.einsum("ae,akdg,eldh,kl->gh", EEI, F, F, Jg)
-    HHL = np.einsum("wkdb,wlde,kl->be", H, H, Lg)
-    Pm = np.einsum("be,bkdg,eldh,kl->gh", HHL, G, G, Kg)
+    EEI = np.einsum("tkda,tlde,kl->ae", E, E, Ig, optimize=True)
+    O = np.einsum("ae,akdg,eldh,kl->gh", EEI, F, F, Jg, optimize=True)
+    HHL = np.einsum("wkdb,wlde,kl->be", H, H, Lg, optimize=True)
+    Pm = np.einsum("be,bkdg,eldh,kl->gh", HHL, G, G, Kg, optimize=True)
 
     # environments of each pair (forward: upper block with P on gamma; backward: lower
     # block with O on gamma), then the squeezers
-    EE4 = np.einsum("tkda,tlDe,kl->daDe", E, E, Ig)                 # (p4 al, p4' al')
-    FPF4 = np.einsum("akdg,gh,elDh,kl->adeD", F, Pm, F, Jg)         # (al q4, al' q4')
+    EE4 = np.einsum("tkda,tlDe,kl->daDe", E, E, Ig, optimize=True)                 # (p4 al, p4' al')
+    FPF4 = np.einsum("akdg,gh,elDh,kl->adeD", F, Pm, F, Jg, optimize=True)         # (al q4, al' q4')
     rho_f = {4: np.einsum("paPe,aqeQ->pqPQ", EE4, FPF4)}           # (p4 q4, p4' q4')
-    GOG4 = np.einsum("bkPg,gh,elQh,kl->bPeQ", G, O, G, Kg)           # (be P4, be' P4')
-    HH4 = np.einsum("wkdb,wlDe,kl->bdeD", H, H, Lg)                  # (be Q4, be' Q4')
+    GOG4 = np.einsum("bkPg,gh,elQh,kl->bPeQ", G, O, G, Kg, optimize=True)           # (be P4, be' P4')
+    HH4 = np.einsum("wkdb,wlDe,kl->bdeD", H, H, Lg, optimize=True)                  # (be Q4, be' Q4')
     rho_b = {4: np.einsum("bPeR,bQeS->PQRS", GOG4, HH4)}
 
     EE2 = np.einsum("tkda,tlde->kale", E, E)                         # (kA al, kA' al')
-    FPF2 = np.einsum("akdg,gh,eldh->akel", F, Pm, F)                 # (al kX, al' kX')
-    GOG2 = np.einsum("bkdg,gh,eldh->kble", G, O, G)                  # (kY be, kY' be')
+    FPF2 = np.einsum("akdg,gh,eldh->akel", F, Pm, F, optimize=True)                 # (al kX, al' kX')
+    GOG2 = np.einsum("bkdg,gh,eldh->kble", G, O, G, optimize=True)                  # (kY be, kY' be')
     HH2 = np.einsum("wkdb,wlde->kble", H, H)                         # (kD be, kD' be')
     for mu, sub in ((2, "bck,Bcl->bkBl"), (3, "cbk,cBl->bkBl")):
         II = np.einsum(sub, I_, I_)                                   # (p kA, p' kA')
@@ -467,7 +467,7 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None):
 
 def contract_upper(E, F, I_, J_, Msq):
     """Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG)."""
-    Theta = np.einsum("bck,BCl,bBm,cCn->klmn", I_, J_, Msq[2], Msq[3])  # (kA kX k2 k3)
+    Theta = np.einsum("bck,BCl,bBm,cCn->klmn", I_, J_, Msq[2], Msq[3], optimize=True)  # (kA kX k2 k3)
     EM = np.einsum("tkda,dDm->tkamD", E, Msq[4])                        # (t kA al k4 q4)
     Phi1 = np.tensordot(EM, F, axes=([2, 4], [0, 2]))                   # (t kA k4 kX g)
     Phi = np.tensordot(Phi1, Theta, axes=([1, 3], [0, 1]))              # (t k4 g k2 k3)
@@ -476,7 +476,7 @@ def contract_upper(E, F, I_, J_, Msq):
 
 def contract_lower(G, H, K_, L_, Nsq):
     """Psi[w,k2',k3',k4',g] = sum (G H N4)(K L N2 N3)   (eq. makeMH), pairs (P, Q)."""
-    Theta = np.einsum("bck,BCl,bBm,cCn->klmn", K_, L_, Nsq[2], Nsq[3])  # (kY kD k2 k3)
+    Theta = np.einsum("bck,BCl,bBm,cCn->klmn", K_, L_, Nsq[2], Nsq[3], optimize=True)  # (kY kD k2 k3)
     HN = np.einsum("wkdb,Ddm->wkbmD", H, Nsq[4])                        # (w kD be k4 P4)
     Psi1 = np.tensordot(HN, G, axes=([2, 4], [0, 2]))                   # (w kD k4 kY g)
     Psi = np.tensordot(Psi1, Theta, axes=([3, 1], [0, 1]))              # (w k4 g k2 k3)
@@ -596,3 +596,4 @@ def run(model: str, d: int, beta: float, h: float, D: int, p: int, nsteps: int,
         ax = (n % d) if axes is None else axes[n]
         step(st, ax, D, p, q_swap, q_rho, seed, method)
     return st
+
