@@ -1,0 +1,112 @@
+/*
+ * trg.h — C ABI of libtrg: the triad-ATRG coarse-graining step for 4D lattice spin
+ * models on one NVIDIA B300 (sm_103a).
+ *
+ * Method: Y. Sugimoto, S. Sasaki, "Triad representation for the anisotropic tensor
+ * renormalization group in four dimensions", arXiv:2507.21909.
+ *
+ * Conventions shared by every entry point
+ *   - One library-global context (not thread-safe).  All device memory is allocated and
+ *     owned by the library; callers pass scalars and HOST pointers only.
+ *   - The coarse tensor is held on the device as T = sum_g Phi[i1,i2,i3,i4,g]
+ *     Psi[j1,j2,j3,j4,g] (forward legs x backward legs, rank-factorised), FP64,
+ *     row-major with g fastest, and an optional impurity factor Psi_imp.
+ *   - Return value: TRG_OK (0) or a negative TRG_ERR_* code; trg_last_error() gives a
+ *     one-line message.  No entry point aborts or exits the process.
+ *   - Results written to host pointers are valid when the call returns (the library
+ *     synchronises its own stream before returning host scalars).
+ */
+#ifndef TRG_H
+#define TRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int trg_status;
+
+#define TRG_OK             0
+#define TRG_ERR_ARG       -1   /* bad argument (range, NULL pointer, unsupported d)   */
+#define TRG_ERR_OOM       -2   /* device allocation failed                            */
+#define TRG_ERR_CUDA      -3   /* a CUDA runtime call or kernel launch failed         */
+#define TRG_ERR_NONFINITE -4   /* NaN/Inf in the norm c_n or a spectrum               */
+#define TRG_ERR_TIMEOUT   -5   /* a bounded device-side iteration did not converge    */
+#define TRG_ERR_NOINIT    -6   /* no model initialised                                */
+
+/* Precision of the contractions (trg_set_params): */
+#define TRG_PREC_FP64      0   /* every GEMM in FP64 on CUDA cores (parity form)       */
+#define TRG_PREC_BF16X3    1   /* bulk GEMMs as 3-term BF16-split tcgen05, FP32 accum */
+#define TRG_PREC_BF16X6    2   /* bulk GEMMs as 6-term BF16-split tcgen05, FP32 accum */
+
+/* Initial tensor of the d-dimensional Ising model, Sec. III (CP form
+ * T = sum_a prod_legs W[a, leg], W = [[sqrt(cosh b), sqrt(sinh b)],
+ * [sqrt(cosh b), -sqrt(sinh b)]]) with an added site field e^{h s}.
+ * d: must be 4 (the triad step is four-dimensional).  beta >= 0.  The impurity
+ * factor (one site carrying s) is created as well.  Resets the log-norm sum to
+ * ln c_0, c_0 = ||T_0||_F, and the step counter to 0.  Errors: TRG_ERR_ARG. */
+trg_status trg_init_ising(int d, double beta, double h);
+
+/* Z_q clock model (extension, not in the paper): bond weight e^{beta cos(th-th')},
+ * th = 2 pi k / q, factorised in the real Fourier basis; site weight e^{h cos th};
+ * impurity observable cos th.  d = 4, q in [2, 8], beta >= 0. */
+trg_status trg_init_clock(int d, int q, double beta, double h);
+
+/* One triad-ATRG coarse-graining step along physical axis `axis` (0..3):
+ * re-split T = A s D (eq. ABCD), bond swap by randomized SVD (Appendix A, eqs.
+ * bond1/bond2, XY), triad isometries from the canonical-form Grams (eq. HOSVD), triads
+ * E..L (eqs. E-L), squeezers from the Gram matrices O, P (Sec. II D), coarse
+ * contraction Phi / Psi (eqs. makeMG, makeMH), then T <- T / c_n with
+ * c_n = ||T||_F and lnZ bookkeeping sum += ln(c_n) / 2^n.
+ * D >= 1: bond dimension kept.  sketch_oversample p >= 0: the overspanned internal
+ * lines have width chi = min(D + p, natural dimension) (r = eta = (D+p)/D).
+ * Errors: TRG_ERR_NOINIT, TRG_ERR_ARG, TRG_ERR_OOM, TRG_ERR_CUDA, TRG_ERR_NONFINITE. */
+trg_status trg_step(int axis, int D, int sketch_oversample);
+
+/* Free energy per site of the current 2^N-site periodic lattice (N = steps taken):
+ * lnZ/V = sum_n ln(c_n)/2^n + 2^-N ln Tr T_N (legs mu paired with mu),
+ * f = -(lnZ/V)/beta (Sec. III A).  f is NaN when beta = 0.  Either pointer may be
+ * NULL.  Errors: TRG_ERR_NOINIT, TRG_ERR_CUDA. */
+trg_status trg_free_energy(double *f_per_site, double *lnZ_per_site);
+
+/* One-site impurity expectation <s> (Ising) or <cos th> (clock):
+ * Tr(Phi Psi_imp^T) / Tr(Phi Psi^T).  The impurity is coarse-grained with the pure
+ * tensor's frozen projectors, averaged over its two slots in each step. */
+trg_status trg_magnetisation_impurity(double *m);
+
+/* Parameters of the randomized SVDs and the precision mode (defaults: 4, 4, 0x5EED,
+ * TRG_PREC_FP64).  q_swap >= 1 rounds of the bond-swap loop; q_rho >= 0 extra power
+ * rounds of the triad / squeezer range finders. */
+trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision);
+
+/* Run all device work on this cudaStream_t (NULL = the library's own stream). */
+trg_status trg_set_stream(void *cuda_stream);
+
+/* Diagnostics of the last step: ln c_n, the smallest relative singular-value gap at
+ * the bond-swap and squeezer truncations, and the number of steps taken. */
+trg_status trg_diag(double *log_c, double *min_gap, int *nsteps);
+
+/* Copy a state factor to the host.  which: 0 = Phi, 1 = Psi, 2 = Psi_imp.
+ * dims_out[0..4] receives (d1, d2, d3, d4, r); host may be NULL (query only), else it
+ * must hold `capacity` doubles >= d1 d2 d3 d4 r.  axes_out[0..3] (may be NULL) gets
+ * the physical axis of each leg slot.  Errors: TRG_ERR_NOINIT, TRG_ERR_ARG. */
+trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
+                         long long capacity);
+
+/* Load a state (e.g. an oracle state at step n, for per-step parity):
+ * dims[0..4] = (d1, d2, d3, d4, r), phi/psi[/psi_imp (may be NULL)] row-major host
+ * arrays, axes[0..3] the physical axis of each slot, nsteps taken so far and the
+ * log-norm sum so far.  Errors: TRG_ERR_ARG, TRG_ERR_OOM. */
+trg_status trg_set_state(double beta, const int *dims, const double *phi,
+                         const double *psi, const double *psi_imp, const int *axes,
+                         int nsteps, double logsum);
+
+/* Release every device buffer of the context. */
+trg_status trg_finalize(void);
+
+/* Message of the last error (static storage, never NULL). */
+const char *trg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRG_H */

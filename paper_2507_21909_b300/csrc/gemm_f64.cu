@@ -1,0 +1,86 @@
+// FP64 batched GEMM on CUDA cores (the parity form of every contraction).
+// C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b], row-major; 64x64 tiles, BK = 16,
+// 256 threads with 4x4 register tiles.  Ragged edges are zero-filled on load.
+#include "trg_internal.h"
+
+namespace trg {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256)
+gemm_f64_kernel(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                const double *__restrict__ A, int64_t lda, int64_t sA,
+                const double *__restrict__ B, int64_t ldb, int64_t sB, double beta,
+                double *__restrict__ C, int64_t ldc, int64_t sC, int64_t batch) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  for (int64_t b = blockIdx.z; b < batch; b += gridDim.z) {
+    const double *Ab = A + b * sA;
+    const double *Bb = B + b * sB;
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+      for (int idx = tid; idx < BM * BK; idx += 256) {
+        int mm, kk;
+        if (ta) { mm = idx % BM; kk = idx / BM; } else { kk = idx % BK; mm = idx / BK; }
+        int64_t gm = m0 + mm, gk = k0 + kk;
+        double v = 0.0;
+        if (gm < M && gk < K) v = ta ? Ab[gk * lda + gm] : Ab[gm * lda + gk];
+        As[kk][mm] = v;
+      }
+      for (int idx = tid; idx < BN * BK; idx += 256) {
+        int nn, kk;
+        if (tb) { kk = idx % BK; nn = idx / BK; } else { nn = idx % BN; kk = idx / BN; }
+        int64_t gn = n0 + nn, gk = k0 + kk;
+        double v = 0.0;
+        if (gn < N && gk < K) v = tb ? Bb[gn * ldb + gk] : Bb[gk * ldb + gn];
+        Bs[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+    double *Cb = C + b * sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int64_t gm = m0 + ty + 16 * i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int64_t gn = n0 + tx + 16 * j;
+        if (gn >= N) continue;
+        double *c = Cb + gm * ldc + gn;
+        *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
+      }
+    }
+  }
+}
+
+void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+              const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
+              int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch,
+              cudaStream_t s) {
+  if (M == 0 || N == 0 || batch == 0) return;
+  int64_t gy = (M + BM - 1) / BM, gx = (N + BN - 1) / BN;
+  if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_f64: M too large for one launch");
+  int64_t gz = batch < 65535 ? batch : 65535;
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz);
+  gemm_f64_kernel<<<grid, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta,
+                                       C, ldc, sC, batch);
+  TRG_LAUNCH_CHECK();
+}
+
+}  // namespace trg

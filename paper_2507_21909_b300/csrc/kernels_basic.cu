@@ -1,0 +1,391 @@
+// Elementwise, permutation, reduction and sketch kernels of libtrg (FP64).
+#include "trg_internal.h"
+
+namespace trg {
+
+// ------------------------------------------------------------------ permutation
+constexpr int kMaxDims = 10;
+struct PermArgs {
+  int nd;
+  int64_t out_dims[kMaxDims];
+  int64_t in_stride_of_out[kMaxDims];  // stride in `in` of each output axis
+};
+
+__global__ void permute_kernel(const double *__restrict__ in, double *__restrict__ out,
+                               int64_t total, PermArgs a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = i, off = 0;
+    for (int d = a.nd - 1; d >= 0; --d) {
+      int64_t c = rem % a.out_dims[d];
+      rem /= a.out_dims[d];
+      off += c * a.in_stride_of_out[d];
+    }
+    out[i] = in[off];
+  }
+}
+
+static int grid_for(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 148 * 64) b = 148 * 64;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void permute(const double *in, double *out, const std::vector<int64_t> &dims_in,
+             const std::vector<int> &perm, cudaStream_t s) {
+  int nd = (int)dims_in.size();
+  if (nd > kMaxDims) throw Error(TRG_ERR_ARG, "permute: too many dims");
+  PermArgs a;
+  a.nd = nd;
+  std::vector<int64_t> st(nd, 1);
+  for (int d = nd - 2; d >= 0; --d) st[d] = st[d + 1] * dims_in[d + 1];
+  int64_t total = 1;
+  for (int d = 0; d < nd; ++d) {
+    a.out_dims[d] = dims_in[perm[d]];
+    a.in_stride_of_out[d] = st[perm[d]];
+    total *= dims_in[d];
+  }
+  if (total == 0) return;
+  permute_kernel<<<grid_for(total), 256, 0, s>>>(in, out, total, a);
+  TRG_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------- counter-based sketches
+// SplitMix64 output function (Steele, Lea, Flood 2014) applied to key + n * gamma.
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+uint64_t sketch_key(uint64_t seed, int step, int tag) {
+  return mix64(seed + kGolden * (uint64_t)(64 * (int64_t)step + tag + 1));
+}
+
+__global__ void gaussian_kernel(double *out, int64_t total, uint64_t key) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t n = (uint64_t)i;
+    uint64_t x = mix64(key + kGolden * (2 * n + 1));
+    uint64_t y = mix64(key + kGolden * (2 * n + 2));
+    double u1 = ((double)(x >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+    double u2 = (double)(y >> 11) * 0x1.0p-53;          // [0, 1)
+    out[i] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  }
+}
+
+void fill_gaussian(double *out, int64_t rows, int64_t cols, uint64_t key, cudaStream_t s) {
+  int64_t total = rows * cols;
+  if (total == 0) return;
+  gaussian_kernel<<<grid_for(total), 256, 0, s>>>(out, total, key);
+  TRG_LAUNCH_CHECK();
+}
+
+__global__ void khatri_rao_kernel(const double *g2, const double *g1, double *out,
+                                  int64_t nj, int64_t nb, int64_t w) {
+  int64_t total = nj * nb * w;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = i % w, jb = i / w, b = jb % nb, j = jb / nb;
+    out[i] = g2[j * w + m] * g1[b * w + m];
+  }
+}
+
+void khatri_rao(const double *g2, const double *g1, double *out, int64_t nj, int64_t nb,
+                int64_t w, cudaStream_t s) {
+  int64_t total = nj * nb * w;
+  if (total == 0) return;
+  khatri_rao_kernel<<<grid_for(total), 256, 0, s>>>(g2, g1, out, nj, nb, w);
+  TRG_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ scaling
+__device__ inline double scale_fn(double v, int mode, double vmax, double tol) {
+  switch (mode) {
+    case 0: return v;
+    case 1: return (v > tol * vmax && v > 0.0) ? 1.0 / v : 0.0;
+    case 2: return (v > tol * vmax && v > 0.0) ? 1.0 / sqrt(v) : 0.0;
+    default: return v > 0.0 ? sqrt(v) : 0.0;
+  }
+}
+
+__global__ void scale_axis_kernel(double *x, int64_t total, int64_t inner, int64_t n,
+                                  const double *v, int mode, const double *vmax,
+                                  double tol) {
+  double mx = vmax ? *vmax : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = (i / inner) % n;
+    x[i] *= scale_fn(v[a], mode, mx, tol);
+  }
+}
+
+void scale_axis(double *x, int64_t total, int64_t inner, int64_t n, const double *v,
+                int mode, const double *vmax, double tol, cudaStream_t s) {
+  if (total == 0) return;
+  scale_axis_kernel<<<grid_for(total), 256, 0, s>>>(x, total, inner, n, v, mode, vmax, tol);
+  TRG_LAUNCH_CHECK();
+}
+
+__global__ void kill_dead_kernel(const double *v, int64_t n, double tol, double *m1,
+                                 int64_t rows1, double *m2, int64_t rows2) {
+  double top = v[0];
+  int64_t tot1 = rows1 * n, tot2 = rows2 * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot1 + tot2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < tot1) {
+      int64_t c = i % n;
+      if (!(v[c] > tol * top && v[c] > 0.0)) m1[i] = 0.0;
+    } else {
+      int64_t j = i - tot1, c = j % n;
+      if (!(v[c] > tol * top && v[c] > 0.0)) m2[j] = 0.0;
+    }
+  }
+}
+__global__ void kill_dead_v_kernel(double *v, int64_t n, double tol) {
+  double top = v[0];
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    if (!(v[i] > tol * top && v[i] > 0.0)) v[i] = 0.0;
+}
+
+void kill_dead(double *v, int64_t n, double tol, double *m1, int64_t rows1, double *m2,
+               int64_t rows2, cudaStream_t s) {
+  if (n == 0) return;
+  if (!m1) rows1 = 0;
+  if (!m2) rows2 = 0;
+  if (rows1 * n + rows2 * n > 0) {
+    kill_dead_kernel<<<grid_for(rows1 * n + rows2 * n), 256, 0, s>>>(v, n, tol, m1, rows1, m2,
+                                                                      rows2);
+    TRG_LAUNCH_CHECK();
+  }
+  kill_dead_v_kernel<<<1, 256, 0, s>>>(v, n, tol);
+  TRG_LAUNCH_CHECK();
+}
+
+// --------------------------------------------------------------- reductions
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+constexpr int kDotBlocks = 256;
+__global__ void dot_partial(const double *a, const double *b, int64_t n, double *part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+__global__ void dot_final(const double *part, int np, double *out) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) v += part[i];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    w = warp_sum(w);
+    if (threadIdx.x == 0) *out = w;
+  }
+}
+
+void dot(const double *a, const double *b, int64_t n, double *out, double *scratch,
+         cudaStream_t s) {
+  dot_partial<<<kDotBlocks, 256, 0, s>>>(a, b, n, scratch);
+  TRG_LAUNCH_CHECK();
+  dot_final<<<1, 256, 0, s>>>(scratch, kDotBlocks, out);
+  TRG_LAUNCH_CHECK();
+}
+
+__global__ void col_max_abs_kernel(const double *v, int64_t n, double *out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    w = warp_max(w);
+    if (threadIdx.x == 0) *out = w;
+  }
+}
+void col_max_abs(const double *v, int64_t n, double *out, cudaStream_t s) {
+  col_max_abs_kernel<<<1, 256, 0, s>>>(v, n, out);
+  TRG_LAUNCH_CHECK();
+}
+
+// one block per column: max |a|, then the first row within 1e-6 of it decides the sign
+__global__ void sign_gauge_kernel(double *m1, int64_t rows1, double *m2, int64_t rows2,
+                                  int64_t cols) {
+  __shared__ double shm[32];
+  __shared__ long long shi[32];
+  __shared__ double s_sign;
+  int64_t c = blockIdx.x;
+  double mx = 0.0;
+  for (int64_t r = threadIdx.x; r < rows1; r += blockDim.x) mx = fmax(mx, fabs(m1[r * cols + c]));
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? shm[threadIdx.x] : 0.0;
+    w = warp_max(w);
+    if (threadIdx.x == 0) shm[0] = w;
+  }
+  __syncthreads();
+  mx = shm[0];
+  __syncthreads();
+  long long first = (long long)rows1;
+  if (mx > 0.0) {
+    double thr = (1.0 - 1e-6) * mx;
+    for (int64_t r = threadIdx.x; r < rows1; r += blockDim.x)
+      if (fabs(m1[r * cols + c]) >= thr) { first = r; break; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    long long other = __shfl_xor_sync(0xffffffffu, first, o);
+    first = other < first ? other : first;
+  }
+  if ((threadIdx.x & 31) == 0) shi[threadIdx.x >> 5] = first;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long f = (long long)rows1;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) f = shi[i] < f ? shi[i] : f;
+    s_sign = (f < (long long)rows1 && m1[f * cols + c] < 0.0) ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  if (s_sign < 0.0) {
+    for (int64_t r = threadIdx.x; r < rows1; r += blockDim.x) m1[r * cols + c] = -m1[r * cols + c];
+    if (m2)
+      for (int64_t r = threadIdx.x; r < rows2; r += blockDim.x) m2[r * cols + c] = -m2[r * cols + c];
+  }
+}
+
+void sign_gauge(double *m1, int64_t rows1, double *m2, int64_t rows2, int64_t cols,
+                cudaStream_t s) {
+  if (cols == 0) return;
+  sign_gauge_kernel<<<(unsigned)cols, 256, 0, s>>>(m1, rows1, m2, rows2, cols);
+  TRG_LAUNCH_CHECK();
+}
+
+__global__ void fill_identity_kernel(double *out, int64_t n, int64_t cols) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * cols;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (i / cols == i % cols) ? 1.0 : 0.0;
+}
+void fill_identity(double *out, int64_t n, int64_t cols, cudaStream_t s) {
+  if (n * cols == 0) return;
+  fill_identity_kernel<<<grid_for(n * cols), 256, 0, s>>>(out, n, cols);
+  TRG_LAUNCH_CHECK();
+}
+
+// mode 0: x *= s; mode 1: x /= s (s > 0, else untouched)
+__global__ void scale_by_scalar_kernel(double *x, int64_t n, const double *scalar, int mode) {
+  double sc = *scalar;
+  double f = mode == 0 ? sc : (sc > 0.0 ? 1.0 / sc : 1.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+void scale_by_scalar(double *x, int64_t n, const double *scalar, int mode, cudaStream_t s) {
+  if (n == 0) return;
+  scale_by_scalar_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scalar, mode);
+  TRG_LAUNCH_CHECK();
+}
+
+__global__ void axpby_kernel(double *y, const double *x, double a, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+void axpby(double *y, const double *x, double a, double b, int64_t n, cudaStream_t s) {
+  if (n == 0) return;
+  axpby_kernel<<<grid_for(n), 256, 0, s>>>(y, x, a, b, n);
+  TRG_LAUNCH_CHECK();
+}
+
+__global__ void norm_update_kernel(const double *tr, double *c_out, double *logsum,
+                                   double weight, int *flag) {
+  double t = *tr;
+  double c = sqrt(t > 0.0 ? t : 0.0);
+  if (!(c > 0.0) || !isfinite(c)) {
+    *flag = TRG_ERR_NONFINITE;
+    c = 1.0;
+  }
+  *c_out = c;
+  *logsum += log(c) * weight;
+}
+void norm_update(const double *tr, double *c_out, double *logsum, double weight, int *flag,
+                 cudaStream_t s) {
+  norm_update_kernel<<<1, 1, 0, s>>>(tr, c_out, logsum, weight, flag);
+  TRG_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ arena
+void *Arena::alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  for (auto &c : chunks_) {
+    if (c.cap - c.used >= bytes) {
+      void *p = c.p + c.used;
+      c.used += bytes;
+      cur_ += bytes;
+      if (cur_ > high_) high_ = cur_;
+      return p;
+    }
+  }
+  size_t cap = bytes;
+  size_t last = chunks_.empty() ? 0 : chunks_.back().cap;
+  if (cap < 2 * last) cap = 2 * last;
+  if (cap < (size_t(64) << 20)) cap = size_t(64) << 20;
+  char *p = nullptr;
+  if (cudaMalloc(&p, cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = bytes;
+    if (cudaMalloc(&p, cap) != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(TRG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+  }
+  chunks_.push_back({p, cap, bytes});
+  cur_ += bytes;
+  if (cur_ > high_) high_ = cur_;
+  return p;
+}
+
+void Arena::reset() {
+  // merge into one chunk of the high-water size so that the next step needs one chunk
+  if (chunks_.size() > 1) {
+    for (auto &c : chunks_) cudaFree(c.p);
+    chunks_.clear();
+    char *p = nullptr;
+    if (cudaMalloc(&p, high_) == cudaSuccess)
+      chunks_.push_back({p, high_, 0});
+    else
+      cudaGetLastError();
+  }
+  for (auto &c : chunks_) c.used = 0;
+  cur_ = 0;
+}
+
+void Arena::release() {
+  for (auto &c : chunks_) cudaFree(c.p);
+  chunks_.clear();
+  cur_ = 0;
+}
+
+}  // namespace trg

@@ -1,0 +1,200 @@
+// Small dense FP64 linear algebra, one CTA per problem:
+//   * chol_rinv: upper Cholesky factor R of G (+ a relative diagonal shift) and R^{-1},
+//     with dead (non-positive) pivots mapped to zero rows/columns;
+//   * svd_jacobi: one-sided (Hestenes) Jacobi SVD with round-robin pair ordering, which
+//     keeps high relative accuracy of small singular values (Demmel & Veselic 1992).
+#include "trg_internal.h"
+
+namespace trg {
+
+// ------------------------------------------------------------------ Cholesky
+__global__ void chol_rinv_kernel(const double *G, double *R, double *Rinv, int n,
+                                 double rel_tol, double shift_rel) {
+  const int64_t off = (int64_t)blockIdx.x * n * n;
+  const double *g = G + off;
+  double *r = R + off;
+  double *x = Rinv + off;
+  __shared__ double s_scale, s_shift, s_piv;
+  __shared__ int s_dead;
+  if (threadIdx.x == 0) {
+    double mx = 0.0, tr = 0.0;
+    for (int i = 0; i < n; ++i) {
+      mx = fmax(mx, g[(int64_t)i * n + i]);
+      tr += g[(int64_t)i * n + i];
+    }
+    s_scale = mx;
+    s_shift = shift_rel * tr;
+  }
+  __syncthreads();
+  // working copy of the upper triangle (+ shift) in R
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
+    int i = (int)(idx / n), j = (int)(idx % n);
+    r[idx] = (j >= i) ? g[idx] + (i == j ? s_shift : 0.0) : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double p = r[(int64_t)j * n + j];
+      s_dead = !(p > rel_tol * s_scale && p > 0.0);
+      s_piv = s_dead ? 0.0 : sqrt(p);
+    }
+    __syncthreads();
+    const double piv = s_piv;
+    if (s_dead) {
+      for (int i = j + threadIdx.x; i < n; i += blockDim.x) r[(int64_t)j * n + i] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) r[(int64_t)j * n + i] /= piv;
+    __syncthreads();
+    if (threadIdx.x == 0) r[(int64_t)j * n + j] = piv;
+    const int t = n - j - 1;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)t * t; idx += blockDim.x) {
+      int a = j + 1 + (int)(idx / t), b = j + 1 + (int)(idx % t);
+      if (b >= a) r[(int64_t)a * n + b] -= r[(int64_t)j * n + a] * r[(int64_t)j * n + b];
+    }
+    __syncthreads();
+  }
+  // inverse of the upper-triangular R, one thread per column; dead rows give zeros
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = 0; i < n; ++i)
+      if (i > c) x[(int64_t)i * n + c] = 0.0;
+    for (int i = c; i >= 0; --i) {
+      double rii = r[(int64_t)i * n + i];
+      double v;
+      if (rii == 0.0) {
+        v = 0.0;
+      } else if (i == c) {
+        v = 1.0 / rii;
+      } else {
+        double sum = 0.0;
+        for (int k = i + 1; k <= c; ++k) sum += r[(int64_t)i * n + k] * x[(int64_t)k * n + c];
+        v = -sum / rii;
+      }
+      x[(int64_t)i * n + c] = v;
+    }
+  }
+}
+
+void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, double rel_tol,
+               double shift_rel, cudaStream_t s) {
+  if (n == 0 || batch == 0) return;
+  chol_rinv_kernel<<<batch, 256, 0, s>>>(G, R, Rinv, n, rel_tol, shift_rel);
+  TRG_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------ one-sided Jacobi
+constexpr int kSvdThreads = 512;
+constexpr int kMaxSweeps = 80;
+
+__device__ inline double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kSvdThreads)
+svd_jacobi_kernel(const double *A, int m, int n, double *U, double *S, double *V,
+                  double *work, int *info) {
+  const int64_t b = blockIdx.x;
+  const double *a = A + b * (int64_t)m * n;
+  double *at = work + b * ((int64_t)n * m + (int64_t)n * n);  // n rows of length m
+  double *vt = at + (int64_t)n * m;                             // n rows of length n
+  __shared__ int s_rot;
+  __shared__ int s_sweeps;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * m; idx += blockDim.x) {
+    int j = (int)(idx / m), r = (int)(idx % m);
+    at[idx] = a[(int64_t)r * n + j];
+  }
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x)
+    vt[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) s_sweeps = -1;
+  __syncthreads();
+  const int nn = n + (n & 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const double tol = 1e-15;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < nn - 1; ++rnd) {
+      for (int k = warp; k < nn / 2; k += nwarps) {
+        int p = (k == 0) ? 0 : ((k - 1 + rnd) % (nn - 1)) + 1;
+        int kk = nn - 1 - k;
+        int q = ((kk - 1 + rnd) % (nn - 1)) + 1;
+        int i = p < q ? p : q, j = p < q ? q : p;
+        if (j >= n) continue;  // dummy partner
+        double *ai = at + (int64_t)i * m, *aj = at + (int64_t)j * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < m; r += 32) {
+          double x = ai[r], y = aj[r];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = wsum(al);
+        be = wsum(be);
+        ga = wsum(ga);
+        if (!(fabs(ga) > tol * sqrt(al * be))) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t;
+        if (fabs(zeta) > 1e150)
+          t = 0.5 / zeta;
+        else
+          t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int r = lane; r < m; r += 32) {
+          double x = ai[r], y = aj[r];
+          ai[r] = c * x - s * y;
+          aj[r] = s * x + c * y;
+        }
+        double *vi = vt + (int64_t)i * n, *vj = vt + (int64_t)j * n;
+        for (int r = lane; r < n; r += 32) {
+          double x = vi[r], y = vj[r];
+          vi[r] = c * x - s * y;
+          vj[r] = s * x + c * y;
+        }
+        if (lane == 0) atomicAdd(&s_rot, 1);
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) {
+      if (threadIdx.x == 0) s_sweeps = sweep + 1;
+      break;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  // singular values = column norms; sort descending (stable by index)
+  __shared__ double s_norm[1024];
+  for (int j = warp; j < n; j += nwarps) {
+    double v = 0.0;
+    for (int r = lane; r < m; r += 32) v += at[(int64_t)j * m + r] * at[(int64_t)j * m + r];
+    v = wsum(v);
+    if (lane == 0) s_norm[j] = sqrt(v);
+  }
+  __syncthreads();
+  double *u = U + b * (int64_t)m * n;
+  double *sv = S + b * (int64_t)n;
+  double *v = V + b * (int64_t)n * n;
+  for (int j = warp; j < n; j += nwarps) {
+    double sj = s_norm[j];
+    int rank = 0;
+    for (int k = 0; k < n; ++k)
+      if (s_norm[k] > sj || (s_norm[k] == sj && k < j)) ++rank;
+    double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    for (int r = lane; r < m; r += 32) u[(int64_t)r * n + rank] = at[(int64_t)j * m + r] * inv;
+    for (int r = lane; r < n; r += 32) v[(int64_t)r * n + rank] = vt[(int64_t)j * n + r];
+    if (lane == 0) sv[rank] = sj;
+  }
+  if (threadIdx.x == 0 && info) info[b] = s_sweeps;
+}
+
+void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, int batch,
+                double *work, int *info, cudaStream_t s) {
+  if (n == 0 || batch == 0) return;
+  if (m < n) throw Error(TRG_ERR_ARG, "svd_jacobi needs m >= n");
+  if (n > 1024) throw Error(TRG_ERR_ARG, "svd_jacobi: n > 1024");
+  svd_jacobi_kernel<<<batch, kSvdThreads, 0, s>>>(A, m, n, U, S, V, work, info);
+  TRG_LAUNCH_CHECK();
+}
+
+}  // namespace trg

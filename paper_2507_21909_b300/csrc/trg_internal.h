@@ -1,0 +1,106 @@
+// Internal declarations of libtrg (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/trg.h"
+
+namespace trg {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define TRG_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw ::trg::Error(TRG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define TRG_LAUNCH_CHECK() TRG_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------------ device arena
+// Bump allocator over a few large cudaMalloc chunks.  Scratch of one step is released
+// at once by reset(); persistent state buffers are separate cudaMalloc'd buffers.
+class Arena {
+ public:
+  void *alloc(size_t bytes);
+  void reset();           // callers must have synchronised the stream first
+  void release();         // frees all chunks
+  size_t high_water() const { return high_; }
+  ~Arena() { release(); }
+
+ private:
+  struct Chunk { char *p; size_t cap; size_t used; };
+  std::vector<Chunk> chunks_;
+  size_t high_ = 0, cur_ = 0;
+};
+
+// dense row-major FP64 tensor living in the arena (or in a persistent buffer)
+struct Tensor {
+  double *p = nullptr;
+  std::vector<int64_t> dims;
+  int64_t size() const {
+    int64_t n = 1;
+    for (auto d : dims) n *= d;
+    return n;
+  }
+  int64_t dim(int i) const { return dims[i]; }
+};
+
+// --------------------------------------------------------------------- kernels
+void permute(const double *in, double *out, const std::vector<int64_t> &dims_in,
+             const std::vector<int> &perm, cudaStream_t s);
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, FP64 on CUDA cores
+void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+              const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
+              int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch,
+              cudaStream_t s);
+// Gaussian sketch: out[r*cols + c] from the counter-based SplitMix64 / Box-Muller rule
+void fill_gaussian(double *out, int64_t rows, int64_t cols, uint64_t key, cudaStream_t s);
+uint64_t sketch_key(uint64_t seed, int step, int tag);
+// out[(j, b), m] = g2[j, m] * g1[b, m]   (Khatri-Rao sketch, rows (J, beta))
+void khatri_rao(const double *g2, const double *g1, double *out, int64_t nj, int64_t nb,
+                int64_t w, cudaStream_t s);
+// x[i] *= f(v[(i / inner) % n])   mode 0: v, 1: pinv(v) (0 if v <= tol*max), 2: 1/sqrt
+// (alive), 3: sqrt(max(v,0)); `vmax` is a device scalar (max of v) for modes 1, 2
+void scale_axis(double *x, int64_t total, int64_t inner, int64_t n, const double *v,
+                int mode, const double *vmax, double tol, cudaStream_t s);
+// zero the entries of v (and of the matching columns of up to two matrices with n
+// columns) whose value is <= tol * v[0] (v sorted descending, v >= 0)
+void kill_dead(double *v, int64_t n, double tol, double *m1, int64_t rows1, double *m2,
+               int64_t rows2, cudaStream_t s);
+// deterministic dot product into a device scalar: *out = sum a[i] b[i]
+void dot(const double *a, const double *b, int64_t n, double *out, double *scratch,
+         cudaStream_t s);
+// per-column sign gauge of an (rows x cols) row-major matrix (first entry within
+// 1e-6 of the column's largest magnitude made positive); applied to m1 and m2
+void sign_gauge(double *m1, int64_t rows1, double *m2, int64_t rows2, int64_t cols,
+                cudaStream_t s);
+void fill_identity(double *out, int64_t n, int64_t cols, cudaStream_t s);
+void scale_by_scalar(double *x, int64_t n, const double *scalar, int mode, cudaStream_t s);
+void axpby(double *y, const double *x, double a, double b, int64_t n, cudaStream_t s);
+// step bookkeeping on device: c = sqrt(max(t, 0)); logsum += ln c * weight; flag non-finite
+void norm_update(const double *tr, double *c_out, double *logsum, double weight, int *flag,
+                 cudaStream_t s);
+void col_max_abs(const double *v, int64_t n, double *out, cudaStream_t s);
+
+// ------------------------------------------------------------- small linear algebra
+// Upper Cholesky factor R (R^T R = G + shift_rel * trace(G) * I) and its inverse, one
+// CTA per problem; a pivot <= rel_tol * max(diag G) marks the column dead (its rows of
+// R and columns of Rinv are zero).  G, R, Rinv: batch x n x n row-major.
+void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, double rel_tol,
+               double shift_rel, cudaStream_t s);
+// One-sided Jacobi SVD of batch m x n (m >= n) row-major matrices: A = U diag(S) V^T,
+// S descending.  U: m x n, V: n x n (row-major).  info[b] = sweeps used, or -1 if the
+// sweep limit was reached.  work: batch * (n*m + n*n) doubles.
+void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, int batch,
+                double *work, int *info, cudaStream_t s);
+
+}  // namespace trg
