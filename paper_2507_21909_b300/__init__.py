@@ -1,0 +1,18 @@
+"""B300-native triad-ATRG coarse-graining step (arXiv 2507.21909).
+
+The compute path is the in-tree CUDA library ``libtrg.so`` (sm_103a); ``_lib`` is a
+thin ctypes binding with the same entry-point names as ``include/trg.h``.  Accessing
+any entry point fails loudly (ImportError) if the library has not been built with
+``python -m paper_2507_21909_b300.build``; there is no CPU fallback.
+"""
+_NAMES = ("TRG_PREC_BF16X3", "TRG_PREC_BF16X6", "TRG_PREC_FP64", "TrgError", "lib",
+          "library_path", "trg_diag", "trg_finalize", "trg_free_energy", "trg_get_state",
+          "trg_init_clock", "trg_init_ising", "trg_magnetisation_impurity", "trg_set_params",
+          "trg_set_state", "trg_set_stream", "trg_step", "EXPORTED")
+
+
+def __getattr__(name):
+    if name in _NAMES:
+        from . import _lib
+        return getattr(_lib, name)
+    raise AttributeError(name)

@@ -1,0 +1,123 @@
+"""ctypes binding of libtrg (argument marshalling only; every step runs in CUDA)."""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_PATH = os.path.join(HERE, "libtrg.so")
+
+TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6 = 0, 1, 2
+EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
+            "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
+            "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error"]
+
+
+class TrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libtrg error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _PATH
+
+
+def _load():
+    if not os.path.exists(_PATH):
+        raise ImportError(f"{_PATH} is missing: build it with `python -m paper_2507_21909_b300.build`")
+    L = ctypes.CDLL(_PATH)
+    d, i, ull, vp = ctypes.c_double, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p
+    pd, pi = ctypes.POINTER(d), ctypes.POINTER(i)
+    sig = {
+        "trg_init_ising": [i, d, d], "trg_init_clock": [i, i, d, d], "trg_step": [i, i, i],
+        "trg_free_energy": [pd, pd], "trg_magnetisation_impurity": [pd],
+        "trg_set_params": [i, i, ull, i], "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
+        "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
+        "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i
+    L.trg_last_error.argtypes = []
+    L.trg_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(code):
+    if code != 0:
+        raise TrgError(code, lib.trg_last_error().decode())
+
+
+def trg_init_ising(d, beta, h=0.0):
+    _check(lib.trg_init_ising(int(d), float(beta), float(h)))
+
+
+def trg_init_clock(d, q, beta, h=0.0):
+    _check(lib.trg_init_clock(int(d), int(q), float(beta), float(h)))
+
+
+def trg_step(axis, D, sketch_oversample):
+    _check(lib.trg_step(int(axis), int(D), int(sketch_oversample)))
+
+
+def trg_free_energy():
+    f, lz = ctypes.c_double(), ctypes.c_double()
+    _check(lib.trg_free_energy(ctypes.byref(f), ctypes.byref(lz)))
+    return f.value, lz.value
+
+
+def trg_magnetisation_impurity():
+    m = ctypes.c_double()
+    _check(lib.trg_magnetisation_impurity(ctypes.byref(m)))
+    return m.value
+
+
+def trg_set_params(q_swap=4, q_rho=4, seed=0x5EED, precision=TRG_PREC_FP64):
+    _check(lib.trg_set_params(int(q_swap), int(q_rho), int(seed), int(precision)))
+
+
+def trg_set_stream(stream_ptr=None):
+    _check(lib.trg_set_stream(ctypes.c_void_p(stream_ptr or 0)))
+
+
+def trg_diag():
+    lc, g, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib.trg_diag(ctypes.byref(lc), ctypes.byref(g), ctypes.byref(n)))
+    return lc.value, g.value, n.value
+
+
+def trg_get_state(which):
+    """Returns (array of shape (d1,d2,d3,d4,r), axes tuple)."""
+    dims = (ctypes.c_int * 5)()
+    axes = (ctypes.c_int * 4)()
+    _check(lib.trg_get_state(int(which), dims, axes, None, 0))
+    shape = tuple(dims)
+    out = np.empty(shape, dtype=np.float64)
+    _check(lib.trg_get_state(int(which), dims, axes,
+                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+    return out, tuple(axes)
+
+
+def trg_set_state(beta, phi, psi, psi_imp, axes, nsteps, logsum):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    if phi.shape != psi.shape or phi.ndim != 5:
+        raise ValueError("phi and psi must have the same 5-leg shape")
+    dims = (ctypes.c_int * 5)(*phi.shape)
+    ax = (ctypes.c_int * 4)(*axes)
+    P = ctypes.POINTER(ctypes.c_double)
+    imp = None
+    if psi_imp is not None:
+        psi_imp = np.ascontiguousarray(psi_imp, dtype=np.float64)
+        imp = psi_imp.ctypes.data_as(P)
+    _check(lib.trg_set_state(float(beta), dims, phi.ctypes.data_as(P), psi.ctypes.data_as(P),
+                             imp, ax, int(nsteps), float(logsum)))
+
+
+def trg_finalize():
+    _check(lib.trg_finalize())

@@ -1,0 +1,821 @@
+// Step orchestration of libtrg and the C ABI (include/trg.h).
+//
+// One triad-ATRG coarse-graining step (arXiv 2507.21909, Sec. II B and Appendix A) as a
+// sequence of device kernels on one stream.  Every tensor contraction is planned as
+// (permute) + batched GEMM; the small dense decompositions run in the kernels of
+// linalg_small.cu.  Shapes are structural (fixed by D, p and the step history), so the
+// host never waits on device data inside a step except for the final status read.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <utility>
+
+#include "trg_internal.h"
+
+namespace trg {
+
+constexpr double kRankTol = 1e-13;     // singular values <= kRankTol * max are zeros
+constexpr double kShiftRel = 1e-14;    // relative shift of the first CholeskyQR pass
+constexpr double kPivotTol = 1e-13;    // dead-pivot threshold of the later passes
+
+// sketch tags of one step (same numbering in every implementation of the method)
+enum { TAG_SWAP_G1 = 1, TAG_SWAP_G2 = 2, TAG_RHO_A = 3, TAG_RHO_X = 4, TAG_RHO_Y = 5,
+       TAG_RHO_D = 6, TAG_SQ_F2 = 7, TAG_SQ_B2 = 10 };
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  Arena arena;
+  bool init = false;
+  bool have_imp = false;
+  double beta = 0.0;
+  double *phi = nullptr, *psi = nullptr, *psi_imp = nullptr;  // persistent state
+  std::vector<int64_t> dims;                                   // d1..d4, r
+  int axes[4] = {0, 1, 2, 3};
+  int nsteps = 0;
+  double *dscal = nullptr;  // [0] logsum [1] c [2] trace [3] trace2; [8..] dot scratch
+  int *dflag = nullptr;
+  int q_swap = 4, q_rho = 4, precision = TRG_PREC_FP64;
+  uint64_t seed = 0x5EED;
+  double last_logc = 0.0, last_gap = INFINITY;
+
+  Tensor alloc(std::vector<int64_t> d) {
+    Tensor t;
+    t.dims = std::move(d);
+    t.p = (double *)arena.alloc(std::max<int64_t>(t.size(), 1) * sizeof(double));
+    return t;
+  }
+  double *scratch() { return dscal + 8; }
+};
+
+static Ctx &ctx() {
+  static Ctx c;
+  return c;
+}
+static std::string g_err = "ok";
+
+static Tensor view(double *p, std::vector<int64_t> d) {
+  Tensor t;
+  t.p = p;
+  t.dims = std::move(d);
+  return t;
+}
+
+static int64_t prod(const std::vector<int64_t> &d, size_t a = 0, size_t b = SIZE_MAX) {
+  int64_t n = 1;
+  for (size_t i = a; i < std::min(b, d.size()); ++i) n *= d[i];
+  return n;
+}
+
+// ------------------------------------------------------------------ tensor helpers
+static Tensor copy(Ctx &c, const Tensor &a) {
+  Tensor t = c.alloc(a.dims);
+  TRG_CUDA(cudaMemcpyAsync(t.p, a.p, a.size() * sizeof(double), cudaMemcpyDeviceToDevice,
+                           c.stream));
+  return t;
+}
+
+static Tensor permuted(Ctx &c, const Tensor &a, const std::vector<int> &perm) {
+  std::vector<int64_t> d(perm.size());
+  for (size_t i = 0; i < perm.size(); ++i) d[i] = a.dims[perm[i]];
+  Tensor t = c.alloc(d);
+  permute(a.p, t.p, a.dims, perm, c.stream);
+  return t;
+}
+
+// C = op(A) op(B) for 2-D views
+static Tensor mm(Ctx &c, const Tensor &A, const Tensor &B, bool ta, bool tb) {
+  int64_t M = ta ? A.dims[1] : A.dims[0], K = ta ? A.dims[0] : A.dims[1];
+  int64_t Kb = tb ? B.dims[1] : B.dims[0], N = tb ? B.dims[0] : B.dims[1];
+  if (K != Kb) throw Error(TRG_ERR_ARG, "mm: inner dimensions differ");
+  Tensor C = c.alloc({M, N});
+  gemm_f64(ta, tb, M, N, K, 1.0, A.p, A.dims[1], 0, B.p, B.dims[1], 0, 0.0, C.p, N, 0, 1,
+           c.stream);
+  return C;
+}
+
+// first `ncols` columns of U (rows x ucols) applied from the right: C = Q U[:, :ncols]
+static Tensor mm_cols(Ctx &c, const Tensor &Q, const Tensor &U, int64_t ncols) {
+  int64_t M = Q.dims[0], K = Q.dims[1];
+  Tensor C = c.alloc({M, ncols});
+  gemm_f64(false, false, M, ncols, K, 1.0, Q.p, K, 0, U.p, U.dims[1], 0, 0.0, C.p, ncols, 0, 1,
+           c.stream);
+  return C;
+}
+
+// einsum-style contraction of two tensors (every index appears in exactly two of the
+// three index strings): batch = in all three, M = A and out, N = B and out, K = A and B.
+static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const Tensor &B) {
+  size_t comma = spec.find(','), arrow = spec.find("->");
+  std::string sa = spec.substr(0, comma), sb = spec.substr(comma + 1, arrow - comma - 1),
+              so = spec.substr(arrow + 2);
+  if ((int)sa.size() != (int)A.dims.size() || (int)sb.size() != (int)B.dims.size())
+    throw Error(TRG_ERR_ARG, "contract: rank mismatch in " + spec);
+  std::map<char, int64_t> dim;
+  for (size_t i = 0; i < sa.size(); ++i) dim[sa[i]] = A.dims[i];
+  for (size_t i = 0; i < sb.size(); ++i) {
+    auto it = dim.find(sb[i]);
+    if (it != dim.end() && it->second != B.dims[i])
+      throw Error(TRG_ERR_ARG, "contract: dimension mismatch in " + spec);
+    dim[sb[i]] = B.dims[i];
+  }
+  auto has = [](const std::string &s, char ch) { return s.find(ch) != std::string::npos; };
+  std::string bt, Mi, Ni, Ki;
+  for (char ch : so) {
+    if (has(sa, ch) && has(sb, ch)) bt += ch;
+    else if (has(sa, ch)) Mi += ch;
+    else if (has(sb, ch)) Ni += ch;
+    else throw Error(TRG_ERR_ARG, "contract: free output index in " + spec);
+  }
+  for (char ch : sa) {
+    if (has(sb, ch) && !has(so, ch)) Ki += ch;
+    if (!has(sb, ch) && !has(so, ch)) throw Error(TRG_ERR_ARG, "contract: lone index " + spec);
+  }
+  for (char ch : sb)
+    if (!has(sa, ch) && !has(so, ch)) throw Error(TRG_ERR_ARG, "contract: lone index " + spec);
+  auto pd = [&](const std::string &s) {
+    int64_t n = 1;
+    for (char ch : s) n *= dim[ch];
+    return n;
+  };
+  auto arrange = [&](const Tensor &T, const std::string &s, const std::string &want) {
+    std::vector<int> perm;
+    for (char ch : want) perm.push_back((int)s.find(ch));
+    return permuted(c, T, perm);
+  };
+  bool ta = false, tb = false;
+  const double *pa, *pb;
+  Tensor tA, tB;
+  if (sa == bt + Mi + Ki) pa = A.p;
+  else if (sa == bt + Ki + Mi) { pa = A.p; ta = true; }
+  else { tA = arrange(A, sa, bt + Mi + Ki); pa = tA.p; }
+  if (sb == bt + Ki + Ni) pb = B.p;
+  else if (sb == bt + Ni + Ki) { pb = B.p; tb = true; }
+  else { tB = arrange(B, sb, bt + Ki + Ni); pb = tB.p; }
+  int64_t nb = pd(bt), M = pd(Mi), N = pd(Ni), K = pd(Ki);
+  std::string nat = bt + Mi + Ni;
+  std::vector<int64_t> ndims;
+  for (char ch : nat) ndims.push_back(dim[ch]);
+  Tensor C = c.alloc(ndims);
+  gemm_f64(ta, tb, M, N, K, 1.0, pa, ta ? M : K, M * K, pb, tb ? K : N, K * N, 0.0, C.p, N,
+           M * N, nb, c.stream);
+  if (so == nat) return C;
+  std::vector<int> perm;
+  for (char ch : so) perm.push_back((int)nat.find(ch));
+  return permuted(c, C, perm);
+}
+
+static void scale_last(Ctx &c, Tensor &t, const double *v, int mode = 0,
+                       const double *vmax = nullptr, double tol = 0.0) {
+  int64_t n = t.dims.back();
+  scale_axis(t.p, t.size(), 1, n, v, mode, vmax, tol, c.stream);
+}
+
+// ------------------------------------------------------------- decompositions
+// Orthonormal basis of range(Y) (n x w) by shifted CholeskyQR3 (Fukaya et al. 2020):
+// each pass Q <- Q R^{-1} keeps the span, so the span error stays O(eps * cond(Y)) like
+// Householder QR; directions at the rounding level come out as zero columns.
+static Tensor orth_sc(Ctx &c, const Tensor &Y) {
+  int64_t w = Y.dims[1];
+  Tensor Q = Y;
+  for (int pass = 0; pass < 3; ++pass) {
+    Tensor G = mm(c, Q, Q, true, false);
+    Tensor R = c.alloc({w, w}), Ri = c.alloc({w, w});
+    chol_rinv(G.p, R.p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
+              pass == 0 ? kShiftRel : 0.0, c.stream);
+    Q = mm(c, Q, Ri, false, false);
+  }
+  return Q;
+}
+
+static std::pair<Tensor, Tensor> orth_qr(Ctx &c, const Tensor &Y) {
+  Tensor Q = orth_sc(c, Y);
+  Tensor R = mm(c, Q, Y, true, false);
+  return {Q, R};
+}
+
+struct Svd {
+  Tensor U, S, V;
+};
+static Svd svd_small(Ctx &c, const Tensor &A) {
+  int64_t m = A.dims[0], n = A.dims[1];
+  Svd r;
+  r.U = c.alloc({m, n});
+  r.S = c.alloc({n});
+  r.V = c.alloc({n, n});
+  Tensor work = c.alloc({n * m + n * n});
+  svd_jacobi(A.p, (int)m, (int)n, r.U.p, r.S.p, r.V.p, 1, work.p, nullptr, c.stream);
+  return r;
+}
+
+static Tensor transpose2(Ctx &c, const Tensor &a) { return permuted(c, a, {1, 0}); }
+
+static Tensor identity(Ctx &c, int64_t n) {
+  Tensor t = c.alloc({n, n});
+  fill_identity(t.p, n, n, c.stream);
+  return t;
+}
+
+// orthonormal basis (n x chi) of range(rho^(q+1) Omega), or the identity if chi >= n
+static Tensor rsvd_sym(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t key) {
+  int64_t n = rho.dims[0];
+  if (chi >= n) return identity(c, n);
+  Tensor Om = c.alloc({n, chi});
+  fill_gaussian(Om.p, n, chi, key, c.stream);
+  Tensor Q = orth_sc(c, mm(c, rho, Om, false, false));
+  for (int i = 0; i < q; ++i) Q = orth_sc(c, mm(c, rho, Q, false, false));
+  return Q;
+}
+
+// R (c' x n) with R^T R = Q Q^T rho Q Q^T, Q the rank-chi range of rho
+static Tensor gram_root(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t key) {
+  Tensor Q = rsvd_sym(c, rho, chi, q, key);
+  Tensor Bm = mm(c, Q, mm(c, rho, Q, false, false), true, false);
+  Svd sv = svd_small(c, Bm);
+  Tensor QV = mm(c, Q, sv.V, false, false);        // n x c'
+  Tensor R = transpose2(c, QV);                     // c' x n
+  scale_axis(R.p, R.size(), R.dims[1], R.dims[0], sv.S.p, 3, nullptr, 0.0, c.stream);
+  return R;
+}
+
+// oblique squeezer pair on one pair bond: M (n x k) on the forward side, N on the backward
+static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor &rb, int64_t D,
+                                          int64_t chi, int q, uint64_t kf, uint64_t kb,
+                                          double *gap_out) {
+  int64_t n = rf.dims[0];
+  if (n <= D) {
+    *gap_out = INFINITY;
+    return {identity(c, n), identity(c, n)};
+  }
+  Tensor R1 = gram_root(c, rf, chi, q, kf), R2 = gram_root(c, rb, chi, q, kb);
+  Tensor K = mm(c, R1, R2, false, true);
+  Svd sv = svd_small(c, K);
+  int64_t k = std::min<int64_t>(D, K.dims[1]);
+  Tensor M = mm_cols(c, transpose2(c, R2), sv.V, k);
+  Tensor N = mm_cols(c, transpose2(c, R1), sv.U, k);
+  scale_axis(M.p, M.size(), 1, k, sv.S.p, 2, sv.S.p, kRankTol, c.stream);
+  scale_axis(N.p, N.size(), 1, k, sv.S.p, 2, sv.S.p, kRankTol, c.stream);
+  sign_gauge(M.p, n, N.p, n, k, c.stream);
+  // relative gap at the cut, for diagnostics
+  std::vector<double> hs(K.dims[1]);
+  TRG_CUDA(cudaMemcpyAsync(hs.data(), sv.S.p, hs.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, c.stream));
+  TRG_CUDA(cudaStreamSynchronize(c.stream));
+  *gap_out = ((int64_t)hs.size() > k && hs[k - 1] > 0) ? (hs[k - 1] - hs[k]) / hs[k - 1]
+                                                        : INFINITY;
+  return {M, N};
+}
+
+// Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG; also eq. makeMH with
+// E=H, F=G roles handled by the caller through the index strings)
+static Tensor contract_upper(Ctx &c, const Tensor &E, const Tensor &F, const Tensor &I_,
+                             const Tensor &J_, const Tensor &M2, const Tensor &M3,
+                             const Tensor &M4) {
+  Tensor IM2 = contract(c, "bck,bBm->ckBm", I_, M2);
+  Tensor IM2J = contract(c, "ckBm,BCl->ckmCl", IM2, J_);
+  Tensor Theta = contract(c, "ckmCl,cCn->klmn", IM2J, M3);       // (kA kX k2 k3)
+  Tensor EM = contract(c, "tkda,dDm->tkamD", E, M4);             // (t kA al k4 q4)
+  Tensor Phi1 = contract(c, "tkamD,alDg->tkmlg", EM, F);         // (t kA k4 kX g)
+  return contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta);          // (t k2 k3 k4 g)
+}
+
+static Tensor contract_lower(Ctx &c, const Tensor &G, const Tensor &H, const Tensor &K_,
+                             const Tensor &L_, const Tensor &N2, const Tensor &N3,
+                             const Tensor &N4) {
+  Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);
+  Tensor KN2L = contract(c, "ckBm,BCl->ckmCl", KN2, L_);
+  Tensor Theta = contract(c, "ckmCl,cCn->klmn", KN2L, N3);       // (kY kD k2 k3)
+  Tensor HN = contract(c, "wkdb,Ddm->wkbmD", H, N4);             // (w kD be k4 P4)
+  Tensor Psi1 = contract(c, "wkbmD,bjDg->wkmjg", HN, G);         // (w kD k4 kY g)
+  return contract(c, "wkmjg,jkKL->wKLmg", Psi1, Theta);          // (w k2 k3 k4 g)
+}
+
+static void replace_state(double *&dst, const Tensor &src, cudaStream_t s) {
+  if (dst) TRG_CUDA(cudaFree(dst));
+  dst = nullptr;
+  if (cudaMalloc(&dst, std::max<int64_t>(src.size(), 1) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    dst = nullptr;
+    throw Error(TRG_ERR_OOM, "state allocation failed");
+  }
+  TRG_CUDA(cudaMemcpyAsync(dst, src.p, src.size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+
+// bring the slot of physical `axis` to the front, keeping the cyclic leg order
+static void rotate(Ctx &c, int axis) {
+  int slot = -1;
+  for (int i = 0; i < 4; ++i)
+    if (c.axes[i] == axis) slot = i;
+  if (slot < 0) throw Error(TRG_ERR_ARG, "axis out of range");
+  if (slot == 0) return;
+  std::vector<int> perm = {slot, (slot + 1) % 4, (slot + 2) % 4, (slot + 3) % 4, 4};
+  for (double **buf : {&c.phi, &c.psi, &c.psi_imp}) {
+    if (!*buf) continue;
+    Tensor t = permuted(c, view(*buf, c.dims), perm);
+    TRG_CUDA(cudaMemcpyAsync(*buf, t.p, t.size() * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c.stream));
+  }
+  std::vector<int64_t> nd(5);
+  int na[4];
+  for (int i = 0; i < 5; ++i) nd[i] = c.dims[perm[i]];
+  for (int i = 0; i < 4; ++i) na[i] = c.axes[perm[i]];
+  c.dims = nd;
+  std::memcpy(c.axes, na, sizeof(na));
+}
+
+// ----------------------------------------------------------------------- the step
+static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
+  cudaStream_t s = c.stream;
+  rotate(c, axis);
+  const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], d4 = c.dims[3], r = c.dims[4];
+  const int64_t Nf = d1 * d2 * d3 * d4;
+  const int n = c.nsteps;
+  auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
+
+  // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
+  Tensor P2 = view(c.phi, {Nf, r}), S2 = view(c.psi, {Nf, r});
+  auto [Qp, Rp] = orth_qr(c, P2);
+  auto [Qs, Rs] = orth_qr(c, S2);
+  Svd rs = svd_small(c, mm(c, Rp, Rs, false, true));
+  const int64_t k = std::min<int64_t>(D, r);
+  Tensor A = mm_cols(c, Qp, rs.U, k), Dm = mm_cols(c, Qs, rs.V, k);
+  sign_gauge(A.p, Nf, Dm.p, Nf, k, s);
+  double *sv = rs.S.p;  // first k entries used
+  kill_dead(sv, k, kRankTol, A.p, Nf, Dm.p, Nf, s);
+  A.dims = {d1, d2, d3, d4, k};
+  Dm.dims = {d1, d2, d3, d4, k};
+
+  // (b) bond swap: sum_x B[x J al] C[x I be] ~ X sigma Y  (Appendix A), applied to the
+  //     uncompressed M; identical in exact arithmetic to the QR-compressed M'.
+  Tensor C = copy(c, A), B = copy(c, Dm);
+  scale_last(c, C, sv);
+  scale_last(c, B, sv);
+  const int64_t x = d1, I = d2 * d3 * d4, J = I;
+  const int64_t w = std::min<int64_t>(D + p, k * I);
+  Tensor g1 = c.alloc({k, w}), g2 = c.alloc({J, w}), Om = c.alloc({J * k, w});
+  fill_gaussian(g1.p, k, w, key(TAG_SWAP_G1), s);
+  fill_gaussian(g2.p, J, w, key(TAG_SWAP_G2), s);
+  khatri_rao(g2.p, g1.p, Om.p, J, k, w, s);
+  Tensor Cp = permuted(c, view(C.p, {x, I, k}), {1, 0, 2});   // (I, x, be)
+  Tensor Bp = permuted(c, view(B.p, {x, J, k}), {1, 0, 2});   // (J, x, al)
+  auto applyM = [&](const Tensor &V) {                          // V: (J be) x w
+    Tensor Z = c.alloc({x, k, k, w});                           // (x, al, be, m)
+    gemm_f64(true, false, k, k * w, J, 1.0, B.p, k, J * k, V.p, k * w, 0, 0.0, Z.p, k * w,
+             k * k * w, x, s);
+    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x, be, al, m)
+    Tensor Y = c.alloc({I * k, w});
+    gemm_f64(false, false, I, k * w, x * k, 1.0, Cp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Y.p,
+             k * w, 0, 1, s);
+    return Y;                                                    // (I al) x w
+  };
+  auto applyMt = [&](const Tensor &U) {                         // U: (I al) x w
+    Tensor Z = c.alloc({x, k, k, w});                           // (x, be, al, m)
+    gemm_f64(true, false, k, k * w, I, 1.0, C.p, k, I * k, U.p, k * w, 0, 0.0, Z.p, k * w,
+             k * k * w, x, s);
+    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x, al, be, m)
+    Tensor Yt = c.alloc({J * k, w});
+    gemm_f64(false, false, J, k * w, x * k, 1.0, Bp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Yt.p,
+             k * w, 0, 1, s);
+    return Yt;                                                   // (J be) x w
+  };
+  Tensor V = Om, Q, Yt;
+  for (int rnd = 0; rnd < c.q_swap; ++rnd) {
+    Q = orth_sc(c, applyM(V));
+    Yt = applyMt(Q);
+    if (rnd + 1 < c.q_swap) V = orth_sc(c, Yt);
+  }
+  auto [Qt, Rt] = orth_qr(c, Yt);              // M^T Q = Qt Rt  ->  Q^T M = Rt^T Qt^T
+  Svd cs = svd_small(c, transpose2(c, Rt));
+  const int64_t Dg = std::min<int64_t>(D, w);
+  Tensor Xf = mm_cols(c, Q, cs.U, Dg), Yf = mm_cols(c, Qt, cs.V, Dg);
+  double *sig = cs.S.p;
+  kill_dead(sig, Dg, kRankTol, Xf.p, I * k, Yf.p, J * k, s);
+  Tensor X = permuted(c, view(Xf.p, {I, k, Dg}), {1, 0, 2});
+  Tensor Y = permuted(c, view(Yf.p, {J, k, Dg}), {1, 0, 2});
+  X.dims = {k, d2, d3, d4, Dg};
+  Y.dims = {k, d2, d3, d4, Dg};
+  double gap_swap = INFINITY;
+  {
+    std::vector<double> hs(w);
+    TRG_CUDA(cudaMemcpyAsync(hs.data(), cs.S.p, w * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRG_CUDA(cudaStreamSynchronize(s));
+    if (w > Dg && hs[Dg - 1] > 0) gap_swap = (hs[Dg - 1] - hs[Dg]) / hs[Dg - 1];
+  }
+
+  // (c) triad isometries from the canonical-form Grams (eq. HOSVD)
+  Tensor Xs = copy(c, X), Ys = copy(c, Y);
+  scale_last(c, Xs, sig);
+  scale_last(c, Ys, sig);
+  Tensor Wal = mm(c, view(Xs.p, {k, I * Dg}), view(Xs.p, {k, I * Dg}), false, true);
+  Tensor Wbe = mm(c, view(Ys.p, {k, J * Dg}), view(Ys.p, {k, J * Dg}), false, true);
+  Tensor AW = mm(c, view(A.p, {Nf, k}), Wal, false, false);
+  AW.dims = A.dims;
+  Tensor DW = mm(c, view(Dm.p, {Nf, k}), Wbe, false, false);
+  DW.dims = Dm.dims;
+  const int64_t npair = d2 * d3;
+  Tensor rhoA = contract(c, "tbcda,tBCda->bcBC", A, AW);
+  Tensor rhoX = contract(c, "abcdg,aBCdg->bcBC", Xs, Xs);
+  Tensor rhoY = contract(c, "bPQRg,bSTRg->PQST", Ys, Ys);
+  Tensor rhoD = contract(c, "wPQRb,wSTRb->PQST", Dm, DW);
+  const int64_t chi = std::min<int64_t>(D + p, npair);
+  auto iso = [&](Tensor &rho, int tag) {
+    Tensor U = rsvd_sym(c, view(rho.p, {npair, npair}), chi, c.q_rho, key(tag));
+    U.dims = {d2, d3, U.dims[1]};
+    return U;
+  };
+  Tensor UA = iso(rhoA, TAG_RHO_A), UX = iso(rhoX, TAG_RHO_X), UY = iso(rhoY, TAG_RHO_Y),
+         UD = iso(rhoD, TAG_RHO_D);
+
+  // (d) triads, eqs. E-L
+  Tensor E = contract(c, "tbcda,bck->tkda", A, UA);
+  Tensor F = contract(c, "abcdg,bck->akdg", X, UX);
+  scale_last(c, F, sig);
+  Tensor G = contract(c, "bPQRg,PQk->bkRg", Y, UY);
+  Tensor H = contract(c, "wPQRb,PQk->wkRb", Dm, UD);
+  const Tensor &I_ = UA, &J_ = UX, &K_ = UY, &L_ = UD;
+
+  // (e) Gram matrices O (upper block) and P (lower block), environments, squeezers
+  Tensor Ig = contract(c, "bck,bcl->kl", I_, I_), Jg = contract(c, "bck,bcl->kl", J_, J_);
+  Tensor Kg = contract(c, "bck,bcl->kl", K_, K_), Lg = contract(c, "bck,bcl->kl", L_, L_);
+  Tensor EI = contract(c, "tkda,kl->tlda", E, Ig);
+  Tensor EEI = contract(c, "tlda,tlde->ae", EI, E);
+  Tensor FJ = contract(c, "eldh,kl->ekdh", F, Jg);
+  Tensor O = contract(c, "akdg,akdh->gh", F, contract(c, "ae,ekdh->akdh", EEI, FJ));
+  Tensor HL = contract(c, "wkdb,kl->wldb", H, Lg);
+  Tensor HHL = contract(c, "wldb,wlde->be", HL, H);
+  Tensor GK = contract(c, "eldh,kl->ekdh", G, Kg);
+  Tensor Pm = contract(c, "bkdg,bkdh->gh", G, contract(c, "be,ekdh->bkdh", HHL, GK));
+
+  std::map<int, Tensor> rf, rb;
+  Tensor EE4 = contract(c, "tlda,tlDe->daDe", EI, E);                       // (p4 al p4' al')
+  Tensor FP = contract(c, "akdg,gh->akdh", F, Pm);
+  Tensor FPJ = contract(c, "akdh,kl->aldh", FP, Jg);
+  Tensor FPF4 = contract(c, "aldh,elDh->adeD", FPJ, F);                     // (al q4 al' q4')
+  rf[4] = contract(c, "paPe,aqeQ->pqPQ", EE4, FPF4);
+  Tensor GO = contract(c, "bkPg,gh->bkPh", G, O);
+  Tensor GOK = contract(c, "bkPh,kl->blPh", GO, Kg);
+  Tensor GOG4 = contract(c, "blPh,elQh->bPeQ", GOK, G);                     // (be P4 be' P4')
+  Tensor HH4 = contract(c, "wldb,wlDe->bdeD", HL, H);                       // (be Q4 be' Q4')
+  rb[4] = contract(c, "bPeR,bQeS->PQRS", GOG4, HH4);
+  Tensor EE2 = contract(c, "tkda,tlde->kale", E, E);
+  Tensor FPF2 = contract(c, "akdh,eldh->akel", FP, F);
+  Tensor GOG2 = contract(c, "bkdh,eldh->kble", GO, G);
+  Tensor HH2 = contract(c, "wkdb,wlde->kble", H, H);
+  for (int mu : {2, 3}) {
+    const char *sub = mu == 2 ? "bck,Bcl->bkBl" : "cbk,cBl->bkBl";
+    Tensor II = contract(c, sub, I_, I_), JJ = contract(c, sub, J_, J_);
+    Tensor KK = contract(c, sub, K_, K_), LL = contract(c, sub, L_, L_);
+    Tensor G1 = contract(c, "pkPl,kale->paPe", II, EE2);
+    Tensor G2 = contract(c, "qkQl,akel->aqeQ", JJ, FPF2);
+    rf[mu] = contract(c, "paPe,aqeQ->pqPQ", G1, G2);
+    Tensor G1b = contract(c, "PkRl,kble->PbRe", KK, GOG2);
+    Tensor G2b = contract(c, "QkSl,kble->bQeS", LL, HH2);
+    rb[mu] = contract(c, "PbRe,bQeS->PQRS", G1b, G2b);
+  }
+  const int64_t dmu[5] = {0, 0, d2, d3, d4};
+  std::map<int, Tensor> Msq, Nsq;
+  double gap_sq = INFINITY;
+  for (int mu : {2, 3, 4}) {
+    int64_t nn = dmu[mu] * dmu[mu];
+    double g;
+    auto [M, N] = squeezer(c, view(rf[mu].p, {nn, nn}), view(rb[mu].p, {nn, nn}), D,
+                           std::min<int64_t>(D + p, nn), c.q_rho, key(TAG_SQ_F2 + mu - 2),
+                           key(TAG_SQ_B2 + mu - 2), &g);
+    gap_sq = std::min(gap_sq, g);
+    M.dims = {dmu[mu], dmu[mu], M.dims[1]};
+    N.dims = {dmu[mu], dmu[mu], N.dims[1]};
+    Msq[mu] = M;
+    Nsq[mu] = N;
+  }
+
+  // (f) coarse contraction, eqs. makeMG / makeMH
+  Tensor PhiN = contract_upper(c, E, F, I_, J_, Msq[2], Msq[3], Msq[4]);
+  Tensor PsiN = contract_lower(c, G, H, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+  Tensor PsiImpN;
+  if (c.have_imp) {
+    // impurity at slot n+1: B_imp = T_imp^T A; frozen X projector -> Y_imp = M_imp^T X / sigma
+    Tensor PA = mm(c, view(c.phi, {Nf, r}), view(A.p, {Nf, k}), true, false);
+    Tensor Bimp = mm(c, view(c.psi_imp, {Nf, r}), PA, false, false);
+    Bimp.dims = {x, d2, d3, d4, k};
+    Tensor CX = contract(c, "xIJKb,aIJKg->xbag", view(C.p, {x, d2, d3, d4, k}), X);
+    Tensor Ytil = contract(c, "xPQRa,xbag->bPQRg", Bimp, CX);
+    scale_last(c, Ytil, sig, 1, sig, 0.0);
+    Tensor Gimp = contract(c, "bPQRg,PQk->bkRg", Ytil, UY);
+    // impurity at slot n: D_imp = T_imp^T A s^+, frozen U^D
+    Tensor Dimp = copy(c, Bimp);
+    scale_last(c, Dimp, sv, 1, sv, 0.0);
+    Tensor Himp = contract(c, "wPQRb,PQk->wkRb", Dimp, UD);
+    PsiImpN = contract_lower(c, Gimp, H, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+    Tensor Pb = contract_lower(c, G, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+    axpby(PsiImpN.p, Pb.p, 0.5, 0.5, PsiImpN.size(), s);
+  }
+
+  // normalisation c_n = ||T||_F and ln Z bookkeeping
+  const int64_t rn = PhiN.dims[4], Nn = PhiN.size() / rn;
+  Tensor Gp = mm(c, view(PhiN.p, {Nn, rn}), view(PhiN.p, {Nn, rn}), true, false);
+  Tensor Gs = mm(c, view(PsiN.p, {Nn, rn}), view(PsiN.p, {Nn, rn}), true, false);
+  dot(Gp.p, Gs.p, rn * rn, c.dscal + 2, c.scratch(), s);
+  norm_update(c.dscal + 2, c.dscal + 1, c.dscal + 0, std::ldexp(1.0, -(n + 1)), c.dflag, s);
+  scale_by_scalar(PsiN.p, PsiN.size(), c.dscal + 1, 1, s);
+  if (c.have_imp) scale_by_scalar(PsiImpN.p, PsiImpN.size(), c.dscal + 1, 1, s);
+
+  replace_state(c.phi, PhiN, s);
+  replace_state(c.psi, PsiN, s);
+  if (c.have_imp) replace_state(c.psi_imp, PsiImpN, s);
+  c.dims = PhiN.dims;
+  c.nsteps = n + 1;
+  double hc = 1.0;
+  int flag = 0;
+  TRG_CUDA(cudaMemcpyAsync(&hc, c.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRG_CUDA(cudaMemcpyAsync(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRG_CUDA(cudaStreamSynchronize(s));
+  c.last_logc = std::log(hc);
+  c.last_gap = std::min(gap_swap, gap_sq);
+  c.arena.reset();
+  if (flag) throw Error(flag, "non-finite norm in the coarse-graining step");
+}
+
+// -------------------------------------------------------------------- init helpers
+static void ensure_ctx(Ctx &c) {
+  if (!c.dscal) {
+    TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
+    TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
+  }
+  if (!c.stream && !c.own_stream) {
+    TRG_CUDA(cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking));
+    c.stream = c.own_stream;
+  }
+}
+
+static void free_state(Ctx &c) {
+  for (double **b : {&c.phi, &c.psi, &c.psi_imp}) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  c.init = false;
+}
+
+// T0 from a CP factor W (rows: site states, columns: bond index), weights and observable
+static void init_cp(Ctx &c, double beta, const std::vector<double> &W, int nstate, int nb,
+                    const std::vector<double> &weight, const std::vector<double> &obs) {
+  ensure_ctx(c);
+  TRG_CUDA(cudaStreamSynchronize(c.stream));
+  free_state(c);
+  int64_t nf = (int64_t)nb * nb * nb * nb;
+  std::vector<double> phi(nf * nstate), psi(nf * nstate), imp(nf * nstate);
+  for (int64_t i = 0; i < nf; ++i) {
+    int64_t leg[4] = {i / (nb * nb * nb), (i / (nb * nb)) % nb, (i / nb) % nb, i % nb};
+    for (int a = 0; a < nstate; ++a) {
+      double v = 1.0;
+      for (int mu = 0; mu < 4; ++mu) v *= W[a * nb + leg[mu]];
+      phi[i * nstate + a] = v;
+      psi[i * nstate + a] = v * weight[a];
+      imp[i * nstate + a] = v * weight[a] * obs[a];
+    }
+  }
+  c.dims = {nb, nb, nb, nb, nstate};
+  for (int i = 0; i < 4; ++i) c.axes[i] = i;
+  for (auto pr : {std::make_pair(&c.phi, &phi), std::make_pair(&c.psi, &psi),
+                  std::make_pair(&c.psi_imp, &imp)}) {
+    TRG_CUDA(cudaMalloc(pr.first, pr.second->size() * sizeof(double)));
+    TRG_CUDA(cudaMemcpyAsync(*pr.first, pr.second->data(), pr.second->size() * sizeof(double),
+                             cudaMemcpyHostToDevice, c.stream));
+  }
+  TRG_CUDA(cudaMemsetAsync(c.dscal, 0, 8 * sizeof(double), c.stream));
+  TRG_CUDA(cudaMemsetAsync(c.dflag, 0, sizeof(int), c.stream));
+  Tensor Gp = mm(c, view(c.phi, {nf, nstate}), view(c.phi, {nf, nstate}), true, false);
+  Tensor Gs = mm(c, view(c.psi, {nf, nstate}), view(c.psi, {nf, nstate}), true, false);
+  dot(Gp.p, Gs.p, (int64_t)nstate * nstate, c.dscal + 2, c.scratch(), c.stream);
+  norm_update(c.dscal + 2, c.dscal + 1, c.dscal + 0, 1.0, c.dflag, c.stream);
+  scale_by_scalar(c.psi, nf * nstate, c.dscal + 1, 1, c.stream);
+  scale_by_scalar(c.psi_imp, nf * nstate, c.dscal + 1, 1, c.stream);
+  TRG_CUDA(cudaStreamSynchronize(c.stream));
+  c.arena.reset();
+  c.beta = beta;
+  c.nsteps = 0;
+  c.have_imp = true;
+  c.init = true;
+}
+
+}  // namespace trg
+
+// ================================================================== C ABI
+using namespace trg;
+
+template <class F>
+static trg_status guarded(F &&f) {
+  try {
+    f();
+    g_err = "ok";
+    return TRG_OK;
+  } catch (const Error &e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::exception &e) {
+    g_err = e.what();
+    return TRG_ERR_CUDA;
+  }
+}
+
+extern "C" {
+
+trg_status trg_init_ising(int d, double beta, double h) {
+  return guarded([&] {
+    if (d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 4");
+    if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
+      throw Error(TRG_ERR_ARG, "need finite beta >= 0 and finite h");
+    double cb = std::sqrt(std::cosh(beta)), sb = std::sqrt(std::sinh(beta));
+    init_cp(ctx(), beta, {cb, sb, cb, -sb}, 2, 2, {std::exp(h), std::exp(-h)}, {1.0, -1.0});
+  });
+}
+
+trg_status trg_init_clock(int d, int q, double beta, double h) {
+  return guarded([&] {
+    if (d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 4");
+    if (q < 2 || q > 8 || !(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
+      throw Error(TRG_ERR_ARG, "need 2 <= q <= 8, finite beta >= 0 and finite h");
+    // real Fourier basis diagonalises the circulant bond matrix exp(beta cos(th - th'))
+    std::vector<std::vector<double>> F;
+    std::vector<double> th(q);
+    for (int k = 0; k < q; ++k) th[k] = 2.0 * M_PI * k / q;
+    F.push_back(std::vector<double>(q, 1.0 / std::sqrt((double)q)));
+    for (int m = 1; m <= (q - 1) / 2; ++m) {
+      std::vector<double> cc(q), ss(q);
+      for (int k = 0; k < q; ++k) {
+        cc[k] = std::cos(m * th[k]) * std::sqrt(2.0 / q);
+        ss[k] = std::sin(m * th[k]) * std::sqrt(2.0 / q);
+      }
+      F.push_back(cc);
+      F.push_back(ss);
+    }
+    if (q % 2 == 0) {
+      std::vector<double> alt(q);
+      for (int k = 0; k < q; ++k) alt[k] = std::cos(M_PI * k) / std::sqrt((double)q);
+      F.push_back(alt);
+    }
+    std::vector<double> W(q * q), wt(q), obs(q);
+    for (int m = 0; m < q; ++m) {
+      double lam = 0.0;
+      for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b)
+          lam += F[m][a] * std::exp(beta * std::cos(th[a] - th[b])) * F[m][b];
+      if (lam < 0.0) lam = 0.0;
+      for (int a = 0; a < q; ++a) W[a * q + m] = F[m][a] * std::sqrt(lam);
+    }
+    for (int a = 0; a < q; ++a) {
+      obs[a] = std::cos(th[a]);
+      wt[a] = std::exp(h * obs[a]);
+    }
+    init_cp(ctx(), beta, W, q, q, wt, obs);
+  });
+}
+
+trg_status trg_step(int axis, int D, int sketch_oversample) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
+    if (axis < 0 || axis > 3 || D < 1 || sketch_oversample < 0)
+      throw Error(TRG_ERR_ARG, "need 0 <= axis < 4, D >= 1, p >= 0");
+    if (c.precision != TRG_PREC_FP64)
+      throw Error(TRG_ERR_ARG, "this build runs the FP64 form only");
+    try {
+      step_impl(c, axis, D, sketch_oversample);
+    } catch (...) {
+      cudaStreamSynchronize(c.stream);
+      c.arena.reset();
+      throw;
+    }
+  });
+}
+
+trg_status trg_free_energy(double *f_per_site, double *lnZ_per_site) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
+    int64_t n = prod(c.dims);
+    dot(c.phi, c.psi, n, c.dscal + 3, c.scratch(), c.stream);
+    double h[4];
+    TRG_CUDA(cudaMemcpyAsync(h, c.dscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    double lz = h[0] + std::log(std::fabs(h[3])) * std::ldexp(1.0, -c.nsteps);
+    if (lnZ_per_site) *lnZ_per_site = lz;
+    if (f_per_site) *f_per_site = c.beta > 0.0 ? -lz / c.beta : NAN;
+  });
+}
+
+trg_status trg_magnetisation_impurity(double *m) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!c.init || !c.have_imp) throw Error(TRG_ERR_NOINIT, "no impurity state");
+    if (!m) throw Error(TRG_ERR_ARG, "m is NULL");
+    int64_t n = prod(c.dims);
+    dot(c.phi, c.psi, n, c.dscal + 3, c.scratch(), c.stream);
+    dot(c.phi, c.psi_imp, n, c.dscal + 4, c.scratch(), c.stream);
+    double h[2];
+    TRG_CUDA(cudaMemcpyAsync(h, c.dscal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    *m = h[1] / h[0];
+  });
+}
+
+trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision) {
+  return guarded([&] {
+    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > 2)
+      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..2");
+    Ctx &c = ctx();
+    c.q_swap = q_swap;
+    c.q_rho = q_rho;
+    c.seed = seed;
+    c.precision = precision;
+  });
+}
+
+trg_status trg_set_stream(void *cuda_stream) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (c.stream) TRG_CUDA(cudaStreamSynchronize(c.stream));
+    c.stream = cuda_stream ? (cudaStream_t)cuda_stream : c.own_stream;
+  });
+}
+
+trg_status trg_diag(double *log_c, double *min_gap, int *nsteps) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (log_c) *log_c = c.last_logc;
+    if (min_gap) *min_gap = c.last_gap;
+    if (nsteps) *nsteps = c.nsteps;
+  });
+}
+
+trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
+                         long long capacity) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
+    if (which < 0 || which > 2 || !dims_out) throw Error(TRG_ERR_ARG, "bad which / dims_out");
+    double *src = which == 0 ? c.phi : which == 1 ? c.psi : c.psi_imp;
+    if (!src) throw Error(TRG_ERR_ARG, "factor not present");
+    for (int i = 0; i < 5; ++i) dims_out[i] = (int)c.dims[i];
+    if (axes_out)
+      for (int i = 0; i < 4; ++i) axes_out[i] = c.axes[i];
+    if (host) {
+      int64_t n = prod(c.dims);
+      if (capacity < n) throw Error(TRG_ERR_ARG, "host buffer too small");
+      TRG_CUDA(cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      TRG_CUDA(cudaStreamSynchronize(c.stream));
+    }
+  });
+}
+
+trg_status trg_set_state(double beta, const int *dims, const double *phi, const double *psi,
+                         const double *psi_imp, const int *axes, int nsteps, double logsum) {
+  return guarded([&] {
+    if (!dims || !phi || !psi || !axes || nsteps < 0) throw Error(TRG_ERR_ARG, "bad state");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    free_state(c);
+    c.dims.assign(dims, dims + 5);
+    for (auto d : c.dims)
+      if (d < 1) throw Error(TRG_ERR_ARG, "dims must be >= 1");
+    for (int i = 0; i < 4; ++i) c.axes[i] = axes[i];
+    int64_t n = prod(c.dims);
+    for (auto pr : {std::make_pair(&c.phi, phi), std::make_pair(&c.psi, psi),
+                    std::make_pair(&c.psi_imp, psi_imp)}) {
+      if (!pr.second) continue;
+      TRG_CUDA(cudaMalloc(pr.first, n * sizeof(double)));
+      TRG_CUDA(cudaMemcpyAsync(*pr.first, pr.second, n * sizeof(double), cudaMemcpyHostToDevice,
+                               c.stream));
+    }
+    double sc[8] = {logsum, 1.0, 0, 0, 0, 0, 0, 0};
+    TRG_CUDA(cudaMemcpyAsync(c.dscal, sc, sizeof(sc), cudaMemcpyHostToDevice, c.stream));
+    TRG_CUDA(cudaMemsetAsync(c.dflag, 0, sizeof(int), c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    c.beta = beta;
+    c.nsteps = nsteps;
+    c.have_imp = psi_imp != nullptr;
+    c.init = true;
+  });
+}
+
+trg_status trg_finalize(void) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    free_state(c);
+    c.arena.release();
+    if (c.dscal) cudaFree(c.dscal);
+    if (c.dflag) cudaFree(c.dflag);
+    c.dscal = nullptr;
+    c.dflag = nullptr;
+    if (c.own_stream) cudaStreamDestroy(c.own_stream);
+    c.own_stream = nullptr;
+    c.stream = nullptr;
+  });
+}
+
+const char *trg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
