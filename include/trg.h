@@ -85,6 +85,12 @@ trg_status trg_set_stream(void *cuda_stream);
  * the bond-swap and squeezer truncations, and the number of steps taken. */
 trg_status trg_diag(double *log_c, double *min_gap, int *nsteps);
 
+/* Device time (ms, CUDA events on the library stream) of the phases of the last step:
+ * [0] leg rotation + re-split, [1] bond swap, [2] triad isometries, [3] triads, Grams O, P
+ * and environments, [4] squeezers, [5] coarse contraction Phi, Psi, [6] impurity,
+ * [7] normalisation and state update.  Writes min(n, 8) values. */
+trg_status trg_step_timings(double *ms, int n);
+
 /* Copy a state factor to the host.  which: 0 = Phi, 1 = Psi, 2 = Psi_imp.
  * dims_out[0..4] receives (d1, d2, d3, d4, r); host may be NULL (query only), else it
  * must hold `capacity` doubles >= d1 d2 d3 d4 r.  axes_out[0..3] (may be NULL) gets

@@ -10,7 +10,8 @@ _PATH = os.path.join(HERE, "libtrg.so")
 TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6 = 0, 1, 2
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
-            "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error"]
+            "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
+            "trg_step_timings"]
 
 
 class TrgError(RuntimeError):
@@ -35,6 +36,7 @@ def _load():
         "trg_set_params": [i, i, ull, i], "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
+        "trg_step_timings": [pd, i],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -117,6 +119,16 @@ def trg_set_state(beta, phi, psi, psi_imp, axes, nsteps, logsum):
         imp = psi_imp.ctypes.data_as(P)
     _check(lib.trg_set_state(float(beta), dims, phi.ctypes.data_as(P), psi.ctypes.data_as(P),
                              imp, ax, int(nsteps), float(logsum)))
+
+
+PHASES = ("resplit", "bond_swap", "triad_isometries", "triads_envs", "squeezers",
+          "contraction", "impurity", "norm")
+
+
+def trg_step_timings():
+    out = (ctypes.c_double * 8)()
+    _check(lib.trg_step_timings(out, 8))
+    return dict(zip(PHASES, list(out)))
 
 
 def trg_finalize():

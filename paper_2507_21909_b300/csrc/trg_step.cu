@@ -40,6 +40,13 @@ struct Ctx {
   int q_swap = 4, q_rho = 4, precision = TRG_PREC_FP64;
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
+  static constexpr int kPhases = 8;
+  cudaEvent_t ev[kPhases + 1] = {};
+  double phase_ms[kPhases] = {};
+  void mark(int i) {
+    if (!ev[i]) TRG_CUDA(cudaEventCreate(&ev[i]));
+    TRG_CUDA(cudaEventRecord(ev[i], stream));
+  }
 
   Tensor alloc(std::vector<int64_t> d) {
     Tensor t;
@@ -328,6 +335,7 @@ static void rotate(Ctx &c, int axis) {
 // ----------------------------------------------------------------------- the step
 static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   cudaStream_t s = c.stream;
+  c.mark(0);
   rotate(c, axis);
   const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], d4 = c.dims[3], r = c.dims[4];
   const int64_t Nf = d1 * d2 * d3 * d4;
@@ -347,6 +355,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   A.dims = {d1, d2, d3, d4, k};
   Dm.dims = {d1, d2, d3, d4, k};
 
+  c.mark(1);
   // (b) bond swap: sum_x B[x J al] C[x I be] ~ X sigma Y  (Appendix A), applied to the
   //     uncompressed M; identical in exact arithmetic to the QR-compressed M'.
   Tensor C = copy(c, A), B = copy(c, Dm);
@@ -404,6 +413,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     if (w > Dg && hs[Dg - 1] > 0) gap_swap = (hs[Dg - 1] - hs[Dg]) / hs[Dg - 1];
   }
 
+  c.mark(2);
   // (c) triad isometries from the canonical-form Grams (eq. HOSVD)
   Tensor Xs = copy(c, X), Ys = copy(c, Y);
   scale_last(c, Xs, sig);
@@ -428,6 +438,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor UA = iso(rhoA, TAG_RHO_A), UX = iso(rhoX, TAG_RHO_X), UY = iso(rhoY, TAG_RHO_Y),
          UD = iso(rhoD, TAG_RHO_D);
 
+  c.mark(3);
   // (d) triads, eqs. E-L
   Tensor E = contract(c, "tbcda,bck->tkda", A, UA);
   Tensor F = contract(c, "abcdg,bck->akdg", X, UX);
@@ -474,6 +485,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     Tensor G2b = contract(c, "QkSl,kble->bQeS", LL, HH2);
     rb[mu] = contract(c, "PbRe,bQeS->PQRS", G1b, G2b);
   }
+  c.mark(4);
   const int64_t dmu[5] = {0, 0, d2, d3, d4};
   std::map<int, Tensor> Msq, Nsq;
   double gap_sq = INFINITY;
@@ -490,9 +502,11 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     Nsq[mu] = N;
   }
 
+  c.mark(5);
   // (f) coarse contraction, eqs. makeMG / makeMH
   Tensor PhiN = contract_upper(c, E, F, I_, J_, Msq[2], Msq[3], Msq[4]);
   Tensor PsiN = contract_lower(c, G, H, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+  c.mark(6);
   Tensor PsiImpN;
   if (c.have_imp) {
     // impurity at slot n+1: B_imp = T_imp^T A; frozen X projector -> Y_imp = M_imp^T X / sigma
@@ -512,6 +526,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     axpby(PsiImpN.p, Pb.p, 0.5, 0.5, PsiImpN.size(), s);
   }
 
+  c.mark(7);
   // normalisation c_n = ||T||_F and ln Z bookkeeping
   const int64_t rn = PhiN.dims[4], Nn = PhiN.size() / rn;
   Tensor Gp = mm(c, view(PhiN.p, {Nn, rn}), view(PhiN.p, {Nn, rn}), true, false);
@@ -530,7 +545,13 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   int flag = 0;
   TRG_CUDA(cudaMemcpyAsync(&hc, c.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   TRG_CUDA(cudaMemcpyAsync(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  c.mark(8);
   TRG_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < Ctx::kPhases; ++i) {
+    float ms = 0.f;
+    TRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
+    c.phase_ms[i] = ms;
+  }
   c.last_logc = std::log(hc);
   c.last_gap = std::min(gap_swap, gap_sq);
   c.arena.reset();
@@ -813,6 +834,14 @@ trg_status trg_finalize(void) {
     if (c.own_stream) cudaStreamDestroy(c.own_stream);
     c.own_stream = nullptr;
     c.stream = nullptr;
+  });
+}
+
+trg_status trg_step_timings(double *ms, int n) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!ms || n < 0) throw Error(TRG_ERR_ARG, "bad timing buffer");
+    for (int i = 0; i < n && i < Ctx::kPhases; ++i) ms[i] = c.phase_ms[i];
   });
 }
 
