@@ -37,6 +37,9 @@ typedef int trg_status;
 #define TRG_PREC_FP64      0   /* every GEMM in FP64 on CUDA cores (parity form)       */
 #define TRG_PREC_BF16X3    1   /* bulk GEMMs as 3-term BF16-split tcgen05, FP32 accum */
 #define TRG_PREC_BF16X6    2   /* bulk GEMMs as 6-term BF16-split tcgen05, FP32 accum */
+#define TRG_PREC_BF16X10   3   /* bulk GEMMs as 10-term BF16-split tcgen05, FP32 accum */
+/* In the mixed forms (1..3) a step runs on the tensor cores only once all four legs and
+ * the bond have reached D; the earlier, smaller steps run in FP64. */
 
 /* Initial tensor of the d-dimensional Ising model, Sec. III (CP form
  * T = sum_a prod_legs W[a, leg], W = [[sqrt(cosh b), sqrt(sinh b)],
@@ -105,6 +108,15 @@ trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
 trg_status trg_set_state(double beta, const int *dims, const double *phi,
                          const double *psi, const double *psi_imp, const int *axes,
                          int nsteps, double logsum);
+
+/* C = alpha op(A) op(B) + beta C for host row-major FP64 buffers (op = transpose when
+ * ta / tb != 0), computed on the device in `precision` (TRG_PREC_*): the FP64 CUDA-core
+ * GEMM or the split-BF16 tcgen05 GEMM that the step uses.  For verification and
+ * benchmarking of the contraction engine.  Errors: TRG_ERR_ARG, TRG_ERR_OOM,
+ * TRG_ERR_CUDA, TRG_ERR_TIMEOUT. */
+trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, long long K,
+                    double alpha, const double *A, long long lda, const double *B,
+                    long long ldb, double beta, double *C, long long ldc);
 
 /* Release every device buffer of the context. */
 trg_status trg_finalize(void);

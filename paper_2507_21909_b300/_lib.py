@@ -7,11 +7,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 _PATH = os.path.join(HERE, "libtrg.so")
 
-TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6 = 0, 1, 2
+TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6, TRG_PREC_BF16X10 = 0, 1, 2, 3
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
-            "trg_step_timings"]
+            "trg_step_timings", "trg_gemm"]
 
 
 class TrgError(RuntimeError):
@@ -37,6 +37,8 @@ def _load():
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
         "trg_step_timings": [pd, i],
+        "trg_gemm": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d, pd,
+                     ctypes.c_longlong, pd, ctypes.c_longlong, d, pd, ctypes.c_longlong],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -129,6 +131,23 @@ def trg_step_timings():
     out = (ctypes.c_double * 8)()
     _check(lib.trg_step_timings(out, 8))
     return dict(zip(PHASES, list(out)))
+
+
+def trg_gemm(A, B, precision=TRG_PREC_FP64, ta=False, tb=False, alpha=1.0, beta=0.0, C=None):
+    """C = alpha op(A) op(B) + beta C on the device (numpy FP64 in and out)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M = A.shape[1] if ta else A.shape[0]
+    K = A.shape[0] if ta else A.shape[1]
+    N = B.shape[0] if tb else B.shape[1]
+    if (B.shape[1] if tb else B.shape[0]) != K:
+        raise ValueError("inner dimensions differ")
+    C = np.zeros((M, N)) if C is None else np.ascontiguousarray(C, dtype=np.float64).copy()
+    P = ctypes.POINTER(ctypes.c_double)
+    _check(lib.trg_gemm(int(precision), int(ta), int(tb), M, N, K, float(alpha),
+                        A.ctypes.data_as(P), A.shape[1], B.ctypes.data_as(P), B.shape[1],
+                        float(beta), C.ctypes.data_as(P), N))
+    return C
 
 
 def trg_finalize():

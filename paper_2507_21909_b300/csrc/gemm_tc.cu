@@ -1,0 +1,433 @@
+// Split-precision GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// C (FP64) = alpha * op(A) op(B) + beta * C, where every FP64 operand is split into
+// `ns` BF16 slices  a = a_0 + a_1 + ... (a_0 = bf16(a), a_1 = bf16(a - a_0), ...)  and the
+// product is the sum of the slice products a_i b_j with i + j < ns (3 products for
+// ns = 2, 6 for ns = 3), accumulated in FP32 in tensor memory.
+//
+// Kernel: one CTA = 128 threads computes a 128 x BN tile.  Warp 0 / lane 0 issues TMA
+// loads (128B-swizzled K-major tiles, 4-stage mbarrier pipeline), warp 1 / lane 0 issues
+// tcgen05.mma (M = 128, N = BN, K = 16) into a TMEM accumulator, then all four warps
+// drain TMEM (tcgen05.ld 32x32b) and write FP64.  Optional split-K writes FP64 partial
+// tiles that a second kernel reduces in a fixed order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "trg_internal.h"
+#include "gemm_tc.h"
+
+namespace trg {
+
+namespace tc {
+
+constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 128;
+constexpr int MAX_PAIRS = 16;
+
+struct Params {
+  int64_t M, N, Kp;           // Kp: padded K (multiple of BK)
+  int64_t batch;
+  int nkb;                    // K blocks per split
+  int ksplit;
+  int npairs;
+  int pi[MAX_PAIRS], pj[MAX_PAIRS];
+  double alpha, beta;
+  double *C;                  // FP64 output (or split-K workspace)
+  int64_t ldc, sC;
+  int to_ws;                  // 1: write raw partial tiles [split][batch][M][N]
+  int *err;
+};
+
+__device__ int g_err_flag;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// bounded wait: gives up after ~2^31 cycles and records the failure
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicExch(&g_err_flag, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row atoms of 1024 bytes
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                           // swizzle: 128B
+  return d;
+}
+
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4)                      // D: F32
+         | (1u << 7)                    // A: BF16
+         | (1u << 10)                   // B: BF16
+         | ((uint32_t)(BN >> 3) << 17)  // N / 8
+         | ((uint32_t)(BM >> 4) << 24); // M / 16
+}
+
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const Params p) {
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * BN, m0 = (int64_t)blockIdx.y * BM;
+  const int64_t z = blockIdx.z;
+  const int64_t b = z % p.batch, split = z / p.batch;
+  const int kb0 = (int)split * p.nkb;
+  const int nkb_total = (int)(p.Kp / BK);
+  const int kb1 = min(kb0 + p.nkb, nkb_total);
+  const int nk = max(kb1 - kb0, 0);
+  const int iters = nk * p.npairs;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u)) break;
+      const int pr = it / nk, kb = kb0 + it % nk;
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_expect_tx(full, STAGE_BYTES);
+      tma_load_4d(sa, &tmA, full, kb * BK, (int)m0, (int)b, p.pi[pr]);
+      tma_load_4d(sb, &tmB, full, kb * BK, (int)n0, (int)b, p.pj[pr]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16<BN>();
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&bars[s]), ph)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t da = sdesc(sa + kk * 32), db = sdesc(sb + kk * 32);
+        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&bars[STAGES + s]))
+          : "memory");
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bars[2 * STAGES]))
+        : "memory");
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> FP64 global
+  const bool have = iters > 0 && mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int64_t row = m0 + warp * 32 + lane;
+  double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
+  const int64_t ldc = p.to_ws ? p.N : p.ldc;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (row < p.M) {
+      double *crow = Cbase + row * ldc;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t col = n0 + c0 + j;
+        if (col < p.N) {
+          const double v = have ? (double)__uint_as_float(r[j]) : 0.0;
+          if (p.to_ws)
+            crow[col] = v;
+          else
+            crow[col] = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * crow[col];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+}
+
+// FP64 -> ns BF16 slices of op(X) laid out [slice][batch][rows][Kp] (K-major), zero
+// padded for k >= K.  op(X)[r][k] = trans ? X[k*ld + r] : X[r*ld + k].  32 x 32 tiles
+// through shared memory keep both the read and the write coalesced.
+__global__ void split_kernel(const double *__restrict__ X, int64_t rows, int64_t K, int64_t ld,
+                             int64_t sX, int trans, int ns, __nv_bfloat16 *__restrict__ out,
+                             int64_t Kp, int64_t batch) {
+  __shared__ double tile[32][33];
+  const int64_t b = blockIdx.z;
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const double *Xb = X + b * sX;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    double v = 0.0;
+    if (trans) {
+      const int64_t k = k0 + i, r = r0 + tx;  // read along r (contiguous)
+      if (k < K && r < rows) v = Xb[k * ld + r];
+      tile[tx][i] = v;
+    } else {
+      const int64_t r = r0 + i, k = k0 + tx;  // read along k (contiguous)
+      if (k < K && r < rows) v = Xb[r * ld + k];
+      tile[i][tx] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, k = k0 + tx;
+    if (r >= rows || k >= Kp) continue;
+    double rem = tile[i][tx];
+    for (int s = 0; s < ns; ++s) {
+      const __nv_bfloat16 h = __double2bfloat16(rem);
+      rem -= (double)__bfloat162float(h);
+      out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = h;
+    }
+  }
+}
+
+__global__ void ws_reduce_kernel(const double *__restrict__ W, int ksplit, int64_t batch,
+                                 int64_t M, int64_t N, double alpha, double beta,
+                                 double *__restrict__ C, int64_t ldc, int64_t sC) {
+  const int64_t total = batch * M * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < ksplit; ++s) acc += W[s * total + i];
+    const int64_t bb = i / (M * N), mn = i % (M * N), m = mn / N, n = mn % N;
+    double *c = C + bb * sC + m * ldc + n;
+    *c = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *c;
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  if (!fn) throw Error(TRG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+// 4-D map over slices laid out [ns][batch][rows][Kp] (bf16), box (BK, box_rows, 1, 1)
+static CUtensorMap make_map(const void *base, int64_t Kp, int64_t rows, int64_t batch, int ns,
+                            int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)ns};
+  cuuint64_t strides[3] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2),
+                           (cuuint64_t)(batch * rows * Kp * 2)};
+  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base),
+                            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(TRG_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+template <int BN>
+static size_t smem_bytes() {
+  return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+}
+
+template <int BN>
+static void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, dim3 grid,
+                   cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    TRG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<BN>()));
+    attr = true;
+  }
+  tc_gemm_kernel<BN><<<grid, THREADS, smem_bytes<BN>(), s>>>(ma, mb, p);
+  TRG_LAUNCH_CHECK();
+}
+
+}  // namespace tc
+
+static int64_t g_tc_launches = 0;
+int64_t tc_launch_count() { return g_tc_launches; }
+
+int tc_error_flag(bool reset) {
+  int v = 0;
+  cudaMemcpyFromSymbol(&v, tc::g_err_flag, sizeof(int));
+  if (reset) {
+    int z = 0;
+    cudaMemcpyToSymbol(tc::g_err_flag, &z, sizeof(int));
+  }
+  return v;
+}
+
+void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+             int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
+             double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
+             cudaStream_t s) {
+  using namespace tc;
+  if (M == 0 || N == 0 || batch == 0) return;
+  if (ns < 1 || ns > 4) throw Error(TRG_ERR_ARG, "gemm_tc: 1 <= slices <= 4");
+  if (M > INT32_MAX || N > INT32_MAX || batch > 65535) throw Error(TRG_ERR_ARG, "gemm_tc: too large");
+  const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
+  // slice buffers
+  const size_t abytes = (size_t)ns * batch * M * Kp * 2, bbytes = (size_t)ns * batch * N * Kp * 2;
+  __nv_bfloat16 *As = (__nv_bfloat16 *)scr.alloc(abytes);
+  __nv_bfloat16 *Bs = (__nv_bfloat16 *)scr.alloc(bbytes);
+  {
+    dim3 blk(32, 8);
+    dim3 ga((unsigned)((Kp + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)batch);
+    split_kernel<<<ga, blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, As, Kp, batch);
+    TRG_LAUNCH_CHECK();
+    // op(B)[k][n] -> rows n, K-major: transpose unless B is stored [n][k] (tb)
+    dim3 gb((unsigned)((Kp + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)batch);
+    split_kernel<<<gb, blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, Bs, Kp, batch);
+    TRG_LAUNCH_CHECK();
+  }
+  Params p{};
+  p.M = M;
+  p.N = N;
+  p.Kp = Kp;
+  p.batch = batch;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.npairs = 0;
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < ns; ++j)
+      if (i + j < ns) {
+        p.pi[p.npairs] = i;
+        p.pj[p.npairs] = j;
+        ++p.npairs;
+      }
+  const int BNsel = N <= 128 ? 128 : 256;
+  const int64_t gx = (N + BNsel - 1) / BNsel, gy = (M + BM - 1) / BM;
+  if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_tc: M too large");
+  const int nkb_total = (int)(Kp / BK);
+  int ksplit = 1;
+  const int64_t tiles = gx * gy * batch;
+  if (tiles < 148 && nkb_total >= 8) {
+    ksplit = (int)std::min<int64_t>(std::min<int64_t>((2 * 148 + tiles - 1) / tiles, nkb_total / 4),
+                                    65535 / batch);
+    ksplit = std::max(ksplit, 1);
+  }
+  p.nkb = (nkb_total + ksplit - 1) / ksplit;
+  ksplit = (nkb_total + p.nkb - 1) / p.nkb;
+  p.ksplit = ksplit;
+  if (ksplit > 1) {
+    p.C = (double *)scr.alloc((size_t)ksplit * batch * M * N * sizeof(double));
+    p.to_ws = 1;
+    p.ldc = N;
+    p.sC = M * N;
+  } else {
+    p.C = C;
+    p.to_ws = 0;
+    p.ldc = ldc;
+    p.sC = sC;
+  }
+  CUtensorMap ma = make_map(As, Kp, M, batch, ns, BM);
+  CUtensorMap mb = make_map(Bs, Kp, N, batch, ns, BNsel);
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
+  if (BNsel == 128)
+    launch<128>(ma, mb, p, grid, s);
+  else
+    launch<256>(ma, mb, p, grid, s);
+  ++g_tc_launches;
+  if (ksplit > 1) {
+    const int64_t total = batch * M * N;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+    ws_reduce_kernel<<<blocks, 256, 0, s>>>(p.C, ksplit, batch, M, N, alpha, beta, C, ldc, sC);
+    TRG_LAUNCH_CHECK();
+  }
+}
+
+}  // namespace trg

@@ -12,6 +12,7 @@
 #include <memory>
 #include <utility>
 
+#include "gemm_tc.h"
 #include "trg_internal.h"
 
 namespace trg {
@@ -38,6 +39,7 @@ struct Ctx {
   double *dscal = nullptr;  // [0] logsum [1] c [2] trace [3] trace2; [8..] dot scratch
   int *dflag = nullptr;
   int q_swap = 4, q_rho = 4, precision = TRG_PREC_FP64;
+  bool mixed_now = false;      // this step runs its bulk GEMMs on the tensor cores
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
   static constexpr int kPhases = 8;
@@ -76,6 +78,33 @@ static int64_t prod(const std::vector<int64_t> &d, size_t a = 0, size_t b = SIZE
   return n;
 }
 
+// ------------------------------------------------------------------ GEMM dispatch
+struct ArenaScratch : TcScratch {
+  Arena &a;
+  explicit ArenaScratch(Arena &ar) : a(ar) {}
+  void *alloc(size_t bytes) override { return a.alloc(bytes); }
+};
+
+static int slices_of(int precision) {
+  return precision == TRG_PREC_BF16X3 ? 2 : precision == TRG_PREC_BF16X6 ? 3 : 4;
+}
+
+// every GEMM of the step goes through here: bulk products run as split-BF16 tcgen05
+// GEMMs in the mixed forms, everything else (and every GEMM of the FP64 form) on the
+// FP64 CUDA cores
+static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                 const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
+                 int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
+  const double work = (double)M * N * K * batch;
+  if (c.mixed_now && work >= (double)(1 << 24) && M >= 64 && N >= 16 && K >= 64) {
+    ArenaScratch scr(c.arena);
+    gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+            slices_of(c.precision), scr, c.stream);
+  } else {
+    gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream);
+  }
+}
+
 // ------------------------------------------------------------------ tensor helpers
 static Tensor copy(Ctx &c, const Tensor &a) {
   Tensor t = c.alloc(a.dims);
@@ -98,8 +127,7 @@ static Tensor mm(Ctx &c, const Tensor &A, const Tensor &B, bool ta, bool tb) {
   int64_t Kb = tb ? B.dims[1] : B.dims[0], N = tb ? B.dims[0] : B.dims[1];
   if (K != Kb) throw Error(TRG_ERR_ARG, "mm: inner dimensions differ");
   Tensor C = c.alloc({M, N});
-  gemm_f64(ta, tb, M, N, K, 1.0, A.p, A.dims[1], 0, B.p, B.dims[1], 0, 0.0, C.p, N, 0, 1,
-           c.stream);
+  gemm(c, ta, tb, M, N, K, 1.0, A.p, A.dims[1], 0, B.p, B.dims[1], 0, 0.0, C.p, N, 0, 1);
   return C;
 }
 
@@ -107,8 +135,7 @@ static Tensor mm(Ctx &c, const Tensor &A, const Tensor &B, bool ta, bool tb) {
 static Tensor mm_cols(Ctx &c, const Tensor &Q, const Tensor &U, int64_t ncols) {
   int64_t M = Q.dims[0], K = Q.dims[1];
   Tensor C = c.alloc({M, ncols});
-  gemm_f64(false, false, M, ncols, K, 1.0, Q.p, K, 0, U.p, U.dims[1], 0, 0.0, C.p, ncols, 0, 1,
-           c.stream);
+  gemm(c, false, false, M, ncols, K, 1.0, Q.p, K, 0, U.p, U.dims[1], 0, 0.0, C.p, ncols, 0, 1);
   return C;
 }
 
@@ -166,8 +193,8 @@ static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const T
   std::vector<int64_t> ndims;
   for (char ch : nat) ndims.push_back(dim[ch]);
   Tensor C = c.alloc(ndims);
-  gemm_f64(ta, tb, M, N, K, 1.0, pa, ta ? M : K, M * K, pb, tb ? K : N, K * N, 0.0, C.p, N,
-           M * N, nb, c.stream);
+  gemm(c, ta, tb, M, N, K, 1.0, pa, ta ? M : K, M * K, pb, tb ? K : N, K * N, 0.0, C.p, N,
+       M * N, nb);
   if (so == nat) return C;
   std::vector<int> perm;
   for (char ch : so) perm.push_back((int)nat.find(ch));
@@ -340,6 +367,9 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], d4 = c.dims[3], r = c.dims[4];
   const int64_t Nf = d1 * d2 * d3 * d4;
   const int n = c.nsteps;
+  // mixed forms: tensor cores only once every leg has reached D (earlier steps are small
+  // and carry the largest weights 2^-n of the free energy)
+  c.mixed_now = c.precision != TRG_PREC_FP64 && d1 >= D && d2 >= D && d3 >= D && d4 >= D && r >= D;
   auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
 
   // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
@@ -371,22 +401,22 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor Bp = permuted(c, view(B.p, {x, J, k}), {1, 0, 2});   // (J, x, al)
   auto applyM = [&](const Tensor &V) {                          // V: (J be) x w
     Tensor Z = c.alloc({x, k, k, w});                           // (x, al, be, m)
-    gemm_f64(true, false, k, k * w, J, 1.0, B.p, k, J * k, V.p, k * w, 0, 0.0, Z.p, k * w,
-             k * k * w, x, s);
+    gemm(c, true, false, k, k * w, J, 1.0, B.p, k, J * k, V.p, k * w, 0, 0.0, Z.p, k * w,
+         k * k * w, x);
     Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x, be, al, m)
     Tensor Y = c.alloc({I * k, w});
-    gemm_f64(false, false, I, k * w, x * k, 1.0, Cp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Y.p,
-             k * w, 0, 1, s);
+    gemm(c, false, false, I, k * w, x * k, 1.0, Cp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Y.p,
+         k * w, 0, 1);
     return Y;                                                    // (I al) x w
   };
   auto applyMt = [&](const Tensor &U) {                         // U: (I al) x w
     Tensor Z = c.alloc({x, k, k, w});                           // (x, be, al, m)
-    gemm_f64(true, false, k, k * w, I, 1.0, C.p, k, I * k, U.p, k * w, 0, 0.0, Z.p, k * w,
-             k * k * w, x, s);
+    gemm(c, true, false, k, k * w, I, 1.0, C.p, k, I * k, U.p, k * w, 0, 0.0, Z.p, k * w,
+         k * k * w, x);
     Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x, al, be, m)
     Tensor Yt = c.alloc({J * k, w});
-    gemm_f64(false, false, J, k * w, x * k, 1.0, Bp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Yt.p,
-             k * w, 0, 1, s);
+    gemm(c, false, false, J, k * w, x * k, 1.0, Bp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Yt.p,
+         k * w, 0, 1);
     return Yt;                                                   // (J be) x w
   };
   Tensor V = Om, Q, Yt;
@@ -556,6 +586,8 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   c.last_gap = std::min(gap_swap, gap_sq);
   c.arena.reset();
   if (flag) throw Error(flag, "non-finite norm in the coarse-graining step");
+  if (c.mixed_now && tc_error_flag(true))
+    throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
 }
 
 // -------------------------------------------------------------------- init helpers
@@ -699,8 +731,6 @@ trg_status trg_step(int axis, int D, int sketch_oversample) {
     if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
     if (axis < 0 || axis > 3 || D < 1 || sketch_oversample < 0)
       throw Error(TRG_ERR_ARG, "need 0 <= axis < 4, D >= 1, p >= 0");
-    if (c.precision != TRG_PREC_FP64)
-      throw Error(TRG_ERR_ARG, "this build runs the FP64 form only");
     try {
       step_impl(c, axis, D, sketch_oversample);
     } catch (...) {
@@ -743,8 +773,8 @@ trg_status trg_magnetisation_impurity(double *m) {
 
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision) {
   return guarded([&] {
-    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > 2)
-      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..2");
+    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > 3)
+      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..3");
     Ctx &c = ctx();
     c.q_swap = q_swap;
     c.q_rho = q_rho;
@@ -842,6 +872,33 @@ trg_status trg_step_timings(double *ms, int n) {
     Ctx &c = ctx();
     if (!ms || n < 0) throw Error(TRG_ERR_ARG, "bad timing buffer");
     for (int i = 0; i < n && i < Ctx::kPhases; ++i) ms[i] = c.phase_ms[i];
+  });
+}
+
+trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, long long K,
+                    double alpha, const double *A, long long lda, const double *B,
+                    long long ldb, double beta, double *C, long long ldc) {
+  return guarded([&] {
+    if (!A || !B || !C || M < 0 || N < 0 || K < 0 || precision < 0 || precision > 3)
+      throw Error(TRG_ERR_ARG, "bad gemm arguments");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    const int64_t rA = ta ? K : M, rB = tb ? N : K;
+    Tensor dA = c.alloc({rA, lda}), dB = c.alloc({rB, ldb}), dC = c.alloc({M, ldc});
+    TRG_CUDA(cudaMemcpyAsync(dA.p, A, rA * lda * 8, cudaMemcpyHostToDevice, c.stream));
+    TRG_CUDA(cudaMemcpyAsync(dB.p, B, rB * ldb * 8, cudaMemcpyHostToDevice, c.stream));
+    TRG_CUDA(cudaMemcpyAsync(dC.p, C, M * ldc * 8, cudaMemcpyHostToDevice, c.stream));
+    if (precision == TRG_PREC_FP64) {
+      gemm_f64(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1, c.stream);
+    } else {
+      ArenaScratch scr(c.arena);
+      gemm_tc(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
+              slices_of(precision), scr, c.stream);
+    }
+    TRG_CUDA(cudaMemcpyAsync(C, dC.p, M * ldc * 8, cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    c.arena.reset();
+    if (tc_error_flag(true)) throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
   });
 }
 
