@@ -1,0 +1,49 @@
+"""The contraction engine on the GPU against a plain NumPy FP64 product.
+
+Error measure: max |C - A B| / max (|A| |B|) (the elementwise bound of a dot product).
+FP64 CUDA-core GEMM: 1e-14.  Split-BF16 tcgen05 GEMM with FP32 accumulation:
+2 slices (3 products) < 1e-4, 3 slices (6 products) < 2e-6, 4 slices (10) < 2e-6;
+the 3/4-slice bound is the FP32 accumulation, not the operand split.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(128, 256, 64, False, False), (300, 200, 1000, False, False),
+          (64, 48, 5000, True, False), (1000, 130, 70, False, True),
+          (257, 129, 333, True, True), (2048, 512, 4096, False, False)]
+BOUND = {0: 1e-14, 1: 1e-4, 2: 2e-6, 3: 2e-6}
+
+
+@pytest.fixture(scope="module")
+def trg(require_gpu):
+    import paper_2507_21909_b300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("M,N,K,ta,tb", SHAPES)
+def test_gemm_against_numpy(trg, prec, M, N, K, ta, tb):
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    opA = A.T if ta else A
+    opB = B.T if tb else B
+    C0 = rng.standard_normal((M, N))
+    ref = 0.5 * (opA @ opB) - 2.0 * C0
+    got = trg.trg_gemm(A, B, precision=prec, ta=ta, tb=tb, alpha=0.5, beta=-2.0, C=C0)
+    scale = 0.5 * (np.abs(opA) @ np.abs(opB)).max() + 2.0 * np.abs(C0).max()
+    err = np.abs(got - ref).max() / scale
+    assert err < BOUND[prec], err
+
+
+def test_gemm_scaled_rows(trg):
+    """Rows spanning 12 orders of magnitude (per-element BF16 exponents handle them)."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((256, 512)) * np.logspace(-6, 6, 256)[:, None]
+    B = rng.standard_normal((512, 384))
+    got = trg.trg_gemm(A, B, precision=2)
+    ref = A @ B
+    rel = np.abs(got - ref).max(axis=1) / (np.abs(A) @ np.abs(B)).max(axis=1)
+    assert rel.max() < 2e-6
