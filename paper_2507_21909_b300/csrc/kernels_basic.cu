@@ -339,7 +339,9 @@ void norm_update(const double *tr, double *c_out, double *logsum, double weight,
 // ------------------------------------------------------------------ arena
 void *Arena::alloc(size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
-  for (auto &c : chunks_) {
+  // only the newest chunk is used, so that mark()/release() form a stack
+  if (!chunks_.empty()) {
+    auto &c = chunks_.back();
     if (c.cap - c.used >= bytes) {
       void *p = c.p + c.used;
       c.used += bytes;
@@ -380,6 +382,12 @@ void Arena::reset() {
   }
   for (auto &c : chunks_) c.used = 0;
   cur_ = 0;
+}
+
+void Arena::release(const Mark &m) {
+  for (size_t i = m.nchunks; i < chunks_.size(); ++i) chunks_[i].used = 0;
+  if (m.nchunks > 0 && m.nchunks <= chunks_.size()) chunks_[m.nchunks - 1].used = m.used_last;
+  cur_ = m.cur;
 }
 
 void Arena::release() {

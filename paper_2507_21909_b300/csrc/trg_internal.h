@@ -30,7 +30,13 @@ struct Error : std::runtime_error {
 // at once by reset(); persistent state buffers are separate cudaMalloc'd buffers.
 class Arena {
  public:
+  struct Mark { size_t nchunks, used_last, cur; };
   void *alloc(size_t bytes);
+  // stack discipline: everything allocated after mark() is released by release(mark)
+  Mark mark() const {
+    return {chunks_.size(), chunks_.empty() ? 0 : chunks_.back().used, cur_};
+  }
+  void release(const Mark &m);
   void reset();           // callers must have synchronised the stream first
   void release();         // frees all chunks
   size_t high_water() const { return high_; }

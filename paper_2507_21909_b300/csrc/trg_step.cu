@@ -213,15 +213,22 @@ static void scale_last(Ctx &c, Tensor &t, const double *v, int mode = 0,
 // Householder QR; directions at the rounding level come out as zero columns.
 static Tensor orth_sc(Ctx &c, const Tensor &Y) {
   int64_t w = Y.dims[1];
+  Tensor out = c.alloc(Y.dims);
+  Arena::Mark mk = c.arena.mark();
   Tensor Q = Y;
   for (int pass = 0; pass < 3; ++pass) {
     Tensor G = mm(c, Q, Q, true, false);
     Tensor R = c.alloc({w, w}), Ri = c.alloc({w, w});
     chol_rinv(G.p, R.p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
               pass == 0 ? kShiftRel : 0.0, c.stream);
-    Q = mm(c, Q, Ri, false, false);
+    if (pass == 2) {
+      gemm(c, false, false, Q.dims[0], w, w, 1.0, Q.p, w, 0, Ri.p, w, 0, 0.0, out.p, w, 0, 1);
+    } else {
+      Q = mm(c, Q, Ri, false, false);
+    }
   }
-  return Q;
+  c.arena.release(mk);
+  return out;
 }
 
 static std::pair<Tensor, Tensor> orth_qr(Ctx &c, const Tensor &Y) {
@@ -399,31 +406,44 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   khatri_rao(g2.p, g1.p, Om.p, J, k, w, s);
   Tensor Cp = permuted(c, view(C.p, {x, I, k}), {1, 0, 2});   // (I, x, be)
   Tensor Bp = permuted(c, view(B.p, {x, J, k}), {1, 0, 2});   // (J, x, al)
-  auto applyM = [&](const Tensor &V) {                          // V: (J be) x w
-    Tensor Z = c.alloc({x, k, k, w});                           // (x, al, be, m)
-    gemm(c, true, false, k, k * w, J, 1.0, B.p, k, J * k, V.p, k * w, 0, 0.0, Z.p, k * w,
-         k * k * w, x);
-    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x, be, al, m)
-    Tensor Y = c.alloc({I * k, w});
+  Tensor Cq = permuted(c, view(C.p, {x, I, k}), {0, 2, 1});   // (x, be, I)
+  Tensor Bq = permuted(c, view(B.p, {x, J, k}), {0, 2, 1});   // (x, al, J)
+  // Y[(I al), m] = sum_{x be} C[x I be] (sum_J B[x J al] V[(J be), m])
+  auto applyM = [&](const Tensor &V, Tensor &Y) {               // V: (J be) x w
+    Arena::Mark mk = c.arena.mark();
+    Tensor Z = c.alloc({x, k, k, w});                           // (x al, be m)
+    gemm(c, false, false, x * k, k * w, J, 1.0, Bq.p, J, 0, V.p, k * w, 0, 0.0, Z.p, k * w, 0, 1);
+    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x be, al m)
     gemm(c, false, false, I, k * w, x * k, 1.0, Cp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Y.p,
          k * w, 0, 1);
-    return Y;                                                    // (I al) x w
+    c.arena.release(mk);
   };
-  auto applyMt = [&](const Tensor &U) {                         // U: (I al) x w
-    Tensor Z = c.alloc({x, k, k, w});                           // (x, be, al, m)
-    gemm(c, true, false, k, k * w, I, 1.0, C.p, k, I * k, U.p, k * w, 0, 0.0, Z.p, k * w,
-         k * k * w, x);
-    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x, al, be, m)
-    Tensor Yt = c.alloc({J * k, w});
+  // Yt[(J be), m] = sum_{x al} B[x J al] (sum_I C[x I be] U[(I al), m])
+  auto applyMt = [&](const Tensor &U, Tensor &Yt) {             // U: (I al) x w
+    Arena::Mark mk = c.arena.mark();
+    Tensor Z = c.alloc({x, k, k, w});                           // (x be, al m)
+    gemm(c, false, false, x * k, k * w, I, 1.0, Cq.p, I, 0, U.p, k * w, 0, 0.0, Z.p, k * w, 0, 1);
+    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x al, be m)
     gemm(c, false, false, J, k * w, x * k, 1.0, Bp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Yt.p,
          k * w, 0, 1);
-    return Yt;                                                   // (J be) x w
+    c.arena.release(mk);
   };
-  Tensor V = Om, Q, Yt;
+  Tensor Q = c.alloc({I * k, w}), Yt = c.alloc({J * k, w}), V = c.alloc({J * k, w});
+  TRG_CUDA(cudaMemcpyAsync(V.p, Om.p, V.size() * 8, cudaMemcpyDeviceToDevice, s));
   for (int rnd = 0; rnd < c.q_swap; ++rnd) {
-    Q = orth_sc(c, applyM(V));
-    Yt = applyMt(Q);
-    if (rnd + 1 < c.q_swap) V = orth_sc(c, Yt);
+    Arena::Mark mk = c.arena.mark();
+    Tensor Y = c.alloc({I * k, w});
+    applyM(V, Y);
+    Tensor Qn = orth_sc(c, Y);
+    TRG_CUDA(cudaMemcpyAsync(Q.p, Qn.p, Q.size() * 8, cudaMemcpyDeviceToDevice, s));
+    c.arena.release(mk);
+    applyMt(Q, Yt);
+    if (rnd + 1 < c.q_swap) {
+      Arena::Mark mk2 = c.arena.mark();
+      Tensor Vn = orth_sc(c, Yt);
+      TRG_CUDA(cudaMemcpyAsync(V.p, Vn.p, V.size() * 8, cudaMemcpyDeviceToDevice, s));
+      c.arena.release(mk2);
+    }
   }
   auto [Qt, Rt] = orth_qr(c, Yt);              // M^T Q = Qt Rt  ->  Q^T M = Rt^T Qt^T
   Svd cs = svd_small(c, transpose2(c, Rt));
