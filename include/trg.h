@@ -94,6 +94,13 @@ trg_status trg_diag(double *log_c, double *min_gap, int *nsteps);
  * [7] normalisation and state update.  Writes min(n, 8) values. */
 trg_status trg_step_timings(double *ms, int n);
 
+/* Counters since the last reset: device time (ms, CUDA events on the launching stream)
+ * and tensor-pipe flop of the split-BF16 tcgen05 GEMM kernel launches inside trg_step
+ * (each slice product counted as a full BF16 GEMM), their number, and the number of all
+ * kernel launches of the library.  reset != 0 zeroes them after reading. */
+trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launches,
+                            long long *all_launches, int reset);
+
 /* Copy a state factor to the host.  which: 0 = Phi, 1 = Psi, 2 = Psi_imp.
  * dims_out[0..4] receives (d1, d2, d3, d4, r); host may be NULL (query only), else it
  * must hold `capacity` doubles >= d1 d2 d3 d4 r.  axes_out[0..3] (may be NULL) gets

@@ -11,7 +11,7 @@ TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6, TRG_PREC_BF16X10 = 0, 1, 2, 3
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
-            "trg_step_timings", "trg_gemm"]
+            "trg_step_timings", "trg_gemm", "trg_kernel_stats"]
 
 
 class TrgError(RuntimeError):
@@ -37,6 +37,8 @@ def _load():
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
         "trg_step_timings": [pd, i],
+        "trg_kernel_stats": [pd, pd, ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong), i],
         "trg_gemm": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d, pd,
                      ctypes.c_longlong, pd, ctypes.c_longlong, d, pd, ctypes.c_longlong],
     }
@@ -148,6 +150,15 @@ def trg_gemm(A, B, precision=TRG_PREC_FP64, ta=False, tb=False, alpha=1.0, beta=
                         A.ctypes.data_as(P), A.shape[1], B.ctypes.data_as(P), B.shape[1],
                         float(beta), C.ctypes.data_as(P), N))
     return C
+
+
+def trg_kernel_stats(reset=False):
+    ms, fl = ctypes.c_double(), ctypes.c_double()
+    n, alln = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib.trg_kernel_stats(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n),
+                                ctypes.byref(alln), int(reset)))
+    return {"tc_ms": ms.value, "tc_flop": fl.value, "tc_launches": n.value,
+            "launches": alln.value}
 
 
 def trg_finalize():

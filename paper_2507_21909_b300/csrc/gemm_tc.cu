@@ -354,7 +354,7 @@ int tc_error_flag(bool reset) {
 void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
              int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
              double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
-             cudaStream_t s) {
+             cudaStream_t s, TcTiming *timing) {
   using namespace tc;
   if (M == 0 || N == 0 || batch == 0) return;
   if (ns < 1 || ns > 4) throw Error(TRG_ERR_ARG, "gemm_tc: 1 <= slices <= 4");
@@ -417,11 +417,14 @@ void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   CUtensorMap ma = make_map(As, Kp, M, batch, ns, BM);
   CUtensorMap mb = make_map(Bs, Kp, N, batch, ns, BNsel);
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
+  if (timing) timing->before(s);
   if (BNsel == 128)
     launch<128>(ma, mb, p, grid, s);
   else
     launch<256>(ma, mb, p, grid, s);
   ++g_tc_launches;
+  // tensor-pipe work of this launch: every slice product is a full M x N x K BF16 GEMM
+  if (timing) timing->after(s, 2.0 * (double)M * N * K * batch * p.npairs);
   if (ksplit > 1) {
     const int64_t total = batch * M * N;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);

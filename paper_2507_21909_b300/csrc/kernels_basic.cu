@@ -3,6 +3,8 @@
 
 namespace trg {
 
+int64_t g_kernel_launches = 0;
+
 // ------------------------------------------------------------------ permutation
 constexpr int kMaxDims = 10;
 struct PermArgs {

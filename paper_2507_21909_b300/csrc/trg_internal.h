@@ -23,7 +23,13 @@ struct Error : std::runtime_error {
     if (e_ != cudaSuccess)                                                             \
       throw ::trg::Error(TRG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-#define TRG_LAUNCH_CHECK() TRG_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this check, which also counts it
+extern int64_t g_kernel_launches;
+#define TRG_LAUNCH_CHECK()        \
+  do {                            \
+    ++::trg::g_kernel_launches;   \
+    TRG_CUDA(cudaGetLastError()); \
+  } while (0)
 
 // ------------------------------------------------------------------ device arena
 // Bump allocator over a few large cudaMalloc chunks.  Scratch of one step is released

@@ -50,6 +50,41 @@ struct Ctx {
     TRG_CUDA(cudaEventRecord(ev[i], stream));
   }
 
+  // CUDA-event timing of the tensor-core kernel launches inside a step
+  struct Timing : TcTiming {
+    std::vector<cudaEvent_t> pool;
+    std::vector<double> flop;
+    size_t used = 0;
+    void before(cudaStream_t s) override {
+      if (pool.size() < 2 * used + 2) {
+        for (int i = 0; i < 2; ++i) {
+          cudaEvent_t e;
+          TRG_CUDA(cudaEventCreate(&e));
+          pool.push_back(e);
+        }
+      }
+      TRG_CUDA(cudaEventRecord(pool[2 * used], s));
+    }
+    void after(cudaStream_t s, double f) override {
+      TRG_CUDA(cudaEventRecord(pool[2 * used + 1], s));
+      if (flop.size() <= used) flop.resize(used + 1);
+      flop[used] = f;
+      ++used;
+    }
+  } timing;
+  double tc_ms = 0.0, tc_flop = 0.0;
+  int64_t tc_launches = 0;
+  void collect_tc() {  // after a stream synchronise
+    for (size_t i = 0; i < timing.used; ++i) {
+      float ms = 0.f;
+      TRG_CUDA(cudaEventElapsedTime(&ms, timing.pool[2 * i], timing.pool[2 * i + 1]));
+      tc_ms += ms;
+      tc_flop += timing.flop[i];
+      ++tc_launches;
+    }
+    timing.used = 0;
+  }
+
   Tensor alloc(std::vector<int64_t> d) {
     Tensor t;
     t.dims = std::move(d);
@@ -97,9 +132,11 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && work >= (double)(1 << 24) && M >= 64 && N >= 16 && K >= 64) {
+    Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-            slices_of(c.precision), scr, c.stream);
+            slices_of(c.precision), scr, c.stream, &c.timing);
+    c.arena.release(mk);
   } else {
     gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream);
   }
@@ -179,6 +216,10 @@ static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const T
     for (char ch : want) perm.push_back((int)s.find(ch));
     return permuted(c, T, perm);
   };
+  std::vector<int64_t> odims;
+  for (char ch : so) odims.push_back(dim[ch]);
+  Tensor out = c.alloc(odims);
+  Arena::Mark mk = c.arena.mark();
   bool ta = false, tb = false;
   const double *pa, *pb;
   Tensor tA, tB;
@@ -192,13 +233,16 @@ static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const T
   std::string nat = bt + Mi + Ni;
   std::vector<int64_t> ndims;
   for (char ch : nat) ndims.push_back(dim[ch]);
-  Tensor C = c.alloc(ndims);
+  Tensor C = (so == nat) ? out : c.alloc(ndims);
   gemm(c, ta, tb, M, N, K, 1.0, pa, ta ? M : K, M * K, pb, tb ? K : N, K * N, 0.0, C.p, N,
        M * N, nb);
-  if (so == nat) return C;
-  std::vector<int> perm;
-  for (char ch : so) perm.push_back((int)nat.find(ch));
-  return permuted(c, C, perm);
+  if (so != nat) {
+    std::vector<int> perm;
+    for (char ch : so) perm.push_back((int)nat.find(ch));
+    permute(C.p, out.p, C.dims, perm, c.stream);
+  }
+  c.arena.release(mk);
+  return out;
 }
 
 static void scale_last(Ctx &c, Tensor &t, const double *v, int mode = 0,
@@ -314,23 +358,35 @@ static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor
 static Tensor contract_upper(Ctx &c, const Tensor &E, const Tensor &F, const Tensor &I_,
                              const Tensor &J_, const Tensor &M2, const Tensor &M3,
                              const Tensor &M4) {
+  const int64_t kt = E.dims[0], kr = F.dims[3];
+  Tensor out = c.alloc({kt, M2.dims[2], M3.dims[2], M4.dims[2], kr});
+  Arena::Mark mk = c.arena.mark();
   Tensor IM2 = contract(c, "bck,bBm->ckBm", I_, M2);
   Tensor IM2J = contract(c, "ckBm,BCl->ckmCl", IM2, J_);
   Tensor Theta = contract(c, "ckmCl,cCn->klmn", IM2J, M3);       // (kA kX k2 k3)
   Tensor EM = contract(c, "tkda,dDm->tkamD", E, M4);             // (t kA al k4 q4)
   Tensor Phi1 = contract(c, "tkamD,alDg->tkmlg", EM, F);         // (t kA k4 kX g)
-  return contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta);          // (t k2 k3 k4 g)
+  Tensor r = contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta);      // (t k2 k3 k4 g)
+  TRG_CUDA(cudaMemcpyAsync(out.p, r.p, r.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  c.arena.release(mk);
+  return out;
 }
 
 static Tensor contract_lower(Ctx &c, const Tensor &G, const Tensor &H, const Tensor &K_,
                              const Tensor &L_, const Tensor &N2, const Tensor &N3,
                              const Tensor &N4) {
+  const int64_t kt = H.dims[0], kr = G.dims[3];
+  Tensor out = c.alloc({kt, N2.dims[2], N3.dims[2], N4.dims[2], kr});
+  Arena::Mark mk = c.arena.mark();
   Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);
   Tensor KN2L = contract(c, "ckBm,BCl->ckmCl", KN2, L_);
   Tensor Theta = contract(c, "ckmCl,cCn->klmn", KN2L, N3);       // (kY kD k2 k3)
   Tensor HN = contract(c, "wkdb,Ddm->wkbmD", H, N4);             // (w kD be k4 P4)
   Tensor Psi1 = contract(c, "wkbmD,bjDg->wkmjg", HN, G);         // (w kD k4 kY g)
-  return contract(c, "wkmjg,jkKL->wKLmg", Psi1, Theta);          // (w k2 k3 k4 g)
+  Tensor r = contract(c, "wkmjg,jkKL->wKLmg", Psi1, Theta);      // (w k2 k3 k4 g)
+  TRG_CUDA(cudaMemcpyAsync(out.p, r.p, r.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  c.arena.release(mk);
+  return out;
 }
 
 static void replace_state(double *&dst, const Tensor &src, cudaStream_t s) {
@@ -597,6 +653,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   TRG_CUDA(cudaMemcpyAsync(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   c.mark(8);
   TRG_CUDA(cudaStreamSynchronize(s));
+  c.collect_tc();
   for (int i = 0; i < Ctx::kPhases; ++i) {
     float ms = 0.f;
     TRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
@@ -919,6 +976,22 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
     TRG_CUDA(cudaStreamSynchronize(c.stream));
     c.arena.reset();
     if (tc_error_flag(true)) throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+  });
+}
+
+trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launches,
+                            long long *all_launches, int reset) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (tc_ms) *tc_ms = c.tc_ms;
+    if (tc_flop) *tc_flop = c.tc_flop;
+    if (tc_launches) *tc_launches = c.tc_launches;
+    if (all_launches) *all_launches = g_kernel_launches;
+    if (reset) {
+      c.tc_ms = c.tc_flop = 0.0;
+      c.tc_launches = 0;
+      g_kernel_launches = 0;
+    }
   });
 }
 
