@@ -1,0 +1,283 @@
+#!/usr/bin/env python3
+"""Benchmark: triad-ATRG RG steps/s at D=48 on the 4D Ising model, one B300.
+
+A "step" is one full coarse-graining step of the triad-ATRG method (re-split, bond
+swap, triad isometries, triads, squeezers, coarse contraction, impurity, normalisation)
+on a steady-state D=48 tensor (all legs and the bond at D, p = 2D).  The tensor is grown
+from the Boltzmann-weight initial tensor by the method itself (untimed), then W warm-up
+and K timed steps continue the RG flow.  Inputs (D^5 factors, 2 GB each in FP64) are
+far larger than the 126 MB L2, so no flush is needed between steps.
+
+Default: the mixed form (bulk GEMMs as 6-term split-BF16 tcgen05 products).  Prints one
+JSON line.  Under torchrun every rank runs an independent replica (the method does not
+shard; "replicas only") and rank 0 prints the whole-job value.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample
+of the same workload on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "triad-ATRG RG steps/s at D=48 4D Ising (mixed vs FP64 form, ΔF/F ≤1e-8)"
+PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "bf16x10": 3}
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--D", type=int, default=48)
+    ap.add_argument("--precision", default="bf16x6", choices=list(PREC))
+    ap.add_argument("--beta", type=float, default=0.1497)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-check", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    return {"workload": f"triad-ATRG coarse-graining step, 4D Ising, beta={a.beta}, h=0, "
+                        f"D={a.D}, p=2D (chi=3D), q_swap=4, q_rho=4, steady state",
+            "D": a.D, "sketch_oversample": 2 * a.D, "precision": a.precision,
+            "l2_flush": "none: inputs (D^5 FP64 factors) far larger than L2"}
+
+
+# ----------------------------------------------------------------- oracle sample
+def oracle_sample(D, budget_s=25.0):
+    """Oracle time per step, from its dominant part: the coarse contraction (eqs.
+    makeMG/makeMH) on D-sized triads with the i1 leg cut to t = 1 and 2 of D slices;
+    T(t) = a + b t is extrapolated to t = D.  Other phases are not timed, so the
+    result is an upper bound on the oracle's steps/s."""
+    import numpy as np
+    from oracle import trg_oracle as O
+    chi = 3 * D
+    rng = np.random.default_rng(0)
+    times = {}
+    for t in (1, 2):
+        E = rng.standard_normal((t, chi, D, D))
+        F = rng.standard_normal((D, chi, D, D))
+        G = rng.standard_normal((D, chi, D, D))
+        H = rng.standard_normal((t, chi, D, D))
+        U = [rng.standard_normal((D, D, chi)) for _ in range(4)]
+        Ms = {mu: rng.standard_normal((D, D, D)) for mu in (2, 3, 4)}
+        t0 = time.time()
+        O.contract_upper(E, F, U[0], U[1], Ms)
+        O.contract_lower(G, H, U[2], U[3], Ms)
+        times[t] = time.time() - t0
+        if times[t] > budget_s:
+            break
+    b = max(times.get(2, times[1]) - times[1], 0.0)
+    a0 = times[1] - b
+    per_step = a0 + b * D
+    return 1.0 / per_step, times, os.cpu_count()
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.time()
+    vals = []
+    for _ in range(max(a.steps, 1)):
+        v, times, cores = oracle_sample(a.D)
+        vals.append(v)
+    v = statistics.median(vals)
+    sample = (f"coarse contraction (eqs. makeMG/makeMH) of one D={a.D} step with the i1 leg "
+              f"cut to 1 and 2 of {a.D} slices, extrapolated linearly to {a.D}; other phases "
+              f"not timed (upper bound); timings {times}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "RG steps/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload(a),
+        "cpu_baseline": {"value": v, "unit": "RG steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "RG steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": time.time() - t0}), flush=True)
+
+
+# ------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- ours
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["bf16_tflops_sustained"], "measured (sustained bf16, MEASURED_PEAKS.json)"
+    except Exception:
+        return 1400.0, "fallback (sustained bf16 estimate)"
+
+
+def precision_check(trg, prec, D=16, nsteps=12):
+    """ΔF/F of the mixed form against the FP64 form of this library at a size where the
+    FP64 form is quick (the FP64 form itself matches the CPU oracle to 1e-10)."""
+    out = {}
+    for p in (0, prec):
+        trg.trg_set_params(4, 4, 0x5EED, p)
+        trg.trg_init_ising(4, 0.1497, 0.0)
+        for n in range(nsteps):
+            trg.trg_step(n % 4, D, 2 * D)
+        out[p] = trg.trg_free_energy()[0]
+    return abs(out[prec] - out[0]) / abs(out[0])
+
+
+def run_ours(a):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_2507_21909_b300 as trg
+    stream = torch.cuda.Stream()
+    trg.trg_set_stream(stream.cuda_stream)
+    prec = PREC[a.precision]
+    D, p = a.D, 2 * a.D
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- whole job, end to end from the host: init (H2D of T0), growth, warm-up, timed
+    barrier()
+    t_job = time.time()
+    trg.trg_set_params(4, 4, 0x5EED, prec)
+    trg.trg_init_ising(4, a.beta, 0.0)
+    n = 0
+    while True:  # grow the tensor until every leg and the bond reach D
+        trg.trg_step(n % 4, D, p)
+        _ = trg.trg_free_energy()
+        n += 1
+        dims = trg.trg_state_dims(0)
+        if all(x == D for x in dims[:4]) and dims[4] == D and n >= 4:
+            break
+        if n > 12:
+            break
+    for _ in range(a.warmup):
+        trg.trg_step(n % 4, D, p)
+        _ = trg.trg_free_energy()
+        n += 1
+    trg.trg_kernel_stats(reset=True)
+    clk = Clocks(local)
+    clk.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phases = {}
+    ev0.record(stream)
+    for _ in range(a.steps):
+        trg.trg_step(n % 4, D, p)
+        f_last = trg.trg_free_energy()
+        n += 1
+        for k, v in trg.trg_step_timings().items():
+            phases[k] = phases.get(k, 0.0) + v / a.steps
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    t_job = time.time() - t_job
+    ms = ev0.elapsed_time(ev1)
+    stats = trg.trg_kernel_stats(reset=True)
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = world * a.steps / (ms / 1e3)
+    e2e = world * n / t_job
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_src = peaks()
+    achieved = stats["tc_flop"] / (stats["tc_ms"] / 1e3) / 1e12 if stats["tc_ms"] > 0 else 0.0
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+            "kernel": "tc_gemm_kernel (split-BF16 tcgen05 GEMM)",
+            "tc_launches": stats["tc_launches"], "tc_ms_per_step": stats["tc_ms"] / a.steps,
+            "tc_share_of_step": stats["tc_ms"] / ms}
+    line = {
+        "metric": METRIC, "value": value, "unit": "RG steps/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic", "config": workload(a),
+        "roofline": roof,
+        "e2e": {"value": e2e, "unit": "RG steps/s", "h2d_bytes_per_step": 3 * 16 * 2 * 8 / n,
+                "d2h_bytes_per_step": 16,
+                "region": f"whole job from the host: trg_init_ising (H2D of T0) + {n} steps "
+                          "(growth, warm-up, timed) each followed by trg_free_energy (D2H)"},
+        "gpu_launches": stats["launches"],
+        "clocks": clocks,
+        "phases_ms": phases,
+        "free_energy": f_last[0],
+    }
+    if not a.no_precision_check and prec != 0:
+        line["delta_f_rel_vs_fp64_form_D16"] = precision_check(trg, prec)
+    if not a.no_cpu_baseline:
+        v, times, cores = oracle_sample(D)
+        line["cpu_baseline"] = {
+            "value": v, "unit": "RG steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"coarse contraction (eqs. makeMG/makeMH) of one D={D} step with the i1 "
+                      f"leg cut to 1 and 2 slices, extrapolated to {D}; other phases not timed"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

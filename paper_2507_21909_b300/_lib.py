@@ -109,6 +109,13 @@ def trg_get_state(which):
     return out, tuple(axes)
 
 
+def trg_state_dims(which=0):
+    """(d1, d2, d3, d4, r) of a state factor without copying it."""
+    dims = (ctypes.c_int * 5)()
+    _check(lib.trg_get_state(int(which), dims, None, None, 0))
+    return tuple(dims)
+
+
 def trg_set_state(beta, phi, psi, psi_imp, axes, nsteps, logsum):
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     psi = np.ascontiguousarray(psi, dtype=np.float64)
