@@ -19,7 +19,7 @@ gemm_f64_kernel(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   for (int64_t z = blockIdx.z; z < batch * nsplit; z += gridDim.z) {
     const int64_t b = z / nsplit, sidx = z % nsplit;
     const int64_t kbeg = sidx * kchunk, kend = min(K, kbeg + kchunk);
@@ -112,7 +112,7 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
               cudaStream_t s) {
   if (M == 0 || N == 0 || batch == 0) return;
   int64_t gy = (M + BM - 1) / BM, gx = (N + BN - 1) / BN;
-  if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_f64: M too large for one launch");
+  if (gx > 65535) throw Error(TRG_ERR_ARG, "gemm_f64: N too large for one launch");
   // split K when the output tiles alone cannot fill the 148 SMs
   int nsplit = 1;
   const int64_t tiles = gx * gy * batch;
@@ -141,7 +141,7 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
     }
   }
   int64_t gz = std::min<int64_t>(batch * nsplit, 65535);
-  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz);
+  dim3 grid((unsigned)gy, (unsigned)gx, (unsigned)gz);  // M tiles on x (up to 2^31 - 1)
   gemm_f64_kernel<<<grid, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta,
                                        C, ldc, sC, batch, kchunk, nsplit, g_ws);
   TRG_LAUNCH_CHECK();

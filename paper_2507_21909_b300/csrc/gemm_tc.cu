@@ -119,7 +119,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n0 = (int64_t)blockIdx.x * BN, m0 = (int64_t)blockIdx.y * BM;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   const int64_t z = blockIdx.z;
   const int64_t b = z % p.batch, split = z / p.batch;
   const int kb0 = (int)split * p.nkb;
@@ -243,31 +243,36 @@ __global__ void split_kernel(const double *__restrict__ X, int64_t rows, int64_t
                              int64_t sX, int trans, int ns, __nv_bfloat16 *__restrict__ out,
                              int64_t Kp, int64_t batch) {
   __shared__ double tile[32][33];
-  const int64_t b = blockIdx.z;
-  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
-  const double *Xb = X + b * sX;
+  const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
+  const int64_t ntiles = rt * kt * batch;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int i = ty; i < 32; i += 8) {
-    double v = 0.0;
-    if (trans) {
-      const int64_t k = k0 + i, r = r0 + tx;  // read along r (contiguous)
-      if (k < K && r < rows) v = Xb[k * ld + r];
-      tile[tx][i] = v;
-    } else {
-      const int64_t r = r0 + i, k = k0 + tx;  // read along k (contiguous)
-      if (k < K && r < rows) v = Xb[r * ld + k];
-      tile[i][tx] = v;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
+    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 32;
+    const double *Xb = X + b * sX;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      double v = 0.0;
+      if (trans) {
+        const int64_t k = k0 + i, r = r0 + tx;  // read along r (contiguous)
+        if (k < K && r < rows) v = Xb[k * ld + r];
+        tile[tx][i] = v;
+      } else {
+        const int64_t r = r0 + i, k = k0 + tx;  // read along k (contiguous)
+        if (k < K && r < rows) v = Xb[r * ld + k];
+        tile[i][tx] = v;
+      }
     }
-  }
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + i, k = k0 + tx;
-    if (r >= rows || k >= Kp) continue;
-    double rem = tile[i][tx];
-    for (int s = 0; s < ns; ++s) {
-      const __nv_bfloat16 h = __double2bfloat16(rem);
-      rem -= (double)__bfloat162float(h);
-      out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = h;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i, k = k0 + tx;
+      if (r >= rows || k >= Kp) continue;
+      double rem2 = tile[i][tx];
+      for (int s = 0; s < ns; ++s) {
+        const __nv_bfloat16 h = __double2bfloat16(rem2);
+        rem2 -= (double)__bfloat162float(h);
+        out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = h;
+      }
     }
   }
 }
@@ -366,12 +371,14 @@ void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   __nv_bfloat16 *Bs = (__nv_bfloat16 *)scr.alloc(bbytes);
   {
     dim3 blk(32, 8);
-    dim3 ga((unsigned)((Kp + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)batch);
-    split_kernel<<<ga, blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, As, Kp, batch);
+    auto nblk = [&](int64_t rows) {
+      int64_t t = ((rows + 31) / 32) * ((Kp + 31) / 32) * batch;
+      return (unsigned)std::min<int64_t>(t, 148 * 32);
+    };
+    split_kernel<<<nblk(M), blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, As, Kp, batch);
     TRG_LAUNCH_CHECK();
     // op(B)[k][n] -> rows n, K-major: transpose unless B is stored [n][k] (tb)
-    dim3 gb((unsigned)((Kp + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)batch);
-    split_kernel<<<gb, blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, Bs, Kp, batch);
+    split_kernel<<<nblk(N), blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, Bs, Kp, batch);
     TRG_LAUNCH_CHECK();
   }
   Params p{};
@@ -391,7 +398,7 @@ void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
       }
   const int BNsel = N <= 128 ? 128 : 256;
   const int64_t gx = (N + BNsel - 1) / BNsel, gy = (M + BM - 1) / BM;
-  if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_tc: M too large");
+  if (gx > 65535) throw Error(TRG_ERR_ARG, "gemm_tc: N too large");
   const int nkb_total = (int)(Kp / BK);
   int ksplit = 1;
   const int64_t tiles = gx * gy * batch;
@@ -416,7 +423,7 @@ void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   }
   CUtensorMap ma = make_map(As, Kp, M, batch, ns, BM);
   CUtensorMap mb = make_map(Bs, Kp, N, batch, ns, BNsel);
-  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
+  dim3 grid((unsigned)gy, (unsigned)gx, (unsigned)(batch * ksplit));  // M tiles on x
   if (timing) timing->before(s);
   if (BNsel == 128)
     launch<128>(ma, mb, p, grid, s);
