@@ -352,10 +352,9 @@ void *Arena::alloc(size_t bytes) {
       return p;
     }
   }
+  // new chunks are sized to the request (at least 1 GiB); reset() merges them into one
   size_t cap = bytes;
-  size_t last = chunks_.empty() ? 0 : chunks_.back().cap;
-  if (cap < 2 * last) cap = 2 * last;
-  if (cap < (size_t(64) << 20)) cap = size_t(64) << 20;
+  if (cap < (size_t(1) << 30)) cap = size_t(1) << 30;
   char *p = nullptr;
   if (cudaMalloc(&p, cap) != cudaSuccess) {
     cudaGetLastError();

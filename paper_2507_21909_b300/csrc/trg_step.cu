@@ -245,6 +245,20 @@ static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const T
   return out;
 }
 
+// run f() in an arena scope and keep only its result (copied into a buffer allocated
+// before the scope)
+template <class F>
+static Tensor keep(Ctx &c, const std::vector<int64_t> &dims, F &&f) {
+  Tensor out = c.alloc(dims);
+  Arena::Mark mk = c.arena.mark();
+  Tensor r = f();
+  if (r.size() != out.size()) throw Error(TRG_ERR_ARG, "keep: size mismatch");
+  TRG_CUDA(cudaMemcpyAsync(out.p, r.p, r.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  c.arena.release(mk);
+  out.dims = r.dims;
+  return out;
+}
+
 static void scale_last(Ctx &c, Tensor &t, const double *v, int mode = 0,
                        const double *vmax = nullptr, double tol = 0.0) {
   int64_t n = t.dims.back();
@@ -460,6 +474,11 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   fill_gaussian(g1.p, k, w, key(TAG_SWAP_G1), s);
   fill_gaussian(g2.p, J, w, key(TAG_SWAP_G2), s);
   khatri_rao(g2.p, g1.p, Om.p, J, k, w, s);
+  const int64_t Dg = std::min<int64_t>(D, w);
+  Tensor X = c.alloc({k, d2, d3, d4, Dg}), Y = c.alloc({k, d2, d3, d4, Dg});
+  Tensor sigT = c.alloc({w});
+  double *sig = sigT.p;
+  Arena::Mark mk_swap = c.arena.mark();
   Tensor Cp = permuted(c, view(C.p, {x, I, k}), {1, 0, 2});   // (I, x, be)
   Tensor Bp = permuted(c, view(B.p, {x, J, k}), {1, 0, 2});   // (J, x, al)
   Tensor Cq = permuted(c, view(C.p, {x, I, k}), {0, 2, 1});   // (x, be, I)
@@ -503,14 +522,11 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   }
   auto [Qt, Rt] = orth_qr(c, Yt);              // M^T Q = Qt Rt  ->  Q^T M = Rt^T Qt^T
   Svd cs = svd_small(c, transpose2(c, Rt));
-  const int64_t Dg = std::min<int64_t>(D, w);
   Tensor Xf = mm_cols(c, Q, cs.U, Dg), Yf = mm_cols(c, Qt, cs.V, Dg);
-  double *sig = cs.S.p;
+  TRG_CUDA(cudaMemcpyAsync(sig, cs.S.p, w * 8, cudaMemcpyDeviceToDevice, s));
   kill_dead(sig, Dg, kRankTol, Xf.p, I * k, Yf.p, J * k, s);
-  Tensor X = permuted(c, view(Xf.p, {I, k, Dg}), {1, 0, 2});
-  Tensor Y = permuted(c, view(Yf.p, {J, k, Dg}), {1, 0, 2});
-  X.dims = {k, d2, d3, d4, Dg};
-  Y.dims = {k, d2, d3, d4, Dg};
+  permute(Xf.p, X.p, {I, k, Dg}, {1, 0, 2}, s);
+  permute(Yf.p, Y.p, {J, k, Dg}, {1, 0, 2}, s);
   double gap_swap = INFINITY;
   {
     std::vector<double> hs(w);
@@ -518,6 +534,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     TRG_CUDA(cudaStreamSynchronize(s));
     if (w > Dg && hs[Dg - 1] > 0) gap_swap = (hs[Dg - 1] - hs[Dg]) / hs[Dg - 1];
   }
+  c.arena.release(mk_swap);
 
   c.mark(2);
   // (c) triad isometries from the canonical-form Grams (eq. HOSVD)
@@ -537,7 +554,9 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor rhoD = contract(c, "wPQRb,wSTRb->PQST", Dm, DW);
   const int64_t chi = std::min<int64_t>(D + p, npair);
   auto iso = [&](Tensor &rho, int tag) {
-    Tensor U = rsvd_sym(c, view(rho.p, {npair, npair}), chi, c.q_rho, key(tag));
+    Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
+      return rsvd_sym(c, view(rho.p, {npair, npair}), chi, c.q_rho, key(tag));
+    });
     U.dims = {d2, d3, U.dims[1]};
     return U;
   };
