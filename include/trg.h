@@ -101,6 +101,9 @@ trg_status trg_step_timings(double *ms, int n);
 trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launches,
                             long long *all_launches, int reset);
 
+/* Device scratch of the step engine in bytes: in use now, high-water mark, reserved. */
+trg_status trg_mem_stats(long long *in_use, long long *high_water, long long *reserved);
+
 /* Copy a state factor to the host.  which: 0 = Phi, 1 = Psi, 2 = Psi_imp.
  * dims_out[0..4] receives (d1, d2, d3, d4, r); host may be NULL (query only), else it
  * must hold `capacity` doubles >= d1 d2 d3 d4 r.  axes_out[0..3] (may be NULL) gets

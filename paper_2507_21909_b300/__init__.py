@@ -9,7 +9,7 @@ _NAMES = ("TRG_PREC_BF16X3", "TRG_PREC_BF16X10", "TRG_PREC_BF16X6", "TRG_PREC_FP
           "library_path", "trg_diag", "trg_finalize", "trg_free_energy", "trg_get_state",
           "trg_init_clock", "trg_init_ising", "trg_magnetisation_impurity", "trg_set_params",
           "trg_set_state", "trg_set_stream", "trg_step", "EXPORTED", "trg_step_timings",
-          "PHASES", "trg_gemm", "trg_kernel_stats", "trg_state_dims")
+          "PHASES", "trg_gemm", "trg_kernel_stats", "trg_state_dims", "trg_mem_stats")
 
 
 def __getattr__(name):

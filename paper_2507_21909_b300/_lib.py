@@ -11,7 +11,7 @@ TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6, TRG_PREC_BF16X10 = 0, 1, 2, 3
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
-            "trg_step_timings", "trg_gemm", "trg_kernel_stats"]
+            "trg_step_timings", "trg_gemm", "trg_kernel_stats", "trg_mem_stats"]
 
 
 class TrgError(RuntimeError):
@@ -37,6 +37,7 @@ def _load():
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
         "trg_step_timings": [pd, i],
+        "trg_mem_stats": [ctypes.POINTER(ctypes.c_longlong)] * 3,
         "trg_kernel_stats": [pd, pd, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong), i],
         "trg_gemm": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d, pd,
@@ -166,6 +167,12 @@ def trg_kernel_stats(reset=False):
                                 ctypes.byref(alln), int(reset)))
     return {"tc_ms": ms.value, "tc_flop": fl.value, "tc_launches": n.value,
             "launches": alln.value}
+
+
+def trg_mem_stats():
+    v = [ctypes.c_longlong() for _ in range(3)]
+    _check(lib.trg_mem_stats(*[ctypes.byref(x) for x in v]))
+    return {"in_use": v[0].value, "high_water": v[1].value, "reserved": v[2].value}
 
 
 def trg_finalize():

@@ -341,12 +341,12 @@ void norm_update(const double *tr, double *c_out, double *logsum, double weight,
 // ------------------------------------------------------------------ arena
 void *Arena::alloc(size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
-  // only the newest chunk is used, so that mark()/release() form a stack
-  if (!chunks_.empty()) {
-    auto &c = chunks_.back();
+  for (size_t i = top_; i < chunks_.size(); ++i) {
+    Chunk &c = chunks_[i];
     if (c.cap - c.used >= bytes) {
       void *p = c.p + c.used;
       c.used += bytes;
+      top_ = i;
       cur_ += bytes;
       if (cur_ > high_) high_ = cur_;
       return p;
@@ -361,10 +361,13 @@ void *Arena::alloc(size_t bytes) {
     cap = bytes;
     if (cudaMalloc(&p, cap) != cudaSuccess) {
       cudaGetLastError();
-      throw Error(TRG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+      throw Error(TRG_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                   " bytes failed (arena in use " + std::to_string(cur_ >> 20) +
+                                   " MiB, reserved " + std::to_string(reserved() >> 20) + " MiB)");
     }
   }
   chunks_.push_back({p, cap, bytes});
+  top_ = chunks_.size() - 1;
   cur_ += bytes;
   if (cur_ > high_) high_ = cur_;
   return p;
@@ -382,18 +385,21 @@ void Arena::reset() {
       cudaGetLastError();
   }
   for (auto &c : chunks_) c.used = 0;
+  top_ = 0;
   cur_ = 0;
 }
 
 void Arena::release(const Mark &m) {
-  for (size_t i = m.nchunks; i < chunks_.size(); ++i) chunks_[i].used = 0;
-  if (m.nchunks > 0 && m.nchunks <= chunks_.size()) chunks_[m.nchunks - 1].used = m.used_last;
+  for (size_t i = m.top + 1; i < chunks_.size(); ++i) chunks_[i].used = 0;
+  if (m.top < chunks_.size()) chunks_[m.top].used = m.used;
+  top_ = m.top;
   cur_ = m.cur;
 }
 
 void Arena::release() {
   for (auto &c : chunks_) cudaFree(c.p);
   chunks_.clear();
+  top_ = 0;
   cur_ = 0;
 }
 

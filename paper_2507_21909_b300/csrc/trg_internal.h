@@ -36,13 +36,17 @@ extern int64_t g_kernel_launches;
 // at once by reset(); persistent state buffers are separate cudaMalloc'd buffers.
 class Arena {
  public:
-  struct Mark { size_t nchunks, used_last, cur; };
+  struct Mark { size_t top, used, cur; };
   void *alloc(size_t bytes);
   // stack discipline: everything allocated after mark() is released by release(mark)
-  Mark mark() const {
-    return {chunks_.size(), chunks_.empty() ? 0 : chunks_.back().used, cur_};
-  }
+  Mark mark() const { return {top_, chunks_.empty() ? 0 : chunks_[top_].used, cur_}; }
   void release(const Mark &m);
+  size_t in_use() const { return cur_; }
+  size_t reserved() const {
+    size_t r = 0;
+    for (auto &c : chunks_) r += c.cap;
+    return r;
+  }
   void reset();           // callers must have synchronised the stream first
   void release();         // frees all chunks
   size_t high_water() const { return high_; }
@@ -50,7 +54,8 @@ class Arena {
 
  private:
   struct Chunk { char *p; size_t cap; size_t used; };
-  std::vector<Chunk> chunks_;
+  std::vector<Chunk> chunks_;  // chunks after top_ are empty
+  size_t top_ = 0;
   size_t high_ = 0, cur_ = 0;
 };
 

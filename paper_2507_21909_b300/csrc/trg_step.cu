@@ -45,7 +45,9 @@ struct Ctx {
   static constexpr int kPhases = 8;
   cudaEvent_t ev[kPhases + 1] = {};
   double phase_ms[kPhases] = {};
+  int phase = 0;
   void mark(int i) {
+    phase = i;
     if (!ev[i]) TRG_CUDA(cudaEventCreate(&ev[i]));
     TRG_CUDA(cudaEventRecord(ev[i], stream));
   }
@@ -829,10 +831,10 @@ trg_status trg_step(int axis, int D, int sketch_oversample) {
       throw Error(TRG_ERR_ARG, "need 0 <= axis < 4, D >= 1, p >= 0");
     try {
       step_impl(c, axis, D, sketch_oversample);
-    } catch (...) {
+    } catch (const Error &e) {
       cudaStreamSynchronize(c.stream);
       c.arena.reset();
-      throw;
+      throw Error(e.code, std::string(e.what()) + " [step phase " + std::to_string(c.phase) + "]");
     }
   });
 }
@@ -1011,6 +1013,15 @@ trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launch
       c.tc_launches = 0;
       g_kernel_launches = 0;
     }
+  });
+}
+
+trg_status trg_mem_stats(long long *in_use, long long *high_water, long long *reserved) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (in_use) *in_use = (long long)c.arena.in_use();
+    if (high_water) *high_water = (long long)c.arena.high_water();
+    if (reserved) *reserved = (long long)c.arena.reserved();
   });
 }
 
