@@ -7,6 +7,7 @@
 // host never waits on device data inside a step except for the final status read.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -40,6 +41,8 @@ struct Ctx {
   int *dflag = nullptr;
   int q_swap = 4, q_rho = 4, precision = TRG_PREC_FP64;
   bool mixed_now = false;      // this step runs its bulk GEMMs on the tensor cores
+  int crit_depth = 0;          // > 0 inside decompositions (QR, re-split, squeezer roots)
+  bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
   static constexpr int kPhases = 8;
@@ -116,6 +119,12 @@ static int64_t prod(const std::vector<int64_t> &d, size_t a = 0, size_t b = SIZE
 }
 
 // ------------------------------------------------------------------ GEMM dispatch
+struct Crit {  // marks a decomposition: its GEMMs may be routed to FP64
+  Ctx &c;
+  explicit Crit(Ctx &cc) : c(cc) { ++c.crit_depth; }
+  ~Crit() { --c.crit_depth; }
+};
+
 struct ArenaScratch : TcScratch {
   Arena &a;
   explicit ArenaScratch(Arena &ar) : a(ar) {}
@@ -133,7 +142,8 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
-  if (c.mixed_now && work >= (double)(1 << 24) && M >= 64 && N >= 16 && K >= 64) {
+  if (c.mixed_now && !(c.crit_fp64 && c.crit_depth > 0) && work >= (double)(1 << 24) &&
+      M >= 64 && N >= 16 && K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
@@ -292,6 +302,7 @@ static Tensor orth_sc(Ctx &c, const Tensor &Y) {
 }
 
 static std::pair<Tensor, Tensor> orth_qr(Ctx &c, const Tensor &Y) {
+  Crit cr(c);
   Tensor Q = orth_sc(c, Y);
   Tensor R = mm(c, Q, Y, true, false);
   return {Q, R};
@@ -330,15 +341,18 @@ static Tensor rsvd_sym(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t k
   return Q;
 }
 
-// R (c' x n) with R^T R = Q Q^T rho Q Q^T, Q the rank-chi range of rho
+// R (c' x n) with R^T R = Q Q^T rho Q Q^T, Q the rank-chi range of rho.  R = L Q^T with
+// L the upper Cholesky factor of Q^T rho Q (dead pivots give zero rows); any square root
+// serves, since the squeezer only uses the singular triplets of R1 R2^T, which are
+// invariant under R -> O R.
 static Tensor gram_root(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t key) {
+  Crit cr(c);
   Tensor Q = rsvd_sym(c, rho, chi, q, key);
   Tensor Bm = mm(c, Q, mm(c, rho, Q, false, false), true, false);
-  Svd sv = svd_small(c, Bm);
-  Tensor QV = mm(c, Q, sv.V, false, false);        // n x c'
-  Tensor R = transpose2(c, QV);                     // c' x n
-  scale_axis(R.p, R.size(), R.dims[1], R.dims[0], sv.S.p, 3, nullptr, 0.0, c.stream);
-  return R;
+  const int64_t cc = Bm.dims[0];
+  Tensor L = c.alloc({cc, cc}), Li = c.alloc({cc, cc});
+  chol_rinv(Bm.p, L.p, Li.p, (int)cc, 1, kPivotTol, 0.0, c.stream);
+  return mm(c, L, Q, false, true);                  // c' x n
 }
 
 // oblique squeezer pair on one pair bond: M (n x k) on the forward side, N on the backward
@@ -350,6 +364,7 @@ static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor
     *gap_out = INFINITY;
     return {identity(c, n), identity(c, n)};
   }
+  Crit cr(c);
   Tensor R1 = gram_root(c, rf, chi, q, kf), R2 = gram_root(c, rb, chi, q, kb);
   Tensor K = mm(c, R1, R2, false, true);
   Svd sv = svd_small(c, K);
@@ -446,13 +461,14 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], d4 = c.dims[3], r = c.dims[4];
   const int64_t Nf = d1 * d2 * d3 * d4;
   const int n = c.nsteps;
-  // mixed forms: tensor cores only once every leg has reached D (earlier steps are small
-  // and carry the largest weights 2^-n of the free energy)
-  c.mixed_now = c.precision != TRG_PREC_FP64 && d1 >= D && d2 >= D && d3 >= D && d4 >= D && r >= D;
+  // mixed forms: tensor cores from the fourth step on; the first three steps carry
+  // weights 1, 1/2, 1/4 of the free energy and have small legs, so they stay in FP64
+  c.mixed_now = c.precision != TRG_PREC_FP64 && n >= 3;
   auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
 
   // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
   Tensor P2 = view(c.phi, {Nf, r}), S2 = view(c.psi, {Nf, r});
+  std::unique_ptr<Crit> crit_resplit(new Crit(c));
   auto [Qp, Rp] = orth_qr(c, P2);
   auto [Qs, Rs] = orth_qr(c, S2);
   Svd rs = svd_small(c, mm(c, Rp, Rs, false, true));
@@ -463,6 +479,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   kill_dead(sv, k, kRankTol, A.p, Nf, Dm.p, Nf, s);
   A.dims = {d1, d2, d3, d4, k};
   Dm.dims = {d1, d2, d3, d4, k};
+  crit_resplit.reset();
 
   c.mark(1);
   // (b) bond swap: sum_x B[x J al] C[x I be] ~ X sigma Y  (Appendix A), applied to the
@@ -514,7 +531,12 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     Tensor Qn = orth_sc(c, Y);
     TRG_CUDA(cudaMemcpyAsync(Q.p, Qn.p, Q.size() * 8, cudaMemcpyDeviceToDevice, s));
     c.arena.release(mk);
-    applyMt(Q, Yt);
+    if (rnd + 1 == c.q_swap) {
+      Crit cr(c);  // the last application feeds the core SVD
+      applyMt(Q, Yt);
+    } else {
+      applyMt(Q, Yt);
+    }
     if (rnd + 1 < c.q_swap) {
       Arena::Mark mk2 = c.arena.mark();
       Tensor Vn = orth_sc(c, Yt);
@@ -522,6 +544,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
       c.arena.release(mk2);
     }
   }
+  std::unique_ptr<Crit> crit_core(new Crit(c));
   auto [Qt, Rt] = orth_qr(c, Yt);              // M^T Q = Qt Rt  ->  Q^T M = Rt^T Qt^T
   Svd cs = svd_small(c, transpose2(c, Rt));
   Tensor Xf = mm_cols(c, Q, cs.U, Dg), Yf = mm_cols(c, Qt, cs.V, Dg);
@@ -529,6 +552,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   kill_dead(sig, Dg, kRankTol, Xf.p, I * k, Yf.p, J * k, s);
   permute(Xf.p, X.p, {I, k, Dg}, {1, 0, 2}, s);
   permute(Yf.p, Y.p, {J, k, Dg}, {1, 0, 2}, s);
+  crit_core.reset();
   double gap_swap = INFINITY;
   {
     std::vector<double> hs(w);
@@ -655,6 +679,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
 
   c.mark(7);
   // normalisation c_n = ||T||_F and ln Z bookkeeping
+  Crit crit_norm(c);
   const int64_t rn = PhiN.dims[4], Nn = PhiN.size() / rn;
   Tensor Gp = mm(c, view(PhiN.p, {Nn, rn}), view(PhiN.p, {Nn, rn}), true, false);
   Tensor Gs = mm(c, view(PsiN.p, {Nn, rn}), view(PsiN.p, {Nn, rn}), true, false);
@@ -690,6 +715,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
 
 // -------------------------------------------------------------------- init helpers
 static void ensure_ctx(Ctx &c) {
+  if (const char *e = getenv("TRG_DECOMP_FP64")) c.crit_fp64 = e[0] == '1';
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
