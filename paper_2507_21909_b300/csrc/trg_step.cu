@@ -43,6 +43,7 @@ struct Ctx {
   bool mixed_now = false;      // this step runs its bulk GEMMs on the tensor cores
   int crit_depth = 0;          // > 0 inside decompositions (QR, re-split, squeezer roots)
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
+  unsigned phase_mask = 0xFFu; // phases whose GEMMs may use the tensor cores
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
   static constexpr int kPhases = 8;
@@ -142,7 +143,8 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
-  if (c.mixed_now && !(c.crit_fp64 && c.crit_depth > 0) && work >= (double)(1 << 24) &&
+  if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
+      work >= (double)(1 << 24) &&
       M >= 64 && N >= 16 && K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
@@ -716,6 +718,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
 // -------------------------------------------------------------------- init helpers
 static void ensure_ctx(Ctx &c) {
   if (const char *e = getenv("TRG_DECOMP_FP64")) c.crit_fp64 = e[0] == '1';
+  if (const char *e = getenv("TRG_TC_PHASES")) c.phase_mask = (unsigned)strtoul(e, nullptr, 0);
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
