@@ -211,6 +211,7 @@ def run_ours(a):
         trg.trg_step(n % 4, D, p)
         _ = trg.trg_free_energy()
         n += 1
+    launches_before = trg.trg_kernel_stats()["launches"]
     trg.trg_kernel_stats(reset=True)
     clk = Clocks(local)
     clk.start()
@@ -258,6 +259,7 @@ def run_ours(a):
                 "region": f"whole job from the host: trg_init_ising (H2D of T0) + {n} steps "
                           "(growth, warm-up, timed) each followed by trg_free_energy (D2H)"},
         "gpu_launches": stats["launches"],
+        "timed_launch_range": [launches_before, launches_before + stats["launches"]],
         "clocks": clocks,
         "phases_ms": phases,
         "free_energy": f_last[0],
