@@ -128,6 +128,30 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
                     double alpha, const double *A, long long lda, const double *B,
                     long long ldb, double beta, double *C, long long ldc);
 
+/* C = alpha op(A) op(B) + beta C like trg_gemm, but on the caller's DEVICE buffers
+ * (row-major FP64, leading dimensions lda, ldb, ldc) and without allocating anything:
+ * for callers that cannot call cudaMalloc at this point, such as code running while a
+ * CUDA graph is captured, host frameworks that own all device memory through their own
+ * pool, or real-time loops that must not allocate after start-up.  The paper has no
+ * counterpart; this is a service of the library's contraction engine.
+ * precision: TRG_PREC_BF16X3, _BF16X6 or _BF16X10 (the split-BF16 tcgen05 GEMM; the
+ * FP64 CUDA-core GEMM needs a workspace and is not offered here).  The only scratch is a
+ * fixed 64 MiB __device__ array in the library (every GPU that loads the library holds
+ * it until the process exits); problems that need more (BF16 slices of A and B plus
+ * split-K partial tiles) are rejected with TRG_ERR_ARG and a message.  The work is
+ * queued on `stream` (a cudaStream_t, NULL = legacy default stream) and not
+ * synchronised.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  Every
+ * call shares the array; calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it — serialise them.  All scratch is overwritten
+ * before it is read, so no state carries over between calls.
+ * Errors (returned before any work is queued): TRG_ERR_ARG, TRG_ERR_CUDA; see
+ * trg_last_error(). */
+trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long M, long long N,
+                            long long K, double alpha, const double *A, long long lda,
+                            const double *B, long long ldb, double beta, double *C,
+                            long long ldc, void *stream);
+
 /* Release every device buffer of the context. */
 trg_status trg_finalize(void);
 

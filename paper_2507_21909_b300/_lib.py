@@ -11,7 +11,8 @@ TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6, TRG_PREC_BF16X10 = 0, 1, 2, 3
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
-            "trg_step_timings", "trg_gemm", "trg_kernel_stats", "trg_mem_stats"]
+            "trg_step_timings", "trg_gemm", "trg_kernel_stats", "trg_mem_stats",
+            "trg_gemm_noalloc"]
 
 
 class TrgError(RuntimeError):
@@ -38,6 +39,9 @@ def _load():
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
         "trg_step_timings": [pd, i],
         "trg_mem_stats": [ctypes.POINTER(ctypes.c_longlong)] * 3,
+        "trg_gemm_noalloc": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d,
+                             vp, ctypes.c_longlong, vp, ctypes.c_longlong, d, vp,
+                             ctypes.c_longlong, vp],
         "trg_kernel_stats": [pd, pd, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong), i],
         "trg_gemm": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d, pd,

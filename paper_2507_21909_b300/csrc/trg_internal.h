@@ -31,6 +31,9 @@ extern int64_t g_kernel_launches;
     TRG_CUDA(cudaGetLastError()); \
   } while (0)
 
+// message returned by trg_last_error()
+void set_last_error(const std::string &msg);
+
 // ------------------------------------------------------------------ device arena
 // Bump allocator over a few large cudaMalloc chunks.  Scratch of one step is released
 // at once by reset(); persistent state buffers are separate cudaMalloc'd buffers.

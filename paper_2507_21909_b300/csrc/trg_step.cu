@@ -105,6 +105,7 @@ static Ctx &ctx() {
   return c;
 }
 static std::string g_err = "ok";
+void set_last_error(const std::string &msg) { g_err = msg; }
 
 static Tensor view(double *p, std::vector<int64_t> d) {
   Tensor t;
