@@ -38,7 +38,11 @@ typedef int trg_status;
 #define TRG_PREC_BF16X3    1   /* bulk GEMMs as 3-term BF16-split tcgen05, FP32 accum */
 #define TRG_PREC_BF16X6    2   /* bulk GEMMs as 6-term BF16-split tcgen05, FP32 accum */
 #define TRG_PREC_BF16X10   3   /* bulk GEMMs as 10-term BF16-split tcgen05, FP32 accum */
-/* In the mixed forms (1..3) a step runs on the tensor cores only once all four legs and
+#define TRG_PREC_OZ4       4   /* bulk GEMMs with 4 exact 7-bit digits per row (10
+                                  tcgen05 products), exact FP32 chunks + int64 sums      */
+#define TRG_PREC_OZ5       5   /* 5 digits (15 products)                               */
+#define TRG_PREC_OZ6       6   /* 6 digits (21 products)                               */
+/* In the mixed forms (1..6) a step runs on the tensor cores only once all four legs and
  * the bond have reached D; the earlier, smaller steps run in FP64. */
 
 /* Initial tensor of the d-dimensional Ising model, Sec. III (CP form

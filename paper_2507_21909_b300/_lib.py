@@ -8,6 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _PATH = os.path.join(HERE, "libtrg.so")
 
 TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6, TRG_PREC_BF16X10 = 0, 1, 2, 3
+TRG_PREC_OZ4, TRG_PREC_OZ5, TRG_PREC_OZ6 = 4, 5, 6
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",

@@ -1,0 +1,517 @@
+// Exact-accumulation split GEMM on the tcgen05 tensor cores (Ozaki-style digits).
+//
+// C (FP64) = alpha * op(A) op(B) + beta * C with ~7*ns bits of every row of op(A) and
+// column of op(B).  Each row r of op(A) gets a common exponent e_r (max |a| < 2^e_r) and
+// a' = a 2^-e_r in (-1, 1) is cut into integer digits d_s (|d_0| <= 128, |d_s| <= 64):
+//     a' = sum_s d_s 2^(-7(s+1)) + O(2^(-7 ns - 1)).
+// Slices are stored pre-scaled as BF16 values  ^a_s = d_s 2^(-7(s-1))  (exact: 8-bit
+// integers times powers of two), so that  a' b' = 2^-28 sum_{i,j} ^a_i ^b_j  and the
+// digit products fall into three tensor-memory accumulators:
+//     L0 = sum ^a_0 ^b_0            (integers x 2^14,  |chunk sum| <= 2^36)
+//     L1 = sum ^a_0 ^b_1 + ^a_1 ^b_0 (integers x 2^7)
+//     H  = sum over i + j in [2, ns-1] of ^a_i ^b_j   (carries 2^-14 of the result)
+// Over a chunk of 256 K the FP32 sums L0 / L1 are exact integers (|L0 2^-14| and
+// |L1 2^-7| <= 2^22), so they are drained every chunk into int64 registers; H stays in
+// FP32 for the whole K (its rounding is 2^-38 of the result).  The epilogue forms
+// C = alpha 2^(e_r + e_c - 28) (S + H) + beta C in FP64.
+//
+// CTA = 10 warps: warp 0 TMA producer (one tile of one A slice and one B slice per
+// stage, 6 stages), warp 1 MMA issuer (M = 128, N = 128, K = 16), warps 2..9 drain TMEM
+// (two warps per 32-lane quadrant, 64 columns each).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "gemm_oz.h"
+#include "trg_internal.h"
+
+namespace trg {
+namespace oz {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
+constexpr int CHUNK_KB = 4;                 // 4 x 64 = 256 K per exact chunk
+constexpr int NWARPS = 10, THREADS = NWARPS * 32;
+constexpr int MAX_PAIRS = 36;
+constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 (power of two)
+
+struct Params {
+  int64_t M, N, Kp, batch;
+  int nkb;                                  // K blocks per split (multiple of CHUNK_KB)
+  int npairs;
+  int pi[MAX_PAIRS], pj[MAX_PAIRS], pl[MAX_PAIRS];  // slice of A, slice of B, level 0/1/2
+  const int *ea, *eb;                       // row exponents [batch][M], [batch][N]
+  double alpha, beta;
+  double *C;
+  int64_t ldc, sC;
+  int to_ws;
+};
+
+__device__ int g_oz_err;
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mb_init(uint32_t b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mb_expect(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint32_t b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ bool mb_wait(uint32_t b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicExch(&g_oz_err, 1);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma4(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c0,
+                                     int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void tld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// exact integer of an FP32 value v with |v| <= 2^22 (v an integer)
+__device__ __forceinline__ int exact_int(float v) {
+  return __float_as_int(v + 12582912.0f) - 0x4B400000;
+}
+
+__global__ void __maxnreg__(200)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const Params p) {
+  constexpr uint32_t TILE = BM * BK * 2;    // 16 KB (A and B tiles are both 128 x 64)
+  constexpr uint32_t STAGE = 2 * TILE;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+  // bar[0..S) full, bar[S..2S) empty, bar[2S] chunk ready, bar[2S+1] chunk drained,
+  // bar[2S+2] all done
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * STAGES + 3);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t b = blockIdx.z % p.batch, split = blockIdx.z / p.batch;
+  const int nkb_total = (int)(p.Kp / BK);
+  const int kb0 = (int)split * p.nkb;
+  const int nk = max(min(kb0 + p.nkb, nkb_total) - kb0, 0);
+  const int nchunks = (nk + CHUNK_KB - 1) / CHUNK_KB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mb_init(su32(&bar[s]), 1);
+      mb_init(su32(&bar[STAGES + s]), 1);
+    }
+    mb_init(su32(&bar[2 * STAGES]), 1);
+    mb_init(su32(&bar[2 * STAGES + 1]), 8 * 32);
+    mb_init(su32(&bar[2 * STAGES + 2]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------------ TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int ch = 0; ch < nchunks && ok; ++ch)
+        for (int kb = ch * CHUNK_KB; kb < min((ch + 1) * CHUNK_KB, nk) && ok; ++kb)
+          for (int pr = 0; pr < p.npairs; ++pr, ++it) {
+            const int s = it % STAGES;
+            if (!mb_wait(su32(&bar[STAGES + s]), ((uint32_t)(it / STAGES) & 1u) ^ 1u)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sa = su32(smem + s * STAGE), sb = sa + TILE;
+            const uint32_t full = su32(&bar[s]);
+            mb_expect(full, STAGE);
+            tma4(sa, &tmA, full, (kb0 + kb) * BK, (int)m0, (int)b, p.pi[pr]);
+            tma4(sb, &tmB, full, (kb0 + kb) * BK, (int)n0, (int)b, p.pj[pr]);
+          }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------ MMA issuer
+      int it = 0;
+      bool ok = true, h_started = false;
+      for (int ch = 0; ch < nchunks && ok; ++ch) {
+        if (ch > 0 && !mb_wait(su32(&bar[2 * STAGES + 1]), (uint32_t)(ch - 1) & 1u)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool l_started[2] = {false, false};
+        for (int kb = ch * CHUNK_KB; kb < min((ch + 1) * CHUNK_KB, nk) && ok; ++kb)
+          for (int pr = 0; pr < p.npairs; ++pr, ++it) {
+            const int s = it % STAGES;
+            if (!mb_wait(su32(&bar[s]), (uint32_t)(it / STAGES) & 1u)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int lvl = p.pl[pr];
+            const uint32_t acc_t = tmem + (uint32_t)(lvl * BN);
+            bool &started = lvl == 2 ? h_started : l_started[lvl];
+            const uint32_t sa = su32(smem + s * STAGE), sb = sa + TILE;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t accum = (started || kk > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc_t),
+                  "l"(sdesc(sa + kk * 32)), "l"(sdesc(sb + kk * 32)), "r"(kIdesc), "r"(accum)
+                  : "memory");
+            }
+            started = true;
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    su32(&bar[STAGES + s]))
+                : "memory");
+          }
+        // L0 / L1 of this chunk complete -> drain (the drainers also handle unused levels)
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&bar[2 * STAGES]))
+            : "memory");
+        (void)l_started;
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(&bar[2 * STAGES + 2]))
+          : "memory");
+      (void)h_started;
+    }
+  } else {  // ------------------------------------------------------ drain warps 2..9
+    const int ew = warp - 2;                  // 0..7
+    const int quad = warp & 3;                // TMEM lane quadrant of this warp
+    const int half = ew >> 2;                 // columns [64 half, 64 half + 64)
+    const int64_t row = m0 + quad * 32 + lane;
+    long long S[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) S[j] = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!mb_wait(su32(&bar[2 * STAGES]), (uint32_t)ch & 1u)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // L0 and L1 always have pairs (ns >= 3): exact integers of this chunk into S
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t r0[32], r1[32];
+        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64 + c * 32);
+        tld32(base, r0);
+        tld32(base + BN, r1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int i0 = exact_int(__uint_as_float(r0[j]) * 0x1.0p-14f);
+          const int i1 = exact_int(__uint_as_float(r1[j]) * 0x1.0p-7f);
+          S[c * 32 + j] += ((long long)i0 << 14) + ((long long)i1 << 7);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mb_arrive(su32(&bar[2 * STAGES + 1]));
+    }
+    bool done = ok && nchunks > 0 && mb_wait(su32(&bar[2 * STAGES + 2]), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
+    const int64_t ldc = p.to_ws ? p.N : p.ldc;
+    const int er = row < p.M ? p.ea[b * p.M + row] : 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      uint32_t r[32];
+      tld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN + half * 64 + c * 32), r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < p.M) {
+        double *crow = Cbase + row * ldc;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = n0 + half * 64 + c * 32 + j;
+          if (col >= p.N) continue;
+          double v = 0.0;
+          if (done) {
+            const double h = (double)__uint_as_float(r[j]);
+            v = ldexp((double)S[c * 32 + j] + h, er + p.eb[b * p.N + col] - 28);
+          }
+          if (p.to_ws)
+            crow[col] = v;
+          else
+            crow[col] = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * crow[col];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// common exponent of every row r of op(X): e with max_k |op(X)[r][k]| < 2^e (0 if zero)
+__global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
+                                 int64_t ld, int64_t sX, int trans, int64_t batch, int *e) {
+  const int64_t nr = rows * batch;
+  if (!trans) {  // one warp per row, contiguous along k
+    const int warps = blockDim.x >> 5;
+    for (int64_t g = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); g < nr;
+         g += (int64_t)gridDim.x * warps) {
+      const int64_t b = g / rows, r = g % rows;
+      const double *x = X + b * sX + r * ld;
+      double m = 0.0;
+      for (int64_t k = threadIdx.x & 31; k < K; k += 32) m = fmax(m, fabs(x[k]));
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0) {
+        int ex = 0;
+        if (m > 0.0) frexp(m, &ex);
+        e[g] = ex;
+      }
+    }
+  } else {  // op(X)[r][k] = X[k ld + r]: threads along r, loop over k
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nr;
+         g += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t b = g / rows, r = g % rows;
+      const double *x = X + b * sX + r;
+      double m = 0.0;
+      for (int64_t k = 0; k < K; ++k) m = fmax(m, fabs(x[k * ld]));
+      int ex = 0;
+      if (m > 0.0) frexp(m, &ex);
+      e[g] = ex;
+    }
+  }
+}
+
+// digits ^a_s = d_s 2^(-7(s-1)) of op(X) rows, layout [slice][batch][rows][Kp] (K-major)
+__global__ void oz_split_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
+                                int64_t ld, int64_t sX, int trans, int ns, const int *e,
+                                __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
+  __shared__ double tile[32][33];
+  const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
+  const int64_t ntiles = rt * kt * batch;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
+    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 32;
+    const double *Xb = X + b * sX;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      double v = 0.0;
+      if (trans) {
+        const int64_t k = k0 + i, r = r0 + tx;
+        if (k < K && r < rows) v = Xb[k * ld + r];
+        tile[tx][i] = v;
+      } else {
+        const int64_t r = r0 + i, k = k0 + tx;
+        if (k < K && r < rows) v = Xb[r * ld + k];
+        tile[i][tx] = v;
+      }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i, k = k0 + tx;
+      if (r >= rows || k >= Kp) continue;
+      double a = ldexp(tile[i][tx], -e[b * rows + r]);  // |a| < 1
+      for (int s = 0; s < ns; ++s) {
+        const double d = rint(ldexp(a, 7 * (s + 1)));   // integer digit
+        a -= ldexp(d, -7 * (s + 1));                     // exact
+        out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] =
+            __double2bfloat16(ldexp(d, -7 * (s - 1)));   // exact (<= 8 significant bits)
+      }
+    }
+  }
+}
+
+__global__ void oz_ws_reduce(const double *__restrict__ W, int ksplit, int64_t batch, int64_t M,
+                             int64_t N, double alpha, double beta, double *__restrict__ C,
+                             int64_t ldc, int64_t sC) {
+  const int64_t total = batch * M * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < ksplit; ++s) acc += W[s * total + i];
+    const int64_t bb = i / (M * N), mn = i % (M * N), m = mn / N, n = mn % N;
+    double *c = C + bb * sC + m * ldc + n;
+    *c = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *c;
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  if (!fn) throw Error(TRG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+static CUtensorMap tmap(const void *base, int64_t Kp, int64_t rows, int64_t batch, int ns) {
+  CUtensorMap m;
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)ns};
+  cuuint64_t strides[3] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2),
+                           (cuuint64_t)(batch * rows * Kp * 2)};
+  cuuint32_t box[4] = {(cuuint32_t)BK, 128u, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(TRG_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+constexpr size_t kSmem = (size_t)STAGES * 2 * BM * BK * 2 + 1024 + 256;
+
+}  // namespace oz
+
+int oz_error_flag(bool reset) {
+  int v = 0;
+  cudaMemcpyFromSymbol(&v, oz::g_oz_err, sizeof(int));
+  if (reset) {
+    int z = 0;
+    cudaMemcpyToSymbol(oz::g_oz_err, &z, sizeof(int));
+  }
+  return v;
+}
+
+void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+             int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
+             double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
+             cudaStream_t s, TcTiming *timing) {
+  using namespace oz;
+  if (M == 0 || N == 0 || batch == 0) return;
+  if (ns < 3 || ns > 6) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 6");
+  if (batch > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: batch too large");
+  const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
+  int *ea = (int *)scr.alloc((size_t)batch * M * sizeof(int));
+  int *eb = (int *)scr.alloc((size_t)batch * N * sizeof(int));
+  __nv_bfloat16 *As = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * M * Kp * 2);
+  __nv_bfloat16 *Bs = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * N * Kp * 2);
+  {
+    const int blk = 256;
+    auto g1 = [&](int64_t rows) { return (unsigned)std::min<int64_t>((rows * batch + 7) / 8 + 1, 148 * 64); };
+    oz_rowexp_kernel<<<g1(M), blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, batch, ea);
+    TRG_LAUNCH_CHECK();
+    oz_rowexp_kernel<<<g1(N), blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, batch, eb);
+    TRG_LAUNCH_CHECK();
+    dim3 b2(32, 8);
+    auto nblk = [&](int64_t rows) {
+      int64_t t = ((rows + 31) / 32) * ((Kp + 31) / 32) * batch;
+      return (unsigned)std::min<int64_t>(t, 148 * 32);
+    };
+    oz_split_kernel<<<nblk(M), b2, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, ea, As, Kp, batch);
+    TRG_LAUNCH_CHECK();
+    oz_split_kernel<<<nblk(N), b2, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, eb, Bs, Kp, batch);
+    TRG_LAUNCH_CHECK();
+  }
+  Params p{};
+  p.M = M;
+  p.N = N;
+  p.Kp = Kp;
+  p.batch = batch;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.ea = ea;
+  p.eb = eb;
+  p.npairs = 0;
+  for (int t = 0; t < ns; ++t)        // level order: L0, L1, then the rest
+    for (int i = 0; i <= t; ++i) {
+      p.pi[p.npairs] = i;
+      p.pj[p.npairs] = t - i;
+      p.pl[p.npairs] = t < 2 ? t : 2;
+      ++p.npairs;
+    }
+  const int64_t gx = (M + BM - 1) / BM, gy = (N + BN - 1) / BN;
+  if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: N too large");
+  const int nkb_total = (int)(Kp / BK);
+  int ksplit = 1;
+  const int64_t tiles = gx * gy * batch;
+  if (tiles < 148 && nkb_total >= 2 * CHUNK_KB) {
+    ksplit = (int)std::min<int64_t>(std::min<int64_t>((2 * 148 + tiles - 1) / tiles,
+                                                      nkb_total / CHUNK_KB),
+                                    65535 / batch);
+    ksplit = std::max(ksplit, 1);
+  }
+  int per = (nkb_total + ksplit - 1) / ksplit;
+  per = (per + CHUNK_KB - 1) / CHUNK_KB * CHUNK_KB;
+  ksplit = (nkb_total + per - 1) / per;
+  p.nkb = per;
+  if (ksplit > 1) {
+    p.C = (double *)scr.alloc((size_t)ksplit * batch * M * N * sizeof(double));
+    p.to_ws = 1;
+    p.ldc = N;
+    p.sC = M * N;
+  } else {
+    p.C = C;
+    p.to_ws = 0;
+    p.ldc = ldc;
+    p.sC = sC;
+  }
+  CUtensorMap ma = tmap(As, Kp, M, batch, ns), mb = tmap(Bs, Kp, N, batch, ns);
+  static bool attr = false;
+  if (!attr) {
+    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmem));
+    attr = true;
+  }
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
+  if (timing) timing->before(s);
+  oz_gemm_kernel<<<grid, THREADS, kSmem, s>>>(ma, mb, p);
+  TRG_LAUNCH_CHECK();
+  if (timing) timing->after(s, 2.0 * (double)M * N * K * batch * p.npairs);
+  if (ksplit > 1) {
+    const int64_t total = batch * M * N;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+    oz_ws_reduce<<<blocks, 256, 0, s>>>(p.C, ksplit, batch, M, N, alpha, beta, C, ldc, sC);
+    TRG_LAUNCH_CHECK();
+  }
+}
+
+}  // namespace trg

@@ -13,6 +13,7 @@
 #include <memory>
 #include <utility>
 
+#include "gemm_oz.h"
 #include "gemm_tc.h"
 #include "trg_internal.h"
 
@@ -149,8 +150,12 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
       M >= 64 && N >= 16 && K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
-    gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-            slices_of(c.precision), scr, c.stream, &c.timing);
+    if (c.precision >= TRG_PREC_OZ4)
+      gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+              c.precision, scr, c.stream, &c.timing);
+    else
+      gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+              slices_of(c.precision), scr, c.stream, &c.timing);
     c.arena.release(mk);
   } else {
     gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream);
@@ -712,7 +717,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   c.last_gap = std::min(gap_swap, gap_sq);
   c.arena.reset();
   if (flag) throw Error(flag, "non-finite norm in the coarse-graining step");
-  if (c.mixed_now && tc_error_flag(true))
+  if (c.mixed_now && (tc_error_flag(true) | oz_error_flag(true)))
     throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
 }
 
@@ -901,8 +906,8 @@ trg_status trg_magnetisation_impurity(double *m) {
 
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision) {
   return guarded([&] {
-    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > 3)
-      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..3");
+    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > 6)
+      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..6");
     Ctx &c = ctx();
     c.q_swap = q_swap;
     c.q_rho = q_rho;
@@ -1007,7 +1012,7 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
                     double alpha, const double *A, long long lda, const double *B,
                     long long ldb, double beta, double *C, long long ldc) {
   return guarded([&] {
-    if (!A || !B || !C || M < 0 || N < 0 || K < 0 || precision < 0 || precision > 3)
+    if (!A || !B || !C || M < 0 || N < 0 || K < 0 || precision < 0 || precision > 6)
       throw Error(TRG_ERR_ARG, "bad gemm arguments");
     Ctx &c = ctx();
     ensure_ctx(c);
@@ -1018,6 +1023,10 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
     TRG_CUDA(cudaMemcpyAsync(dC.p, C, M * ldc * 8, cudaMemcpyHostToDevice, c.stream));
     if (precision == TRG_PREC_FP64) {
       gemm_f64(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1, c.stream);
+    } else if (precision >= TRG_PREC_OZ4) {
+      ArenaScratch scr(c.arena);
+      gemm_oz(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
+              precision, scr, c.stream);
     } else {
       ArenaScratch scr(c.arena);
       gemm_tc(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
@@ -1026,7 +1035,8 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
     TRG_CUDA(cudaMemcpyAsync(C, dC.p, M * ldc * 8, cudaMemcpyDeviceToHost, c.stream));
     TRG_CUDA(cudaStreamSynchronize(c.stream));
     c.arena.reset();
-    if (tc_error_flag(true)) throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+    if (tc_error_flag(true) | oz_error_flag(true))
+      throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
   });
 }
 
