@@ -114,7 +114,7 @@ __device__ __forceinline__ int exact_int(float v) {
   return __float_as_int(v + 12582912.0f) - 0x4B400000;
 }
 
-__global__ void __maxnreg__(200)
+__global__ void __maxnreg__(184)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const Params p) {
   constexpr uint32_t TILE = BM * BK * 2;    // 16 KB (A and B tiles are both 128 x 64)
