@@ -23,6 +23,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "gemm_oz.h"
@@ -500,6 +502,19 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSmem));
     attr = true;
+    if (getenv("TRG_DEBUG_ATTR")) {
+      const void *fns[4] = {(const void *)oz_gemm_kernel, (const void *)oz_rowexp_kernel,
+                            (const void *)oz_split_kernel, (const void *)oz_ws_reduce};
+      for (int i = 0; i < 4; ++i) {
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, fns[i]);
+        fprintf(stderr, "oz kernel %d: regs %d maxThreads %d static smem %zu max dyn smem %d local %zu\n",
+                i, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
+                fa.maxDynamicSharedSizeBytes, fa.localSizeBytes);
+      }
+      fprintf(stderr, "launch: grid %lld %lld %lld threads %d smem %zu params %zu\n", (long long)gx,
+              (long long)gy, (long long)(batch * ksplit), THREADS, kSmem, sizeof(Params));
+    }
   }
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
   if (timing) timing->before(s);
