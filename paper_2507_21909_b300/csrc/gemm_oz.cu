@@ -35,7 +35,9 @@ namespace oz {
 
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int CHUNK_KB = 4;                 // 4 x 64 = 256 K per exact chunk
-constexpr int NWARPS = 10, THREADS = NWARPS * 32;
+// 12 warps: registers are allocated in groups of four warps, so a 10-warp block costs
+// as much as 12; warps 10 and 11 only take part in the block-wide barriers
+constexpr int NWARPS = 12, THREADS = NWARPS * 32;
 constexpr int MAX_PAIRS = 36;
 constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 (power of two)
 
@@ -98,6 +100,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
 
+__device__ __forceinline__ void tld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void tld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -116,7 +128,7 @@ __device__ __forceinline__ int exact_int(float v) {
   return __float_as_int(v + 12582912.0f) - 0x4B400000;
 }
 
-__global__ void __maxnreg__(184)
+__global__ void __launch_bounds__(THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const Params p) {
   constexpr uint32_t TILE = BM * BK * 2;    // 16 KB (A and B tiles are both 128 x 64)
@@ -225,7 +237,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           : "memory");
       (void)h_started;
     }
-  } else {  // ------------------------------------------------------ drain warps 2..9
+  } else if (warp < 10) {  // ------------------------------------------ drain warps 2..9
     const int ew = warp - 2;                  // 0..7
     const int quad = warp & 3;                // TMEM lane quadrant of this warp
     const int half = ew >> 2;                 // columns [64 half, 64 half + 64)
@@ -239,17 +251,17 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // L0 and L1 always have pairs (ns >= 3): exact integers of this chunk into S
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        uint32_t r0[32], r1[32];
-        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64 + c * 32);
-        tld32(base, r0);
-        tld32(base + BN, r1);
+      for (int c = 0; c < 4; ++c) {
+        uint32_t r0[16], r1[16];
+        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64 + c * 16);
+        tld16(base, r0);
+        tld16(base + BN, r1);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < 16; ++j) {
           const int i0 = exact_int(__uint_as_float(r0[j]) * 0x1.0p-14f);
           const int i1 = exact_int(__uint_as_float(r1[j]) * 0x1.0p-7f);
-          S[c * 32 + j] += ((long long)i0 << 14) + ((long long)i1 << 7);
+          S[c * 16 + j] += ((long long)i0 << 14) + ((long long)i1 << 7);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -261,20 +273,20 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int64_t ldc = p.to_ws ? p.N : p.ldc;
     const int er = row < p.M ? p.ea[b * p.M + row] : 0;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      uint32_t r[32];
-      tld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN + half * 64 + c * 32), r);
+    for (int c = 0; c < 4; ++c) {
+      uint32_t r[16];
+      tld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN + half * 64 + c * 16), r);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < p.M) {
         double *crow = Cbase + row * ldc;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t col = n0 + half * 64 + c * 32 + j;
+        for (int j = 0; j < 16; ++j) {
+          const int64_t col = n0 + half * 64 + c * 16 + j;
           if (col >= p.N) continue;
           double v = 0.0;
           if (done) {
             const double h = (double)__uint_as_float(r[j]);
-            v = ldexp((double)S[c * 32 + j] + h, er + p.eb[b * p.N + col] - 28);
+            v = ldexp((double)S[c * 16 + j] + h, er + p.eb[b * p.N + col] - 28);
           }
           if (p.to_ws)
             crow[col] = v;
