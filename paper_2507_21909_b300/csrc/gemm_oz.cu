@@ -46,7 +46,7 @@ struct Params {
   int nkb;                                  // K blocks per split (multiple of CHUNK_KB)
   int npairs;
   int pi[MAX_PAIRS], pj[MAX_PAIRS], pl[MAX_PAIRS];  // slice of A, slice of B, level 0/1/2
-  const int *ea, *eb;                       // row exponents [batch][M], [batch][N]
+  const unsigned *ea, *eb;                  // row exponent codes [batch][M], [batch][N]
   double alpha, beta;
   double *C;
   int64_t ldc, sC;
@@ -122,6 +122,9 @@ __device__ __forceinline__ void tld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+
+// row exponent codes: e + 4096, 0 for an all-zero row
+__device__ __forceinline__ int decode_exp(unsigned code) { return code ? (int)code - 4096 : 0; }
 
 // exact integer of an FP32 value v with |v| <= 2^22 (v an integer)
 __device__ __forceinline__ int exact_int(float v) {
@@ -271,7 +274,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
     const int64_t ldc = p.to_ws ? p.N : p.ldc;
-    const int er = row < p.M ? p.ea[b * p.M + row] : 0;
+    const int er = row < p.M ? decode_exp(p.ea[b * p.M + row]) : 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint32_t r[16];
@@ -286,7 +289,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           double v = 0.0;
           if (done) {
             const double h = (double)__uint_as_float(r[j]);
-            v = ldexp((double)S[c * 16 + j] + h, er + p.eb[b * p.N + col] - 28);
+            v = ldexp((double)S[c * 16 + j] + h, er + decode_exp(p.eb[b * p.N + col]) - 28);
           }
           if (p.to_ws)
             crow[col] = v;
@@ -304,42 +307,51 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                  : "memory");
 }
 
-// common exponent of every row r of op(X): e with max_k |op(X)[r][k]| < 2^e (0 if zero)
+// common exponent of every row r of op(X): e with max_k |op(X)[r][k]| < 2^e, stored as
+// code = e + 4096 (0 for an all-zero row) and combined across blocks with atomicMax.
+// Tiles of 32 rows x 1024 k; the read is coalesced along whichever index is contiguous.
 __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
-                                 int64_t ld, int64_t sX, int trans, int64_t batch, int *e) {
-  const int64_t nr = rows * batch;
-  if (!trans) {  // one warp per row, contiguous along k
-    const int warps = blockDim.x >> 5;
-    for (int64_t g = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); g < nr;
-         g += (int64_t)gridDim.x * warps) {
-      const int64_t b = g / rows, r = g % rows;
-      const double *x = X + b * sX + r * ld;
-      double m = 0.0;
-      for (int64_t k = threadIdx.x & 31; k < K; k += 32) m = fmax(m, fabs(x[k]));
-      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((threadIdx.x & 31) == 0) {
-        int ex = 0;
-        if (m > 0.0) frexp(m, &ex);
-        e[g] = ex;
+                                 int64_t ld, int64_t sX, int trans, int64_t batch,
+                                 unsigned *__restrict__ code) {
+  constexpr int KT = 1024;
+  const int64_t rt = (rows + 31) / 32, kt = (K + KT - 1) / KT;
+  const int64_t ntiles = rt * kt * batch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
+    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * KT;
+    const int64_t k1 = min(K, k0 + KT);
+    const double *Xb = X + b * sX;
+    if (!trans) {  // warp per row, lanes along k
+      for (int i = warp; i < 32; i += nw) {
+        const int64_t r = r0 + i;
+        if (r >= rows) continue;
+        double m = 0.0;
+        for (int64_t k = k0 + lane; k < k1; k += 32) m = fmax(m, fabs(Xb[r * ld + k]));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m > 0.0) {
+          int ex;
+          frexp(m, &ex);
+          atomicMax(&code[b * rows + r], (unsigned)(ex + 4096));
+        }
       }
-    }
-  } else {  // op(X)[r][k] = X[k ld + r]: threads along r, loop over k
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nr;
-         g += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t b = g / rows, r = g % rows;
-      const double *x = X + b * sX + r;
+    } else {  // lanes along r (contiguous), warps split the k range
+      const int64_t r = r0 + lane;
       double m = 0.0;
-      for (int64_t k = 0; k < K; ++k) m = fmax(m, fabs(x[k * ld]));
-      int ex = 0;
-      if (m > 0.0) frexp(m, &ex);
-      e[g] = ex;
+      if (r < rows)
+        for (int64_t k = k0 + warp; k < k1; k += nw) m = fmax(m, fabs(Xb[k * ld + r]));
+      if (r < rows && m > 0.0) {
+        int ex;
+        frexp(m, &ex);
+        atomicMax(&code[b * rows + r], (unsigned)(ex + 4096));
+      }
     }
   }
 }
 
 // digits ^a_s = d_s 2^(-7(s-1)) of op(X) rows, layout [slice][batch][rows][Kp] (K-major)
 __global__ void oz_split_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
-                                int64_t ld, int64_t sX, int trans, int ns, const int *e,
+                                int64_t ld, int64_t sX, int trans, int ns, const unsigned *e,
                                 __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
   __shared__ double tile[32][33];
   const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
@@ -366,7 +378,7 @@ __global__ void oz_split_kernel(const double *__restrict__ X, int64_t rows, int6
     for (int i = ty; i < 32; i += 8) {
       const int64_t r = r0 + i, k = k0 + tx;
       if (r >= rows || k >= Kp) continue;
-      double a = ldexp(tile[i][tx], -e[b * rows + r]);  // |a| < 1
+      double a = ldexp(tile[i][tx], -decode_exp(e[b * rows + r]));  // |a| < 1
       for (int s = 0; s < ns; ++s) {
         const double d = rint(ldexp(a, 7 * (s + 1)));   // integer digit
         a -= ldexp(d, -7 * (s + 1));                     // exact
@@ -444,16 +456,20 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   if (ns < 3 || ns > 6) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 6");
   if (batch > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: batch too large");
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
-  int *ea = (int *)scr.alloc((size_t)batch * M * sizeof(int));
-  int *eb = (int *)scr.alloc((size_t)batch * N * sizeof(int));
+  unsigned *ea = (unsigned *)scr.alloc((size_t)batch * M * sizeof(unsigned));
+  unsigned *eb = (unsigned *)scr.alloc((size_t)batch * N * sizeof(unsigned));
+  TRG_CUDA(cudaMemsetAsync(ea, 0, (size_t)batch * M * sizeof(unsigned), s));
+  TRG_CUDA(cudaMemsetAsync(eb, 0, (size_t)batch * N * sizeof(unsigned), s));
   __nv_bfloat16 *As = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * M * Kp * 2);
   __nv_bfloat16 *Bs = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * N * Kp * 2);
   {
-    const int blk = 256;
-    auto g1 = [&](int64_t rows) { return (unsigned)std::min<int64_t>((rows * batch + 7) / 8 + 1, 148 * 64); };
-    oz_rowexp_kernel<<<g1(M), blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, batch, ea);
+    auto g1 = [&](int64_t rows) {
+      int64_t t = ((rows + 31) / 32) * ((K + 1023) / 1024) * batch;
+      return (unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32);
+    };
+    oz_rowexp_kernel<<<g1(M), 256, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, batch, ea);
     TRG_LAUNCH_CHECK();
-    oz_rowexp_kernel<<<g1(N), blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, batch, eb);
+    oz_rowexp_kernel<<<g1(N), 256, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, batch, eb);
     TRG_LAUNCH_CHECK();
     dim3 b2(32, 8);
     auto nblk = [&](int64_t rows) {

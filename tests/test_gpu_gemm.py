@@ -3,7 +3,8 @@
 Error measure: max |C - A B| / max (|A| |B|) (the elementwise bound of a dot product).
 FP64 CUDA-core GEMM: 1e-14.  Split-BF16 tcgen05 GEMM with FP32 accumulation:
 2 slices (3 products) < 1e-4, 3 slices (6 products) < 2e-6, 4 slices (10) < 2e-6;
-the 3/4-slice bound is the FP32 accumulation, not the operand split.
+the 3/4-slice bound is the FP32 accumulation, not the operand split.  Exact-accumulation
+digit GEMM (row exponents, 7-bit digits): 4 digits < 1e-7, 5 and 6 digits < 5e-9.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(128, 256, 64, False, False), (300, 200, 1000, False, False),
           (64, 48, 5000, True, False), (1000, 130, 70, False, True),
           (257, 129, 333, True, True), (2048, 512, 4096, False, False)]
-BOUND = {0: 1e-14, 1: 1e-4, 2: 2e-6, 3: 2e-6}
+BOUND = {0: 1e-14, 1: 1e-4, 2: 2e-6, 3: 2e-6, 4: 1e-7, 5: 5e-9, 6: 5e-9}
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +23,7 @@ def trg(require_gpu):
     return pkg
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("M,N,K,ta,tb", SHAPES)
 def test_gemm_against_numpy(trg, prec, M, N, K, ta, tb):
     rng = np.random.default_rng(M * 7 + N * 3 + K)
@@ -38,12 +39,14 @@ def test_gemm_against_numpy(trg, prec, M, N, K, ta, tb):
     assert err < BOUND[prec], err
 
 
-def test_gemm_scaled_rows(trg):
-    """Rows spanning 12 orders of magnitude (per-element BF16 exponents handle them)."""
+@pytest.mark.parametrize("prec,bound", [(2, 2e-6), (5, 5e-9)])
+def test_gemm_scaled_rows(trg, prec, bound):
+    """Rows spanning 12 orders of magnitude: per-element BF16 exponents (split modes) and
+    per-row exponents (digit modes) both keep every row's relative accuracy."""
     rng = np.random.default_rng(5)
     A = rng.standard_normal((256, 512)) * np.logspace(-6, 6, 256)[:, None]
     B = rng.standard_normal((512, 384))
-    got = trg.trg_gemm(A, B, precision=2)
+    got = trg.trg_gemm(A, B, precision=prec)
     ref = A @ B
     rel = np.abs(got - ref).max(axis=1) / (np.abs(A) @ np.abs(B)).max(axis=1)
-    assert rel.max() < 2e-6
+    assert rel.max() < bound

@@ -123,6 +123,21 @@ def test_per_step_parity_from_oracle_state(trg):
     assert np.allclose(s_gpu, s_ref, rtol=1e-10, atol=1e-13 * s_ref[0])
 
 
+def test_mixed_form_oz5_within_1e8_of_oracle(trg):
+    """The exact-accumulation mixed form (5 digits, tensor cores from the fourth step) keeps
+    the free energy within 1e-8 relative of the FP64 oracle (16 steps, D=16, p=2D)."""
+    beta, D, N = 0.1497, 16, 16
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_OZ5)
+    trg.trg_init_ising(4, beta, 0.0)
+    for n in range(N):
+        trg.trg_step(n % 4, D, 2 * D)
+    f_gpu, _ = trg.trg_free_energy()
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
+    st = O.run("ising", 4, beta, 0.0, D=D, p=2 * D, nsteps=N, q_swap=4, q_rho=4)
+    f_ref, _ = O.free_energy(st)
+    assert abs(f_gpu - f_ref) < 1e-8 * abs(f_ref)
+
+
 def test_errors_are_reported(trg):
     with pytest.raises(trg.TrgError) as e:
         trg.trg_init_ising(3, 0.1, 0.0)
