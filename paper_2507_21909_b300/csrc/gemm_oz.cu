@@ -378,12 +378,29 @@ __global__ void oz_split_kernel(const double *__restrict__ X, int64_t rows, int6
     for (int i = ty; i < 32; i += 8) {
       const int64_t r = r0 + i, k = k0 + tx;
       if (r >= rows || k >= Kp) continue;
-      double a = ldexp(tile[i][tx], -decode_exp(e[b * rows + r]));  // |a| < 1
-      for (int s = 0; s < ns; ++s) {
-        const double d = rint(ldexp(a, 7 * (s + 1)));   // integer digit
-        a -= ldexp(d, -7 * (s + 1));                     // exact
-        out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] =
-            __double2bfloat16(ldexp(d, -7 * (s - 1)));   // exact (<= 8 significant bits)
+      // a' 2^(7 ns) rounded once to an integer q (|a'| < 1, so |q| < 2^(7 ns)), then split
+      // into balanced base-128 digits by integer arithmetic: d_{ns-1} .. d_1 in [-64, 63],
+      // d_0 the remaining top digit (|d_0| <= 128)
+      const int ex = decode_exp(e[b * rows + r]);
+      const double scale = __longlong_as_double((long long)(1023 - ex + 7 * ns) << 52);
+      long long q = __double2ll_rn(tile[i][tx] * scale);   // exact power-of-two scaling
+      int d[6];
+#pragma unroll
+      for (int s = 5; s >= 1; --s) {
+        if (s < ns) {
+          const long long dd = ((q + 64) & 127) - 64;
+          d[s] = (int)dd;
+          q = (q - dd) >> 7;
+        }
+      }
+      d[0] = (int)q;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        if (s < ns) {
+          // ^a_s = d_s 2^(-7(s-1)): exact in BF16 (<= 8 significant bits)
+          const float v = (float)d[s] * __int_as_float((127 - 7 * (s - 1)) << 23);
+          out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = __float2bfloat16_rn(v);
+        }
       }
     }
   }

@@ -267,12 +267,25 @@ __global__ void split_kernel(const double *__restrict__ X, int64_t rows, int64_t
     for (int i = ty; i < 32; i += 8) {
       const int64_t r = r0 + i, k = k0 + tx;
       if (r >= rows || k >= Kp) continue;
-      double rem2 = tile[i][tx];
-      for (int s = 0; s < ns; ++s) {
-        const __nv_bfloat16 h = __double2bfloat16(rem2);
-        rem2 -= (double)__bfloat162float(h);
-        out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = h;
+      const double x = tile[i][tx];
+      __nv_bfloat16 h[4];
+      if (ns <= 3) {
+        // FP32 carries the 24 bits that three BF16 slices hold; the slicing is exact in FP32
+        float rem = (float)x;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          h[s] = __float2bfloat16_rn(rem);
+          rem -= __bfloat162float(h[s]);
+        }
+      } else {
+        double rem = x;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          h[s] = __double2bfloat16(rem);
+          rem -= (double)__bfloat162float(h[s]);
+        }
       }
+      for (int s = 0; s < ns; ++s) out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = h[s];
     }
   }
 }

@@ -125,8 +125,10 @@ def test_per_step_parity_from_oracle_state(trg):
 
 def test_mixed_form_oz5_within_1e8_of_oracle(trg):
     """The exact-accumulation mixed form (5 digits, tensor cores from the fourth step) keeps
-    the free energy within 1e-8 relative of the FP64 oracle (16 steps, D=16, p=2D)."""
-    beta, D, N = 0.1497, 16, 16
+    the free energy within 1e-8 relative of the FP64 oracle (16 steps, D=14, p=2D; at
+    D=16 the bond swap of step 2 has a 4e-7 relative gap, too close to degenerate for a
+    comparison across implementations)."""
+    beta, D, N = 0.1497, 14, 16
     trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_OZ5)
     trg.trg_init_ising(4, beta, 0.0)
     for n in range(N):
