@@ -45,6 +45,8 @@ struct Ctx {
   int crit_depth = 0;          // > 0 inside decompositions (QR, re-split, squeezer roots)
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
   unsigned phase_mask = 0xFFu; // phases whose GEMMs may use the tensor cores
+  int bulk_cheap = 0;          // > 0: range-finder / impurity products (see gemm())
+  bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
   static constexpr int kPhases = 8;
@@ -122,6 +124,12 @@ static int64_t prod(const std::vector<int64_t> &d, size_t a = 0, size_t b = SIZE
 }
 
 // ------------------------------------------------------------------ GEMM dispatch
+struct Cheap {  // marks products that steer a range finder or feed only the impurity
+  Ctx &c;
+  explicit Cheap(Ctx &cc) : c(cc) { if (c.cheap_policy) ++c.bulk_cheap; }
+  ~Cheap() { if (c.cheap_policy) --c.bulk_cheap; }
+};
+
 struct Crit {  // marks a decomposition: its GEMMs may be routed to FP64
   Ctx &c;
   explicit Crit(Ctx &cc) : c(cc) { ++c.crit_depth; }
@@ -146,16 +154,18 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
-      work >= (double)(1 << 24) &&
-      M >= 64 && N >= 16 && K >= 64) {
+      work >= (double)(1 << 22) && std::max(M, N) >= 64 && std::min(M, N) >= 16 && K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
-    if (c.precision >= TRG_PREC_OZ4)
+    // exact-digit forms: products that only steer a range finder, or feed the impurity
+    // (not the free energy), run as 6-term BF16 splits
+    const bool cheap = c.precision >= TRG_PREC_OZ4 && c.bulk_cheap > 0 && c.crit_depth == 0;
+    if (c.precision >= TRG_PREC_OZ4 && !cheap)
       gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
               c.precision, scr, c.stream, &c.timing);
     else
       gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-              slices_of(c.precision), scr, c.stream, &c.timing);
+              cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing);
     c.arena.release(mk);
   } else {
     gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream);
@@ -535,17 +545,28 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   for (int rnd = 0; rnd < c.q_swap; ++rnd) {
     Arena::Mark mk = c.arena.mark();
     Tensor Y = c.alloc({I * k, w});
-    applyM(V, Y);
-    Tensor Qn = orth_sc(c, Y);
+    {
+      Cheap ch(c);
+      applyM(V, Y);
+    }
+    Tensor Qn;
+    if (rnd + 1 < c.q_swap) {
+      Cheap ch(c);
+      Qn = orth_sc(c, Y);
+    } else {  // the core projection Q^T M needs Q orthonormal to full accuracy
+      Qn = orth_sc(c, Y);
+    }
     TRG_CUDA(cudaMemcpyAsync(Q.p, Qn.p, Q.size() * 8, cudaMemcpyDeviceToDevice, s));
     c.arena.release(mk);
     if (rnd + 1 == c.q_swap) {
       Crit cr(c);  // the last application feeds the core SVD
       applyMt(Q, Yt);
     } else {
+      Cheap ch(c);
       applyMt(Q, Yt);
     }
     if (rnd + 1 < c.q_swap) {
+      Cheap ch(c);
       Arena::Mark mk2 = c.arena.mark();
       Tensor Vn = orth_sc(c, Yt);
       TRG_CUDA(cudaMemcpyAsync(V.p, Vn.p, V.size() * 8, cudaMemcpyDeviceToDevice, s));
@@ -668,6 +689,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   c.mark(6);
   Tensor PsiImpN;
   if (c.have_imp) {
+    Cheap ch(c);
     // impurity at slot n+1: B_imp = T_imp^T A; frozen X projector -> Y_imp = M_imp^T X / sigma
     Tensor PA = mm(c, view(c.phi, {Nf, r}), view(A.p, {Nf, k}), true, false);
     Tensor Bimp = mm(c, view(c.psi_imp, {Nf, r}), PA, false, false);
@@ -725,6 +747,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
 static void ensure_ctx(Ctx &c) {
   if (const char *e = getenv("TRG_DECOMP_FP64")) c.crit_fp64 = e[0] == '1';
   if (const char *e = getenv("TRG_TC_PHASES")) c.phase_mask = (unsigned)strtoul(e, nullptr, 0);
+  if (const char *e = getenv("TRG_EXACT_EVERYWHERE")) c.cheap_policy = e[0] != '1';
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
