@@ -124,7 +124,7 @@ static int64_t prod(const std::vector<int64_t> &d, size_t a = 0, size_t b = SIZE
 }
 
 // ------------------------------------------------------------------ GEMM dispatch
-struct Cheap {  // marks products that steer a range finder or feed only the impurity
+struct Cheap {  // marks products that feed only the impurity
   Ctx &c;
   explicit Cheap(Ctx &cc) : c(cc) { if (c.cheap_policy) ++c.bulk_cheap; }
   ~Cheap() { if (c.cheap_policy) --c.bulk_cheap; }
@@ -154,11 +154,12 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
-      work >= (double)(1 << 22) && std::max(M, N) >= 64 && std::min(M, N) >= 16 && K >= 64) {
+      work >= (double)(1 << 22) && std::min(M, N) >= 16 && K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
-    // exact-digit forms: products that only steer a range finder, or feed the impurity
-    // (not the free energy), run as 6-term BF16 splits
+    // exact-digit forms: products that feed only the impurity (not the free energy) run
+    // as 6-term BF16 splits (the bond-swap range finder stays exact: with q_swap = 4
+    // rounds its range depends on the iterates at first order)
     const bool cheap = c.precision >= TRG_PREC_OZ4 && c.bulk_cheap > 0 && c.crit_depth == 0;
     if (c.precision >= TRG_PREC_OZ4 && !cheap)
       gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
@@ -545,28 +546,17 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   for (int rnd = 0; rnd < c.q_swap; ++rnd) {
     Arena::Mark mk = c.arena.mark();
     Tensor Y = c.alloc({I * k, w});
-    {
-      Cheap ch(c);
-      applyM(V, Y);
-    }
-    Tensor Qn;
-    if (rnd + 1 < c.q_swap) {
-      Cheap ch(c);
-      Qn = orth_sc(c, Y);
-    } else {  // the core projection Q^T M needs Q orthonormal to full accuracy
-      Qn = orth_sc(c, Y);
-    }
+    applyM(V, Y);
+    Tensor Qn = orth_sc(c, Y);
     TRG_CUDA(cudaMemcpyAsync(Q.p, Qn.p, Q.size() * 8, cudaMemcpyDeviceToDevice, s));
     c.arena.release(mk);
     if (rnd + 1 == c.q_swap) {
       Crit cr(c);  // the last application feeds the core SVD
       applyMt(Q, Yt);
     } else {
-      Cheap ch(c);
       applyMt(Q, Yt);
     }
     if (rnd + 1 < c.q_swap) {
-      Cheap ch(c);
       Arena::Mark mk2 = c.arena.mark();
       Tensor Vn = orth_sc(c, Yt);
       TRG_CUDA(cudaMemcpyAsync(V.p, Vn.p, V.size() * 8, cudaMemcpyDeviceToDevice, s));
