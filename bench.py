@@ -8,8 +8,10 @@ from the Boltzmann-weight initial tensor by the method itself (untimed), then W 
 and K timed steps continue the RG flow.  Inputs (D^5 factors, 2 GB each in FP64) are
 far larger than the 126 MB L2, so no flush is needed between steps.
 
-Default: the mixed form (bulk GEMMs as 6-term split-BF16 tcgen05 products).  Prints one
-JSON line.  Under torchrun every rank runs an independent replica (the method does not
+Default: the mixed form "oz5": every bulk GEMM runs on the tcgen05 tensor cores as exact
+products of 5 seven-bit digits per row (15 BF16 products, exact FP32 chunks summed in
+int64), FP64 for the small decompositions and the log-norm sum; it keeps ΔF/F <= 1e-8.
+Prints one JSON line.  Under torchrun every rank runs an independent replica (the method does not
 shard; "replicas only") and rank 0 prints the whole-job value.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample
@@ -28,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "triad-ATRG RG steps/s at D=48 4D Ising (mixed vs FP64 form, ΔF/F ≤1e-8)"
-PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "bf16x10": 3}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "bf16x10": 3, "oz4": 4, "oz5": 5, "oz6": 6}
 
 
 def args_():
@@ -38,7 +40,9 @@ def args_():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=48)
-    ap.add_argument("--precision", default="bf16x6", choices=list(PREC))
+    ap.add_argument("--precision", default="oz5", choices=list(PREC))
+    ap.add_argument("--fp64-form-steps", type=int, default=0,
+                    help="also time this many steady-state steps of the FP64 form (slow)")
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-check", action="store_true")
@@ -158,17 +162,47 @@ def peaks():
         return 1400.0, "fallback (sustained bf16 estimate)"
 
 
-def precision_check(trg, prec, D=16, nsteps=12):
-    """ΔF/F of the mixed form against the FP64 form of this library at a size where the
-    FP64 form is quick (the FP64 form itself matches the CPU oracle to 1e-10)."""
-    out = {}
-    for p in (0, prec):
-        trg.trg_set_params(4, 4, 0x5EED, p)
-        trg.trg_init_ising(4, 0.1497, 0.0)
-        for n in range(nsteps):
-            trg.trg_step(n % 4, D, 2 * D)
-        out[p] = trg.trg_free_energy()[0]
-    return abs(out[prec] - out[0]) / abs(out[0])
+def run_f(trg, prec, D, nsteps):
+    trg.trg_set_params(4, 4, 0x5EED, prec)
+    trg.trg_init_ising(4, 0.1497, 0.0)
+    for n in range(nsteps):
+        trg.trg_step(n % 4, D, 2 * D)
+    return trg.trg_free_energy()[0]
+
+
+def precision_check(trg, prec):
+    """ΔF/F of the mixed form: against the FP64 CPU oracle at D=14 (16 steps; no
+    near-degenerate truncation there) and against this library's FP64 form at D=24
+    (12 steps; the FP64 form matches the oracle to 1e-10)."""
+    from oracle import trg_oracle as O
+    st = O.run("ising", 4, 0.1497, 0.0, D=14, p=28, nsteps=16, q_swap=4, q_rho=4)
+    f_or = O.free_energy(st)[0]
+    f14 = run_f(trg, prec, 14, 16)
+    f24_64 = run_f(trg, 0, 24, 12)
+    f24 = run_f(trg, prec, 24, 12)
+    return {"vs_oracle_D14_16steps": abs(f14 - f_or) / abs(f_or),
+            "vs_fp64_form_D24_12steps": abs(f24 - f24_64) / abs(f24_64)}
+
+
+def fp64_form_rate(trg, D, nsteps, beta):
+    """Steady-state steps/s of the FP64 form (every GEMM on the FP64 CUDA cores)."""
+    import torch
+    trg.trg_set_params(4, 4, 0x5EED, 0)
+    trg.trg_init_ising(4, beta, 0.0)
+    n = 0
+    while n < 12:
+        trg.trg_step(n % 4, D, 2 * D)
+        n += 1
+        dims = trg.trg_state_dims(0)
+        if all(x == D for x in dims) and n >= 4:
+            break
+    torch.cuda.synchronize()
+    t = time.time()
+    for _ in range(nsteps):
+        trg.trg_step(n % 4, D, 2 * D)
+        n += 1
+    torch.cuda.synchronize()
+    return nsteps / (time.time() - t)
 
 
 def run_ours(a):
@@ -246,7 +280,8 @@ def run_ours(a):
     achieved = stats["tc_flop"] / (stats["tc_ms"] / 1e3) / 1e12 if stats["tc_ms"] > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-            "kernel": "tc_gemm_kernel (split-BF16 tcgen05 GEMM)",
+            "kernel": "tcgen05 GEMMs (oz_gemm_kernel digit products, tc_gemm_kernel BF16 splits); "
+                      "flop = BF16 tensor work of every slice/digit product",
             "tc_launches": stats["tc_launches"], "tc_ms_per_step": stats["tc_ms"] / a.steps,
             "tc_share_of_step": stats["tc_ms"] / ms}
     line = {
@@ -267,7 +302,11 @@ def run_ours(a):
         "free_energy": f_last[0],
     }
     if not a.no_precision_check and prec != 0:
-        line["delta_f_rel_vs_fp64_form_D16"] = precision_check(trg, prec)
+        line["delta_f_rel"] = precision_check(trg, prec)
+    if a.fp64_form_steps > 0:
+        r = fp64_form_rate(trg, D, a.fp64_form_steps, a.beta)
+        line["fp64_form"] = {"value": r, "unit": "RG steps/s", "steps": a.fp64_form_steps,
+                             "speedup_of_value": value / r}
     if not a.no_cpu_baseline:
         v, times, cores = oracle_sample(D)
         line["cpu_baseline"] = {
