@@ -46,6 +46,7 @@ struct Ctx {
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
   unsigned phase_mask = 0xFFu; // phases whose GEMMs may use the tensor cores
   int bulk_cheap = 0;          // > 0: range-finder / impurity products (see gemm())
+  int64_t tc_min_mn = 16, tc_min_max = 16;  // smallest GEMM sides sent to the tensor cores
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
@@ -154,7 +155,8 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
-      work >= (double)(1 << 22) && std::min(M, N) >= 16 && K >= 64) {
+      work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
+      K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     // exact-digit forms: products that feed only the impurity (not the free energy) run
@@ -738,6 +740,7 @@ static void ensure_ctx(Ctx &c) {
   if (const char *e = getenv("TRG_DECOMP_FP64")) c.crit_fp64 = e[0] == '1';
   if (const char *e = getenv("TRG_TC_PHASES")) c.phase_mask = (unsigned)strtoul(e, nullptr, 0);
   if (const char *e = getenv("TRG_EXACT_EVERYWHERE")) c.cheap_policy = e[0] != '1';
+  if (const char *e = getenv("TRG_TC_MIN_MAX")) c.tc_min_max = atoll(e);
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
