@@ -46,7 +46,10 @@ struct Ctx {
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
   unsigned phase_mask = 0xFFu; // phases whose GEMMs may use the tensor cores
   int bulk_cheap = 0;          // > 0: range-finder / impurity products (see gemm())
-  int64_t tc_min_mn = 16, tc_min_max = 16;  // smallest GEMM sides sent to the tensor cores
+  // smallest GEMM sides sent to the tensor cores: thin products (max side < 64, e.g. the
+  // re-split Grams and Q R^-1 with a 48-column R) stay FP64, because a per-column
+  // exponent cannot hold the dynamic range of a triangular inverse
+  int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
