@@ -473,12 +473,14 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   if (ns < 3 || ns > 6) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 6");
   if (batch > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: batch too large");
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
+  // a Gram op(A) = X^T, op(B) = X of one matrix X has identical digit planes
+  const bool gram = A == B && ta && !tb && M == N && lda == ldb && sA == sB;
   unsigned *ea = (unsigned *)scr.alloc((size_t)batch * M * sizeof(unsigned));
-  unsigned *eb = (unsigned *)scr.alloc((size_t)batch * N * sizeof(unsigned));
+  unsigned *eb = gram ? ea : (unsigned *)scr.alloc((size_t)batch * N * sizeof(unsigned));
   TRG_CUDA(cudaMemsetAsync(ea, 0, (size_t)batch * M * sizeof(unsigned), s));
-  TRG_CUDA(cudaMemsetAsync(eb, 0, (size_t)batch * N * sizeof(unsigned), s));
+  if (!gram) TRG_CUDA(cudaMemsetAsync(eb, 0, (size_t)batch * N * sizeof(unsigned), s));
   __nv_bfloat16 *As = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * M * Kp * 2);
-  __nv_bfloat16 *Bs = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * N * Kp * 2);
+  __nv_bfloat16 *Bs = gram ? As : (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * N * Kp * 2);
   {
     auto g1 = [&](int64_t rows) {
       int64_t t = ((rows + 31) / 32) * ((K + 1023) / 1024) * batch;
@@ -486,8 +488,10 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     };
     oz_rowexp_kernel<<<g1(M), 256, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, batch, ea);
     TRG_LAUNCH_CHECK();
-    oz_rowexp_kernel<<<g1(N), 256, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, batch, eb);
-    TRG_LAUNCH_CHECK();
+    if (!gram) {
+      oz_rowexp_kernel<<<g1(N), 256, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, batch, eb);
+      TRG_LAUNCH_CHECK();
+    }
     dim3 b2(32, 8);
     auto nblk = [&](int64_t rows) {
       int64_t t = ((rows + 31) / 32) * ((Kp + 31) / 32) * batch;
@@ -495,8 +499,10 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     };
     oz_split_kernel<<<nblk(M), b2, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, ea, As, Kp, batch);
     TRG_LAUNCH_CHECK();
-    oz_split_kernel<<<nblk(N), b2, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, eb, Bs, Kp, batch);
-    TRG_LAUNCH_CHECK();
+    if (!gram) {
+      oz_split_kernel<<<nblk(N), b2, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, eb, Bs, Kp, batch);
+      TRG_LAUNCH_CHECK();
+    }
   }
   Params p{};
   p.M = M;
