@@ -46,11 +46,10 @@ struct Ctx {
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
   unsigned phase_mask = 0xFFu; // phases whose GEMMs may use the tensor cores
   int bulk_cheap = 0;          // > 0: range-finder / impurity products (see gemm())
-  int wide_range = 0;          // > 0: an operand is a triangular inverse (keep FP64 if thin)
-  // smallest GEMM sides sent to the tensor cores.  Thin products with a triangular
-  // inverse (Q R^-1 with a 48-column R) stay FP64: a per-column exponent cannot hold
-  // the dynamic range of R^-1's columns; thin Grams are fine on the digit path.
-  int64_t tc_min_mn = 16, tc_min_max = 16, tc_min_max_wide = 64;
+  // smallest GEMM sides sent to the tensor cores: thin products (max side < 64, e.g. the
+  // re-split Grams and Q R^-1 with a 48-column R) stay FP64, because a per-column
+  // exponent cannot hold the dynamic range of a triangular inverse
+  int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
@@ -159,8 +158,8 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
-      work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn &&
-      std::max(M, N) >= (c.wide_range ? c.tc_min_max_wide : c.tc_min_max) && K >= 64) {
+      work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
+      K >= 64) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     // exact-digit forms: products that feed only the impurity (not the free energy) run
@@ -316,13 +315,11 @@ static Tensor orth_sc(Ctx &c, const Tensor &Y) {
     Tensor R = c.alloc({w, w}), Ri = c.alloc({w, w});
     chol_rinv(G.p, R.p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
               pass == 0 ? kShiftRel : 0.0, c.stream);
-    ++c.wide_range;
     if (pass == 2) {
       gemm(c, false, false, Q.dims[0], w, w, 1.0, Q.p, w, 0, Ri.p, w, 0, 0.0, out.p, w, 0, 1);
     } else {
       Q = mm(c, Q, Ri, false, false);
     }
-    --c.wide_range;
   }
   c.arena.release(mk);
   return out;
@@ -747,7 +744,6 @@ static void ensure_ctx(Ctx &c) {
   if (const char *e = getenv("TRG_TC_PHASES")) c.phase_mask = (unsigned)strtoul(e, nullptr, 0);
   if (const char *e = getenv("TRG_EXACT_EVERYWHERE")) c.cheap_policy = e[0] != '1';
   if (const char *e = getenv("TRG_TC_MIN_MAX")) c.tc_min_max = atoll(e);
-  if (const char *e = getenv("TRG_TC_MIN_MAX_WIDE")) c.tc_min_max_wide = atoll(e);
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
