@@ -473,8 +473,8 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   if (ns < 3 || ns > 6) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 6");
   if (batch > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: batch too large");
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
-  // a Gram op(A) = X^T, op(B) = X of one matrix X has identical digit planes
-  const bool gram = A == B && ta && !tb && M == N && lda == ldb && sA == sB;
+  // a Gram (op(A) = X^T, op(B) = X, or op(A) = X, op(B) = X^T) has identical digit planes
+  const bool gram = A == B && ta != tb && M == N && lda == ldb && sA == sB;
   unsigned *ea = (unsigned *)scr.alloc((size_t)batch * M * sizeof(unsigned));
   unsigned *eb = gram ? ea : (unsigned *)scr.alloc((size_t)batch * N * sizeof(unsigned));
   TRG_CUDA(cudaMemsetAsync(ea, 0, (size_t)batch * M * sizeof(unsigned), s));

@@ -84,8 +84,11 @@ void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, doubl
 }
 
 // ------------------------------------------------------------ one-sided Jacobi
-constexpr int kSvdThreads = 512;
+constexpr int kSvdThreads = 1024;
 constexpr int kMaxSweeps = 80;
+// the working columns live in shared memory when they fit (n m doubles); otherwise in
+// the global work buffer
+constexpr size_t kSvdSmemMax = 200 * 1024;
 
 __device__ inline double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -94,11 +97,13 @@ __device__ inline double wsum(double v) {
 
 __global__ void __launch_bounds__(kSvdThreads)
 svd_jacobi_kernel(const double *A, int m, int n, double *U, double *S, double *V,
-                  double *work, int *info) {
+                  double *work, int *info, int in_smem) {
+  extern __shared__ double s_cols[];
   const int64_t b = blockIdx.x;
   const double *a = A + b * (int64_t)m * n;
-  double *at = work + b * ((int64_t)n * m + (int64_t)n * n);  // n rows of length m
-  double *vt = at + (int64_t)n * m;                             // n rows of length n
+  double *wb = work + b * ((int64_t)n * m + (int64_t)n * n);
+  double *at = in_smem ? s_cols : wb;  // n rows of length m
+  double *vt = wb + (int64_t)n * m;    // n rows of length n
   __shared__ int s_rot;
   __shared__ int s_sweeps;
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * m; idx += blockDim.x) {
@@ -193,7 +198,16 @@ void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, 
   if (n == 0 || batch == 0) return;
   if (m < n) throw Error(TRG_ERR_ARG, "svd_jacobi needs m >= n");
   if (n > 1024) throw Error(TRG_ERR_ARG, "svd_jacobi: n > 1024");
-  svd_jacobi_kernel<<<batch, kSvdThreads, 0, s>>>(A, m, n, U, S, V, work, info);
+  static bool attr_set = false;
+  if (!attr_set) {
+    TRG_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSvdSmemMax));
+    attr_set = true;
+  }
+  const size_t bytes = (size_t)n * m * sizeof(double);
+  const int in_smem = bytes <= kSvdSmemMax;
+  svd_jacobi_kernel<<<batch, kSvdThreads, in_smem ? bytes : 0, s>>>(A, m, n, U, S, V, work, info,
+                                                                     in_smem);
   TRG_LAUNCH_CHECK();
 }
 

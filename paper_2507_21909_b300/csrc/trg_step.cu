@@ -159,7 +159,7 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
       work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
-      K >= 64) {
+      K >= 16) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     // exact-digit forms: products that feed only the impurity (not the free energy) run
@@ -341,8 +341,16 @@ static Svd svd_small(Ctx &c, const Tensor &A) {
   r.U = c.alloc({m, n});
   r.S = c.alloc({n});
   r.V = c.alloc({n, n});
-  Tensor work = c.alloc({n * m + n * n});
-  svd_jacobi(A.p, (int)m, (int)n, r.U.p, r.S.p, r.V.p, 1, work.p, nullptr, c.stream);
+  Tensor work = c.alloc({n * m + n * n + 1});
+  static const bool dbg = getenv("TRG_DEBUG_SVD") != nullptr;
+  int *info = dbg ? reinterpret_cast<int *>(work.p + n * m + n * n) : nullptr;
+  svd_jacobi(A.p, (int)m, (int)n, r.U.p, r.S.p, r.V.p, 1, work.p, info, c.stream);
+  if (dbg) {
+    int sweeps = 0;
+    TRG_CUDA(cudaMemcpyAsync(&sweeps, info, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    fprintf(stderr, "svd_jacobi %lld x %lld: %d sweeps\n", (long long)m, (long long)n, sweeps);
+  }
   return r;
 }
 
@@ -506,76 +514,125 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   crit_resplit.reset();
 
   c.mark(1);
-  // (b) bond swap: sum_x B[x J al] C[x I be] ~ X sigma Y  (Appendix A), applied to the
-  //     uncompressed M; identical in exact arithmetic to the QR-compressed M'.
+  // (b) bond swap: M[(I al),(J be)] = sum_x C[x I be] B[x J al] ~ X sigma Y (Appendix A).
+  //     The randomized SVD of M runs in the compressed space of Appendix A, written in
+  //     Gram coordinates: a left vector is Y = (C (x) 1) Y' and a right vector
+  //     V = (B (x) 1) W, so that with G^C = C^T C and G^B = B^T B (D^2 x D^2, the QR
+  //     compression's R^T R)
+  //         M V  = (C (x) 1) P (G^B W),        M^T Q = (B (x) 1) P (G^C Q'),
+  //         Y^T Y = Y'^T (G^C (x) 1) Y',        V^T V = W^T (G^B (x) 1) W,
+  //     with P the swap of the two bond legs.  Only the two Grams and the final
+  //     X = (C (x) 1) X', Y = (B (x) 1) Y' cost D^7; the power rounds cost D^6.
   Tensor C = copy(c, A), B = copy(c, Dm);
   scale_last(c, C, sv);
   scale_last(c, B, sv);
   const int64_t x = d1, I = d2 * d3 * d4, J = I;
   const int64_t w = std::min<int64_t>(D + p, k * I);
-  Tensor g1 = c.alloc({k, w}), g2 = c.alloc({J, w}), Om = c.alloc({J * k, w});
-  fill_gaussian(g1.p, k, w, key(TAG_SWAP_G1), s);
-  fill_gaussian(g2.p, J, w, key(TAG_SWAP_G2), s);
-  khatri_rao(g2.p, g1.p, Om.p, J, k, w, s);
+  const int64_t xk = x * k, rows = x * k * k;     // coordinate rows (x, leg, leg)
   const int64_t Dg = std::min<int64_t>(D, w);
   Tensor X = c.alloc({k, d2, d3, d4, Dg}), Y = c.alloc({k, d2, d3, d4, Dg});
   Tensor sigT = c.alloc({w});
   double *sig = sigT.p;
   Arena::Mark mk_swap = c.arena.mark();
-  Tensor Cp = permuted(c, view(C.p, {x, I, k}), {1, 0, 2});   // (I, x, be)
-  Tensor Bp = permuted(c, view(B.p, {x, J, k}), {1, 0, 2});   // (J, x, al)
   Tensor Cq = permuted(c, view(C.p, {x, I, k}), {0, 2, 1});   // (x, be, I)
   Tensor Bq = permuted(c, view(B.p, {x, J, k}), {0, 2, 1});   // (x, al, J)
-  // Y[(I al), m] = sum_{x be} C[x I be] (sum_J B[x J al] V[(J be), m])
-  auto applyM = [&](const Tensor &V, Tensor &Y) {               // V: (J be) x w
-    Arena::Mark mk = c.arena.mark();
-    Tensor Z = c.alloc({x, k, k, w});                           // (x al, be m)
-    gemm(c, false, false, x * k, k * w, J, 1.0, Bq.p, J, 0, V.p, k * w, 0, 0.0, Z.p, k * w, 0, 1);
-    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x be, al m)
-    gemm(c, false, false, I, k * w, x * k, 1.0, Cp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Y.p,
-         k * w, 0, 1);
-    c.arena.release(mk);
+  Tensor GC = c.alloc({xk, xk}), GB = c.alloc({xk, xk});
+  gemm(c, false, true, xk, xk, I, 1.0, Cq.p, I, 0, Cq.p, I, 0, 0.0, GC.p, xk, 0, 1);
+  gemm(c, false, true, xk, xk, J, 1.0, Bq.p, J, 0, Bq.p, J, 0, 0.0, GB.p, xk, 0, 1);
+  // G (x) 1 applied to coordinates [(x leg) rows][(leg m)], then the two bond legs swapped
+  auto apply_g = [&](const Tensor &G, const Tensor &Yc) {
+    Tensor Z = c.alloc({x, k, k, w});
+    gemm(c, false, false, xk, k * w, xk, 1.0, G.p, xk, 0, Yc.p, k * w, 0, 0.0, Z.p, k * w, 0,
+         1);
+    return Z;
   };
-  // Yt[(J be), m] = sum_{x al} B[x J al] (sum_I C[x I be] U[(I al), m])
-  auto applyMt = [&](const Tensor &U, Tensor &Yt) {             // U: (I al) x w
+  auto apply_gp = [&](const Tensor &G, const Tensor &Yc) {
+    Tensor out = c.alloc({x, k, k, w});
     Arena::Mark mk = c.arena.mark();
-    Tensor Z = c.alloc({x, k, k, w});                           // (x be, al m)
-    gemm(c, false, false, x * k, k * w, I, 1.0, Cq.p, I, 0, U.p, k * w, 0, 0.0, Z.p, k * w, 0, 1);
-    Tensor Zp = permuted(c, Z, {0, 2, 1, 3});                   // (x al, be m)
-    gemm(c, false, false, J, k * w, x * k, 1.0, Bp.p, x * k, 0, Zp.p, k * w, 0, 0.0, Yt.p,
-         k * w, 0, 1);
+    Tensor Z = apply_g(G, Yc);
+    permute(Z.p, out.p, Z.dims, {0, 2, 1, 3}, c.stream);
     c.arena.release(mk);
+    return out;
   };
-  Tensor Q = c.alloc({I * k, w}), Yt = c.alloc({J * k, w}), V = c.alloc({J * k, w});
-  TRG_CUDA(cudaMemcpyAsync(V.p, Om.p, V.size() * 8, cudaMemcpyDeviceToDevice, s));
-  for (int rnd = 0; rnd < c.q_swap; ++rnd) {
+  // shifted CholeskyQR3 in the metric G (x) 1: Q'^T (G (x) 1) Q' = 1 (cf. orth_sc)
+  auto orth_g = [&](const Tensor &G, const Tensor &Yc) {
+    Tensor out = c.alloc({x, k, k, w});
     Arena::Mark mk = c.arena.mark();
-    Tensor Y = c.alloc({I * k, w});
-    applyM(V, Y);
-    Tensor Qn = orth_sc(c, Y);
-    TRG_CUDA(cudaMemcpyAsync(Q.p, Qn.p, Q.size() * 8, cudaMemcpyDeviceToDevice, s));
+    Tensor Qc = Yc;
+    for (int pass = 0; pass < 3; ++pass) {
+      Tensor Z = apply_g(G, Qc);
+      Tensor S = c.alloc({w, w}), R = c.alloc({w, w}), Ri = c.alloc({w, w});
+      gemm(c, true, false, w, w, rows, 1.0, Qc.p, w, 0, Z.p, w, 0, 0.0, S.p, w, 0, 1);
+      chol_rinv(S.p, R.p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
+                pass == 0 ? kShiftRel : 0.0, c.stream);
+      Tensor Qn = pass == 2 ? out : c.alloc({x, k, k, w});
+      gemm(c, false, false, rows, w, w, 1.0, Qc.p, w, 0, Ri.p, w, 0, 0.0, Qn.p, w, 0, 1);
+      Qc = Qn;
+    }
     c.arena.release(mk);
-    if (rnd + 1 == c.q_swap) {
-      Crit cr(c);  // the last application feeds the core SVD
-      applyMt(Q, Yt);
-    } else {
-      applyMt(Q, Yt);
-    }
-    if (rnd + 1 < c.q_swap) {
-      Arena::Mark mk2 = c.arena.mark();
-      Tensor Vn = orth_sc(c, Yt);
-      TRG_CUDA(cudaMemcpyAsync(V.p, Vn.p, V.size() * 8, cudaMemcpyDeviceToDevice, s));
-      c.arena.release(mk2);
-    }
+    return out;
+  };
+  // first left block M Omega for the Khatri-Rao sketch Omega[(J be), m] = g2[J,m] g1[be,m]:
+  // Y'[(x be), al, m] = (B^T g2)[(x al), m] g1[be, m]
+  Tensor Yc = c.alloc({x, k, k, w});
+  {
+    Arena::Mark mk = c.arena.mark();
+    Tensor g1 = c.alloc({k, w}), g2 = c.alloc({J, w}), h = c.alloc({x, k, w});
+    fill_gaussian(g1.p, k, w, key(TAG_SWAP_G1), s);
+    fill_gaussian(g2.p, J, w, key(TAG_SWAP_G2), s);
+    gemm(c, false, false, xk, w, J, 1.0, Bq.p, J, 0, g2.p, w, 0, 0.0, h.p, w, 0, 1);
+    for (int64_t ix = 0; ix < x; ++ix)
+      khatri_rao(g1.p, h.p + ix * k * w, Yc.p + ix * k * k * w, k, k, w, s);
+    c.arena.release(mk);
   }
+  Tensor Qc = c.alloc({x, k, k, w}), Ytc = c.alloc({x, k, k, w});
+  const int qs = std::max(c.q_swap, 1);
+  for (int rnd = 0; rnd < qs; ++rnd) {
+    Arena::Mark mk = c.arena.mark();
+    if (rnd > 0) {
+      Tensor Wc = orth_g(GB, Ytc);
+      Tensor Yn = apply_gp(GB, Wc);
+      TRG_CUDA(cudaMemcpyAsync(Yc.p, Yn.p, Yc.size() * 8, cudaMemcpyDeviceToDevice, s));
+      c.arena.release(mk);
+    }
+    {
+      Tensor Qn = orth_g(GC, Yc);
+      TRG_CUDA(cudaMemcpyAsync(Qc.p, Qn.p, Qc.size() * 8, cudaMemcpyDeviceToDevice, s));
+      c.arena.release(mk);
+    }
+    std::unique_ptr<Crit> cr(rnd + 1 == qs ? new Crit(c) : nullptr);  // feeds the core SVD
+    Tensor Yt = apply_gp(GC, Qc);
+    TRG_CUDA(cudaMemcpyAsync(Ytc.p, Yt.p, Ytc.size() * 8, cudaMemcpyDeviceToDevice, s));
+    c.arena.release(mk);
+  }
+  // core: M^T Q = (B (x) 1) Ytc = Qt Rt with Qt orthonormal  ->  Q^T M = Rt^T Qt^T
   std::unique_ptr<Crit> crit_core(new Crit(c));
-  auto [Qt, Rt] = orth_qr(c, Yt);              // M^T Q = Qt Rt  ->  Q^T M = Rt^T Qt^T
+  Tensor Qtc = orth_g(GB, Ytc);
+  Tensor Rt = c.alloc({w, w});
+  {
+    Arena::Mark mk = c.arena.mark();
+    Tensor Z = apply_g(GB, Ytc);
+    gemm(c, true, false, w, w, rows, 1.0, Qtc.p, w, 0, Z.p, w, 0, 0.0, Rt.p, w, 0, 1);
+    c.arena.release(mk);
+  }
   Svd cs = svd_small(c, transpose2(c, Rt));
-  Tensor Xf = mm_cols(c, Q, cs.U, Dg), Yf = mm_cols(c, Qt, cs.V, Dg);
+  Tensor Xc = mm_cols(c, view(Qc.p, {rows, w}), cs.U, Dg);    // [(x be) al, g]
+  Tensor Yd = mm_cols(c, view(Qtc.p, {rows, w}), cs.V, Dg);   // [(x al) be, g]
   TRG_CUDA(cudaMemcpyAsync(sig, cs.S.p, w * 8, cudaMemcpyDeviceToDevice, s));
-  kill_dead(sig, Dg, kRankTol, Xf.p, I * k, Yf.p, J * k, s);
-  permute(Xf.p, X.p, {I, k, Dg}, {1, 0, 2}, s);
-  permute(Yf.p, Y.p, {J, k, Dg}, {1, 0, 2}, s);
+  kill_dead(sig, Dg, kRankTol, Xc.p, rows, Yd.p, rows, s);
+  {
+    // X[al, I, g] = sum_{x be} C[x I be] Xc[(x be), (al g)]; same for Y with B
+    Arena::Mark mk = c.arena.mark();
+    Tensor Xf = c.alloc({I, k, Dg});
+    gemm(c, true, false, I, k * Dg, xk, 1.0, Cq.p, I, 0, Xc.p, k * Dg, 0, 0.0, Xf.p, k * Dg, 0,
+         1);
+    permute(Xf.p, X.p, {I, k, Dg}, {1, 0, 2}, s);
+    Tensor Yf = c.alloc({J, k, Dg});
+    gemm(c, true, false, J, k * Dg, xk, 1.0, Bq.p, J, 0, Yd.p, k * Dg, 0, 0.0, Yf.p, k * Dg, 0,
+         1);
+    permute(Yf.p, Y.p, {J, k, Dg}, {1, 0, 2}, s);
+    c.arena.release(mk);
+  }
   crit_core.reset();
   double gap_swap = INFINITY;
   {
