@@ -116,7 +116,9 @@ svd_jacobi_kernel(const double *A, int m, int n, double *U, double *S, double *V
   __syncthreads();
   const int nn = n + (n & 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const double tol = 1e-15;
+  // rotation threshold sqrt(m) eps (the usual one-sided Jacobi choice): the rounding
+  // error of a length-m dot product is about that large, so a smaller one never settles
+  const double tol = sqrt((double)m) * 2.220446049250313e-16;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
@@ -193,6 +195,149 @@ svd_jacobi_kernel(const double *A, int m, int n, double *U, double *S, double *V
   if (threadIdx.x == 0 && info) info[b] = s_sweeps;
 }
 
+// ------------------------------------------- one-sided Jacobi across the whole GPU
+// FP64 runs at a few FMA per clock per SM, so a single CTA needs ~0.1 s for a 144 x 144
+// SVD.  This variant gives every column pair of a round its own CTA (one warp) and
+// separates rounds with a grid barrier; the launch is cooperative, so all CTAs are
+// resident.  Same pair order, reductions and rotations as svd_jacobi_kernel, hence the
+// same result.  The barrier waits are bounded (about 2 s); a CTA that gives up raises
+// g_lin_err and leaves, and the others then give up at their next barrier.
+__device__ int g_lin_err;
+
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks,
+                                             unsigned &my_gen) {
+  __threadfence();
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    const unsigned g = my_gen;
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*(volatile unsigned *)gen == g) {
+        if (clock64() - t0 > (1ll << 32)) {
+          atomicExch(&g_lin_err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  ++my_gen;
+  return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(32)
+svd_jacobi_coop_kernel(const double *A, int m, int n, double *U, double *S, double *V,
+                       double *work, unsigned *sync, int *info) {
+  double *at = work, *vt = work + (int64_t)n * m, *nrm = vt + (int64_t)n * n;
+  unsigned *count = sync, *gen = sync + 1;
+  int *rot = reinterpret_cast<int *>(sync + 2);  // one counter per sweep
+  const unsigned nb = gridDim.x;
+  unsigned my_gen = 0;
+  const int lane = threadIdx.x;
+  const int64_t stride = (int64_t)nb * 32;
+  for (int64_t idx = blockIdx.x * 32 + lane; idx < (int64_t)n * m; idx += stride) {
+    int j = (int)(idx / m), r = (int)(idx % m);
+    __stcg(&at[idx], A[(int64_t)r * n + j]);
+  }
+  for (int64_t idx = blockIdx.x * 32 + lane; idx < (int64_t)n * n; idx += stride)
+    __stcg(&vt[idx], (idx / n == idx % n) ? 1.0 : 0.0);
+  if (!grid_barrier(count, gen, nb, my_gen)) return;
+  const int nn = n + (n & 1);
+  const double tol = sqrt((double)m) * 2.220446049250313e-16;
+  int sweeps = -1;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    for (int rnd = 0; rnd < nn - 1; ++rnd) {
+      for (int k = blockIdx.x; k < nn / 2; k += nb) {
+        int p = (k == 0) ? 0 : ((k - 1 + rnd) % (nn - 1)) + 1;
+        int kk = nn - 1 - k;
+        int q = ((kk - 1 + rnd) % (nn - 1)) + 1;
+        int i = p < q ? p : q, j = p < q ? q : p;
+        if (j >= n) continue;  // dummy partner
+        double *ai = at + (int64_t)i * m, *aj = at + (int64_t)j * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < m; r += 32) {
+          double x = __ldcg(&ai[r]), y = __ldcg(&aj[r]);
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = wsum(al);
+        be = wsum(be);
+        ga = wsum(ga);
+        if (!(fabs(ga) > tol * sqrt(al * be))) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t;
+        if (fabs(zeta) > 1e150)
+          t = 0.5 / zeta;
+        else
+          t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int r = lane; r < m; r += 32) {
+          double x = __ldcg(&ai[r]), y = __ldcg(&aj[r]);
+          __stcg(&ai[r], c * x - s * y);
+          __stcg(&aj[r], s * x + c * y);
+        }
+        double *vi = vt + (int64_t)i * n, *vj = vt + (int64_t)j * n;
+        for (int r = lane; r < n; r += 32) {
+          double x = __ldcg(&vi[r]), y = __ldcg(&vj[r]);
+          __stcg(&vi[r], c * x - s * y);
+          __stcg(&vj[r], s * x + c * y);
+        }
+        if (lane == 0) atomicAdd(&rot[sweep], 1);
+      }
+      if (!grid_barrier(count, gen, nb, my_gen)) return;
+    }
+    if (*(volatile int *)&rot[sweep] == 0) {
+      sweeps = sweep + 1;
+      break;
+    }
+  }
+  for (int j = blockIdx.x; j < n; j += nb) {
+    double v = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      const double x = __ldcg(&at[(int64_t)j * m + r]);
+      v += x * x;
+    }
+    v = wsum(v);
+    if (lane == 0) __stcg(&nrm[j], sqrt(v));
+  }
+  if (!grid_barrier(count, gen, nb, my_gen)) return;
+  for (int j = blockIdx.x; j < n; j += nb) {
+    const double sj = __ldcg(&nrm[j]);
+    int rank = 0;
+    for (int k = 0; k < n; ++k) {
+      const double sk = __ldcg(&nrm[k]);
+      if (sk > sj || (sk == sj && k < j)) ++rank;
+    }
+    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    for (int r = lane; r < m; r += 32) U[(int64_t)r * n + rank] = __ldcg(&at[(int64_t)j * m + r]) * inv;
+    for (int r = lane; r < n; r += 32) V[(int64_t)r * n + rank] = __ldcg(&vt[(int64_t)j * n + r]);
+    if (lane == 0) S[rank] = sj;
+  }
+  if (blockIdx.x == 0 && lane == 0 && info) info[0] = sweeps;
+}
+
+int linalg_error_flag(bool reset) {
+  int v = 0;
+  cudaMemcpyFromSymbol(&v, g_lin_err, sizeof(int));
+  if (reset) {
+    int z = 0;
+    cudaMemcpyToSymbol(g_lin_err, &z, sizeof(int));
+  }
+  return v;
+}
+
+size_t svd_jacobi_work(int m, int n, int batch) {
+  return (size_t)batch * ((size_t)n * m + (size_t)n * n) + (size_t)n + 8 + (kMaxSweeps + 8) / 2;
+}
+
 void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, int batch,
                 double *work, int *info, cudaStream_t s) {
   if (n == 0 || batch == 0) return;
@@ -203,6 +348,23 @@ void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, 
     TRG_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSvdSmemMax));
     attr_set = true;
+  }
+  if (batch == 1 && n >= 24) {
+    // cooperative form: work = [at | vt | norms | sync words]
+    double *nrm_end = work + (size_t)n * m + (size_t)n * n + n;
+    unsigned *sync = reinterpret_cast<unsigned *>(nrm_end);
+    TRG_CUDA(cudaMemsetAsync(sync, 0, (2 + kMaxSweeps) * sizeof(unsigned), s));
+    int dev = 0, nsm = 0;
+    TRG_CUDA(cudaGetDevice(&dev));
+    TRG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int pairs = (n + (n & 1)) / 2;
+    const unsigned grid = (unsigned)std::min(pairs, nsm);
+    void *args[] = {(void *)&A, (void *)&m, (void *)&n, (void *)&U, (void *)&S, (void *)&V,
+                    (void *)&work, (void *)&sync, (void *)&info};
+    TRG_CUDA(cudaLaunchCooperativeKernel((const void *)svd_jacobi_coop_kernel, dim3(grid),
+                                         dim3(32), args, 0, s));
+    ++g_kernel_launches;
+    return;
   }
   const size_t bytes = (size_t)n * m * sizeof(double);
   const int in_smem = bytes <= kSvdSmemMax;

@@ -77,11 +77,12 @@ struct Tensor {
 // --------------------------------------------------------------------- kernels
 void permute(const double *in, double *out, const std::vector<int64_t> &dims_in,
              const std::vector<int> &perm, cudaStream_t s);
-// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, FP64 on CUDA cores
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, FP64 on CUDA cores.
+// b_upper: the caller guarantees op(B) is upper triangular (lets thin kernels skip zeros).
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
               const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
               int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch,
-              cudaStream_t s);
+              cudaStream_t s, bool b_upper = false);
 // Gaussian sketch: out[r*cols + c] from the counter-based SplitMix64 / Box-Muller rule
 void fill_gaussian(double *out, int64_t rows, int64_t cols, uint64_t key, cudaStream_t s);
 uint64_t sketch_key(uint64_t seed, int step, int tag);
@@ -120,7 +121,12 @@ void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, doubl
 // One-sided Jacobi SVD of batch m x n (m >= n) row-major matrices: A = U diag(S) V^T,
 // S descending.  U: m x n, V: n x n (row-major).  info[b] = sweeps used, or -1 if the
 // sweep limit was reached.  work: batch * (n*m + n*n) doubles.
+// One problem with n >= 64 runs as a cooperative launch over many SMs (bounded grid
+// barriers; a timed-out wait raises linalg_error_flag).  work: svd_jacobi_work doubles.
 void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, int batch,
                 double *work, int *info, cudaStream_t s);
+size_t svd_jacobi_work(int m, int n, int batch);
+// nonzero if a grid barrier of the cooperative Jacobi timed out since the last reset
+int linalg_error_flag(bool reset);
 
 }  // namespace trg

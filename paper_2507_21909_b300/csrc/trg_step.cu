@@ -51,6 +51,7 @@ struct Ctx {
   // exponent cannot hold the dynamic range of a triangular inverse
   int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
+  bool b_upper = false;        // the next GEMM's right factor is upper triangular (R^-1)
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
   static constexpr int kPhases = 8;
@@ -174,7 +175,8 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
               cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing);
     c.arena.release(mk);
   } else {
-    gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream);
+    gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream,
+             c.b_upper && !tb);
   }
 }
 
@@ -315,11 +317,13 @@ static Tensor orth_sc(Ctx &c, const Tensor &Y) {
     Tensor R = c.alloc({w, w}), Ri = c.alloc({w, w});
     chol_rinv(G.p, R.p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
               pass == 0 ? kShiftRel : 0.0, c.stream);
+    c.b_upper = true;
     if (pass == 2) {
       gemm(c, false, false, Q.dims[0], w, w, 1.0, Q.p, w, 0, Ri.p, w, 0, 0.0, out.p, w, 0, 1);
     } else {
       Q = mm(c, Q, Ri, false, false);
     }
+    c.b_upper = false;
   }
   c.arena.release(mk);
   return out;
@@ -341,9 +345,9 @@ static Svd svd_small(Ctx &c, const Tensor &A) {
   r.U = c.alloc({m, n});
   r.S = c.alloc({n});
   r.V = c.alloc({n, n});
-  Tensor work = c.alloc({n * m + n * n + 1});
+  Tensor work = c.alloc({(int64_t)svd_jacobi_work((int)m, (int)n, 1) + 1});
   static const bool dbg = getenv("TRG_DEBUG_SVD") != nullptr;
-  int *info = dbg ? reinterpret_cast<int *>(work.p + n * m + n * n) : nullptr;
+  int *info = dbg ? reinterpret_cast<int *>(work.p + work.size() - 1) : nullptr;
   svd_jacobi(A.p, (int)m, (int)n, r.U.p, r.S.p, r.V.p, 1, work.p, info, c.stream);
   if (dbg) {
     int sweeps = 0;
@@ -791,6 +795,8 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   c.last_gap = std::min(gap_swap, gap_sq);
   c.arena.reset();
   if (flag) throw Error(flag, "non-finite norm in the coarse-graining step");
+  if (linalg_error_flag(true))
+    throw Error(TRG_ERR_TIMEOUT, "grid barrier of the cooperative Jacobi SVD timed out");
   if (c.mixed_now && (tc_error_flag(true) | oz_error_flag(true)))
     throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
 }
@@ -1093,9 +1099,13 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
     Ctx &c = ctx();
     ensure_ctx(c);
     const int64_t rA = ta ? K : M, rB = tb ? N : K;
-    Tensor dA = c.alloc({rA, lda}), dB = c.alloc({rB, ldb}), dC = c.alloc({M, ldc});
+    // one host matrix passed as both operands (a Gram) is uploaded once, so that the
+    // device kernels see A == B
+    const bool same = A == B && rA == rB && lda == ldb;
+    Tensor dA = c.alloc({rA, lda}), dB = same ? dA : c.alloc({rB, ldb}), dC = c.alloc({M, ldc});
     TRG_CUDA(cudaMemcpyAsync(dA.p, A, rA * lda * 8, cudaMemcpyHostToDevice, c.stream));
-    TRG_CUDA(cudaMemcpyAsync(dB.p, B, rB * ldb * 8, cudaMemcpyHostToDevice, c.stream));
+    if (!same)
+      TRG_CUDA(cudaMemcpyAsync(dB.p, B, rB * ldb * 8, cudaMemcpyHostToDevice, c.stream));
     TRG_CUDA(cudaMemcpyAsync(dC.p, C, M * ldc * 8, cudaMemcpyHostToDevice, c.stream));
     if (precision == TRG_PREC_FP64) {
       gemm_f64(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1, c.stream);

@@ -50,3 +50,37 @@ def test_gemm_scaled_rows(trg, prec, bound):
     ref = A @ B
     rel = np.abs(got - ref).max(axis=1) / (np.abs(A) @ np.abs(B)).max(axis=1)
     assert rel.max() < bound
+
+
+THIN = [(48, 48, 100003, True, False), (64, 64, 8192, False, True), (17, 33, 5000, True, True),
+        (48, 48, 4096, False, False)]
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb", THIN)
+def test_gemm_f64_thin(trg, M, N, K, ta, tb):
+    """FP64 products with an output of at most 64 x 64 over a long inner dimension (the
+    split-K micro-tile kernel), including ragged K and sizes off the 16-grid."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    opA, opB = (A.T if ta else A), (B.T if tb else B)
+    C0 = rng.standard_normal((M, N))
+    got = trg.trg_gemm(A, B, precision=0, ta=ta, tb=tb, alpha=0.5, beta=-2.0, C=C0)
+    ref = 0.5 * (opA @ opB) - 2.0 * C0
+    scale = 0.5 * (np.abs(opA) @ np.abs(opB)).max() + 2.0 * np.abs(C0).max()
+    assert np.abs(got - ref).max() / scale < 1e-14
+
+
+@pytest.mark.parametrize("M,K", [(100003, 48), (5000, 64), (4096, 7)])
+def test_gemm_f64_gram_and_tall(trg, M, K):
+    """A Gram X^T X passed as one host matrix (the symmetric upper-triangle kernel) is
+    exactly symmetric and matches NumPy; a tall X R product (M x K times K x K)."""
+    rng = np.random.default_rng(M + K)
+    X = rng.standard_normal((M, K))
+    G = trg.trg_gemm(X, X, precision=0, ta=True, tb=False)
+    ref = X.T @ X
+    assert np.array_equal(G, G.T)
+    assert np.abs(G - ref).max() / (np.abs(X).T @ np.abs(X)).max() < 1e-14
+    R = np.triu(rng.standard_normal((K, K)))
+    P = trg.trg_gemm(X, R, precision=0)
+    assert np.abs(P - X @ R).max() / (np.abs(X) @ np.abs(R)).max() < 1e-14
