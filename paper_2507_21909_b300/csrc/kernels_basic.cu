@@ -34,22 +34,162 @@ static int grid_for(int64_t n, int threads = 256) {
   return (int)b;
 }
 
+// Offsets of a mixed-radix index over `nb` axes (innermost last) in two layouts.
+struct BatchMap {
+  int nb;
+  int64_t dims[kMaxDims];
+  int64_t s_in[kMaxDims], s_out[kMaxDims];
+};
+__device__ __forceinline__ void batch_offsets(const BatchMap &m, int64_t idx, int64_t &oi,
+                                              int64_t &oo) {
+  oi = 0;
+  oo = 0;
+  for (int d = m.nb - 1; d >= 0; --d) {
+    const int64_t c = idx % m.dims[d];
+    idx /= m.dims[d];
+    oi += c * m.s_in[d];
+    oo += c * m.s_out[d];
+  }
+}
+
+// The innermost axis is kept: rows of L contiguous elements are copied, one block per
+// `rpb` rows; the row offsets are decoded once per row.
+__global__ void permute_rows_kernel(const double *__restrict__ in, double *__restrict__ out,
+                                    int64_t rows, int64_t L, int rpb, BatchMap m) {
+  __shared__ int64_t s_off[256];
+  for (int64_t r0 = (int64_t)blockIdx.x * rpb; r0 < rows; r0 += (int64_t)gridDim.x * rpb) {
+    __syncthreads();
+    if (threadIdx.x < rpb && r0 + threadIdx.x < rows) {
+      int64_t oi, oo;
+      batch_offsets(m, r0 + threadIdx.x, oi, oo);
+      s_off[threadIdx.x] = oi;
+    }
+    __syncthreads();
+    const int64_t nrow = min((int64_t)rpb, rows - r0);
+    const int64_t n = nrow * L;
+    double *dst = out + r0 * L;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t r = i / L, j = i - r * L;
+      dst[i] = in[s_off[r] + j];
+    }
+  }
+}
+
+// 32 x 32 tiles through shared memory: reads run along the input's innermost axis (a),
+// writes along the output's innermost axis (b); the other axes are a batch decoded once
+// per tile.
+__global__ void __launch_bounds__(256)
+permute_tile_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t na,
+                    int64_t nbb, int64_t sa_out, int64_t sb_in, int64_t ntiles, BatchMap m) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t ta_n = (na + 31) / 32, tb_n = (nbb + 31) / 32;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t per = ta_n * tb_n;
+    const int64_t bi = t / per, rem = t - bi * per;
+    const int64_t a0 = (rem % ta_n) * 32, b0 = (rem / ta_n) * 32;
+    int64_t oi, oo;
+    batch_offsets(m, bi, oi, oo);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t b = b0 + r, a = a0 + tx;
+      if (a < na && b < nbb) tile[r][tx] = in[oi + b * sb_in + a];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t a = a0 + r, b = b0 + tx;
+      if (a < na && b < nbb) out[oo + a * sa_out + b] = tile[tx][r];
+    }
+  }
+}
+
 void permute(const double *in, double *out, const std::vector<int64_t> &dims_in,
              const std::vector<int> &perm, cudaStream_t s) {
-  int nd = (int)dims_in.size();
-  if (nd > kMaxDims) throw Error(TRG_ERR_ARG, "permute: too many dims");
-  PermArgs a;
-  a.nd = nd;
-  std::vector<int64_t> st(nd, 1);
-  for (int d = nd - 2; d >= 0; --d) st[d] = st[d + 1] * dims_in[d + 1];
+  const int nd0 = (int)dims_in.size();
+  if (nd0 > kMaxDims) throw Error(TRG_ERR_ARG, "permute: too many dims");
   int64_t total = 1;
-  for (int d = 0; d < nd; ++d) {
-    a.out_dims[d] = dims_in[perm[d]];
-    a.in_stride_of_out[d] = st[perm[d]];
-    total *= dims_in[d];
-  }
+  for (int d = 0; d < nd0; ++d) total *= dims_in[d];
   if (total == 0) return;
-  permute_kernel<<<grid_for(total), 256, 0, s>>>(in, out, total, a);
+  // merge output axes that are also adjacent (and in order) in the input; drop 1-axes
+  std::vector<int64_t> st(nd0, 1);
+  for (int d = nd0 - 2; d >= 0; --d) st[d] = st[d + 1] * dims_in[d + 1];
+  std::vector<int64_t> od, os;   // merged output dims and their input strides
+  std::vector<int> first;        // input axis of each merged group's outermost member
+  for (int j = 0; j < nd0; ++j) {
+    const int ax = perm[j];
+    if (dims_in[ax] == 1) continue;
+    if (!od.empty() && first.back() >= 0 && os.back() == st[ax] * dims_in[ax]) {
+      od.back() *= dims_in[ax];
+      os.back() = st[ax];
+    } else {
+      od.push_back(dims_in[ax]);
+      os.push_back(st[ax]);
+      first.push_back(ax);
+    }
+  }
+  const int nd = (int)od.size();
+  if (nd <= 1 || (os.back() == 1 && nd == 1)) {
+    TRG_CUDA(cudaMemcpyAsync(out, in, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  bool identity = true;
+  for (int j = 0; j < nd; ++j) {
+    int64_t want = 1;
+    for (int k = j + 1; k < nd; ++k) want *= od[k];
+    if (os[j] != want) identity = false;
+  }
+  if (identity) {
+    TRG_CUDA(cudaMemcpyAsync(out, in, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  std::vector<int64_t> ostr(nd, 1);  // output strides of the merged axes
+  for (int j = nd - 2; j >= 0; --j) ostr[j] = ostr[j + 1] * od[j + 1];
+  if (os[nd - 1] == 1) {
+    // innermost axis kept
+    const int64_t L = od[nd - 1], rows = total / L;
+    BatchMap m;
+    m.nb = nd - 1;
+    for (int j = 0; j < nd - 1; ++j) {
+      m.dims[j] = od[j];
+      m.s_in[j] = os[j];
+      m.s_out[j] = ostr[j] / L;
+    }
+    const int rpb = (int)std::max<int64_t>(1, std::min<int64_t>(256, 1024 / L));
+    const int64_t blocks = std::min<int64_t>((rows + rpb - 1) / rpb, 148 * 32);
+    permute_rows_kernel<<<(int)blocks, 256, 0, s>>>(in, out, rows, L, rpb, m);
+    TRG_LAUNCH_CHECK();
+    return;
+  }
+  // the input's innermost axis sits at output position q (stride 1 in the input)
+  int q = -1;
+  for (int j = 0; j < nd; ++j)
+    if (os[j] == 1) q = j;
+  const int64_t na = q >= 0 ? od[q] : 0, nbb = od[nd - 1];
+  if (q < 0 || na < 8 || nbb < 8) {
+    PermArgs a;
+    a.nd = nd;
+    for (int j = 0; j < nd; ++j) {
+      a.out_dims[j] = od[j];
+      a.in_stride_of_out[j] = os[j];
+    }
+    permute_kernel<<<grid_for(total), 256, 0, s>>>(in, out, total, a);
+    TRG_LAUNCH_CHECK();
+    return;
+  }
+  BatchMap m;
+  m.nb = 0;
+  for (int j = 0; j < nd; ++j) {
+    if (j == q || j == nd - 1) continue;
+    m.dims[m.nb] = od[j];
+    m.s_in[m.nb] = os[j];
+    m.s_out[m.nb] = ostr[j];
+    ++m.nb;
+  }
+  const int64_t nbatch = total / (na * nbb);
+  const int64_t ntiles = nbatch * ((na + 31) / 32) * ((nbb + 31) / 32);
+  const int64_t blocks = std::min<int64_t>(ntiles, 148 * 64);
+  permute_tile_kernel<<<(int)blocks, 256, 0, s>>>(in, out, na, nbb, ostr[q], os[nd - 1],
+                                                  ntiles, m);
   TRG_LAUNCH_CHECK();
 }
 

@@ -47,8 +47,8 @@ struct Ctx {
   unsigned phase_mask = 0xFFu; // phases whose GEMMs may use the tensor cores
   int bulk_cheap = 0;          // > 0: range-finder / impurity products (see gemm())
   // smallest GEMM sides sent to the tensor cores: thin products (max side < 64, e.g. the
-  // re-split Grams and Q R^-1 with a 48-column R) stay FP64, because a per-column
-  // exponent cannot hold the dynamic range of a triangular inverse
+  // re-split Grams) and Q R^-1 with a narrow R stay FP64, because a per-column exponent
+  // cannot hold the dynamic range of a triangular inverse
   int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   bool b_upper = false;        // the next GEMM's right factor is upper triangular (R^-1)
@@ -160,7 +160,7 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
   const double work = (double)M * N * K * batch;
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
       work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
-      K >= 16) {
+      K >= 16 && !(c.b_upper && N < c.tc_min_max)) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     // exact-digit forms: products that feed only the impurity (not the free energy) run
