@@ -15,9 +15,12 @@
 // FP32 for the whole K (its rounding is 2^-38 of the result).  The epilogue forms
 // C = alpha 2^(e_r + e_c - 28) (S + H) + beta C in FP64.
 //
-// CTA = 10 warps: warp 0 TMA producer (one tile of one A slice and one B slice per
-// stage, 6 stages), warp 1 MMA issuer (M = 128, N = 128, K = 16), warps 2..9 drain TMEM
-// (two warps per 32-lane quadrant, 64 columns each).
+// CTA = 12 warps: warp 0 TMA producer, warp 1 MMA issuer (M = 128, N = 128, K = 16),
+// warps 2..9 drain TMEM (two warps per 32-lane quadrant, 64 columns each).  A pipeline
+// stage holds one 16-wide K block of every digit slice of A and of B (32-byte rows,
+// 32-byte swizzle), so each slice tile is loaded once and serves all pairs (i, j) that
+// use it; at the first stage of a chunk the lower-level pairs are issued before waiting
+// for the drain of the previous chunk, which hides the drain behind them.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -33,8 +36,14 @@
 namespace trg {
 namespace oz {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
-constexpr int CHUNK_KB = 4;                 // 4 x 64 = 256 K per exact chunk
+constexpr int BM = 128, BN = 128;
+constexpr int BK = 64;                      // K padding granule of the digit planes
+constexpr int KS = 16;                      // K per pipeline stage (= one MMA, 32-byte rows)
+constexpr int CHUNK_K = 256;                // exact chunk of levels 0 / 1
+constexpr int CHUNK_KS = CHUNK_K / KS;      // stages per chunk
+constexpr uint32_t SLICE_TILE = BM * KS * 2;    // 4 KB: 128 rows x 16 K of one slice
+constexpr size_t kStageBudget = 200 * 1024;     // shared memory for the stage ring
+constexpr int MAX_STAGES = 8;
 // 12 warps: registers are allocated in groups of four warps, so a 10-warp block costs
 // as much as 12; warps 10 and 11 only take part in the block-wide barriers
 constexpr int NWARPS = 12, THREADS = NWARPS * 32;
@@ -43,7 +52,8 @@ constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 (power of 
 
 struct Params {
   int64_t M, N, Kp, batch;
-  int nkb;                                  // K blocks per split (multiple of CHUNK_KB)
+  int nks;                                  // K stages per split (multiple of CHUNK_KS)
+  int ns, stages;                           // digit slices; stages in the ring
   int npairs;
   int pi[MAX_PAIRS], pj[MAX_PAIRS], pl[MAX_PAIRS];  // slice of A, slice of B, level 0/1/2
   const unsigned *ea, *eb;                  // row exponent codes [batch][M], [batch][N]
@@ -93,9 +103,10 @@ __device__ __forceinline__ void tma4(uint32_t dst, const CUtensorMap *m, uint32_
       "l"(reinterpret_cast<uint64_t>(m)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
+// K-major tile with 32-byte rows, 32-byte swizzle: 8-row groups 256 bytes apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
@@ -131,34 +142,44 @@ __device__ __forceinline__ int exact_int(float v) {
   return __float_as_int(v + 12582912.0f) - 0x4B400000;
 }
 
+__device__ __forceinline__ void umma(uint32_t acc_t, uint64_t da, uint64_t db, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc_t),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+template <int NS>
 __global__ void __launch_bounds__(THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const Params p) {
-  constexpr uint32_t TILE = BM * BK * 2;    // 16 KB (A and B tiles are both 128 x 64)
-  constexpr uint32_t STAGE = 2 * TILE;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
-  // bar[0..S) full, bar[S..2S) empty, bar[2S] chunk ready, bar[2S+1] chunk drained,
-  // bar[2S+2] all done
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * STAGES + 3);
+  constexpr int ns = NS;
+  const int nst = p.stages;
+  const uint32_t STAGE = 2u * (uint32_t)ns * SLICE_TILE;   // all A slices, then all B slices
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * STAGE);
+  // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] chunk
+  // drained, bar[2nst+2] all done
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * MAX_STAGES + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   const int64_t b = blockIdx.z % p.batch, split = blockIdx.z / p.batch;
-  const int nkb_total = (int)(p.Kp / BK);
-  const int kb0 = (int)split * p.nkb;
-  const int nk = max(min(kb0 + p.nkb, nkb_total) - kb0, 0);
-  const int nchunks = (nk + CHUNK_KB - 1) / CHUNK_KB;
+  const int nks_total = (int)(p.Kp / KS);
+  const int ks0 = (int)split * p.nks;
+  const int nk = max(min(ks0 + p.nks, nks_total) - ks0, 0);
+  const int nchunks = (nk + CHUNK_KS - 1) / CHUNK_KS;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mb_init(su32(&bar[s]), 1);
-      mb_init(su32(&bar[STAGES + s]), 1);
+    for (int st = 0; st < nst; ++st) {
+      mb_init(su32(&bar[st]), 1);
+      mb_init(su32(&bar[nst + st]), 1);
     }
-    mb_init(su32(&bar[2 * STAGES]), 1);
-    mb_init(su32(&bar[2 * STAGES + 1]), 8 * 32);
-    mb_init(su32(&bar[2 * STAGES + 2]), 1);
+    mb_init(su32(&bar[2 * nst]), 1);
+    mb_init(su32(&bar[2 * nst + 1]), 8 * 32);
+    mb_init(su32(&bar[2 * nst + 2]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -175,70 +196,68 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (warp == 0) {
     if (lane == 0) {  // ------------------------------------------ TMA producer
-      int it = 0;
-      bool ok = true;
-      for (int ch = 0; ch < nchunks && ok; ++ch)
-        for (int kb = ch * CHUNK_KB; kb < min((ch + 1) * CHUNK_KB, nk) && ok; ++kb)
-          for (int pr = 0; pr < p.npairs; ++pr, ++it) {
-            const int s = it % STAGES;
-            if (!mb_wait(su32(&bar[STAGES + s]), ((uint32_t)(it / STAGES) & 1u) ^ 1u)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sa = su32(smem + s * STAGE), sb = sa + TILE;
-            const uint32_t full = su32(&bar[s]);
-            mb_expect(full, STAGE);
-            tma4(sa, &tmA, full, (kb0 + kb) * BK, (int)m0, (int)b, p.pi[pr]);
-            tma4(sb, &tmB, full, (kb0 + kb) * BK, (int)n0, (int)b, p.pj[pr]);
-          }
+      for (int it = 0; it < nk; ++it) {
+        const int st = it % nst;
+        if (!mb_wait(su32(&bar[nst + st]), ((uint32_t)(it / nst) & 1u) ^ 1u)) break;
+        const uint32_t base = su32(smem + (size_t)st * STAGE);
+        const uint32_t full = su32(&bar[st]);
+        mb_expect(full, STAGE);
+        const int kc = (ks0 + it) * KS;
+        for (int sl = 0; sl < ns; ++sl) {
+          tma4(base + sl * SLICE_TILE, &tmA, full, kc, (int)m0, (int)b, sl);
+          tma4(base + (ns + sl) * SLICE_TILE, &tmB, full, kc, (int)n0, (int)b, sl);
+        }
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------ MMA issuer
+      // per stage: every digit pair (i, j) from the resident slices.  Levels 0 / 1 are
+      // exact per chunk and drained by warps 2..9; at the first stage of a chunk the
+      // lower-level pairs go first, so they overlap the drain of the previous chunk.
+      // descriptors of slice tiles: the stage base's descriptor plus the byte offset / 16
+      constexpr uint64_t kTileStep = SLICE_TILE >> 4;
+      bool ok = true;
       int it = 0;
-      bool ok = true, h_started = false;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
-        if (ch > 0 && !mb_wait(su32(&bar[2 * STAGES + 1]), (uint32_t)(ch - 1) & 1u)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        bool l_started[2] = {false, false};
-        for (int kb = ch * CHUNK_KB; kb < min((ch + 1) * CHUNK_KB, nk) && ok; ++kb)
-          for (int pr = 0; pr < p.npairs; ++pr, ++it) {
-            const int s = it % STAGES;
-            if (!mb_wait(su32(&bar[s]), (uint32_t)(it / STAGES) & 1u)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int lvl = p.pl[pr];
-            const uint32_t acc_t = tmem + (uint32_t)(lvl * BN);
-            bool &started = lvl == 2 ? h_started : l_started[lvl];
-            const uint32_t sa = su32(smem + s * STAGE), sb = sa + TILE;
+        const int kbeg = ch * CHUNK_KS, kend = min((ch + 1) * CHUNK_KS, nk);
+        for (int ks = kbeg; ks < kend; ++ks, ++it) {
+          const int st = it % nst;
+          if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = sdesc(su32(smem + (size_t)st * STAGE));
+          const uint64_t db = da + (uint64_t)ns * kTileStep;
+          // lower levels (i + j >= 2) into H, which is never drained before the end
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint32_t accum = (started || kk > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc_t),
-                  "l"(sdesc(sa + kk * 32)), "l"(sdesc(sb + kk * 32)), "r"(kIdesc), "r"(accum)
-                  : "memory");
-            }
-            started = true;
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    su32(&bar[STAGES + s]))
-                : "memory");
+          for (int t = 2; t < ns; ++t)
+#pragma unroll
+            for (int i = 0; i <= t; ++i)
+              umma(tmem + 2 * BN, da + i * kTileStep, db + (t - i) * kTileStep,
+                   (it > 0 || t > 2 || i > 0) ? 1u : 0u);
+          // levels 0 / 1 restart every chunk; the previous chunk must be drained first
+          if (ks == kbeg && ch > 0) {
+            if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           }
-        // L0 / L1 of this chunk complete -> drain (the drainers also handle unused levels)
+          const uint32_t acc_l = ks > kbeg ? 1u : 0u;
+          umma(tmem, da, db, acc_l);
+          umma(tmem + BN, da, db + kTileStep, acc_l);
+          umma(tmem + BN, da + kTileStep, db, 1u);
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  su32(&bar[nst + st]))
+              : "memory");
+        }
+        if (!ok) break;
+        // levels 0 / 1 of this chunk complete -> drain
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                su32(&bar[2 * STAGES]))
+                su32(&bar[2 * nst]))
             : "memory");
-        (void)l_started;
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bar[2 * STAGES + 2]))
+              su32(&bar[2 * nst + 2]))
           : "memory");
-      (void)h_started;
     }
   } else if (warp < 10) {  // ------------------------------------------ drain warps 2..9
     const int ew = warp - 2;                  // 0..7
@@ -250,7 +269,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int j = 0; j < 64; ++j) S[j] = 0;
     bool ok = true;
     for (int ch = 0; ch < nchunks; ++ch) {
-      if (!mb_wait(su32(&bar[2 * STAGES]), (uint32_t)ch & 1u)) { ok = false; break; }
+      if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // L0 and L1 always have pairs (ns >= 3): exact integers of this chunk into S
 #pragma unroll
@@ -268,9 +287,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mb_arrive(su32(&bar[2 * STAGES + 1]));
+      mb_arrive(su32(&bar[2 * nst + 1]));
     }
-    bool done = ok && nchunks > 0 && mb_wait(su32(&bar[2 * STAGES + 2]), 0);
+    bool done = ok && nchunks > 0 && mb_wait(su32(&bar[2 * nst + 2]), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
     const int64_t ldc = p.to_ws ? p.N : p.ldc;
@@ -440,17 +459,18 @@ static CUtensorMap tmap(const void *base, int64_t Kp, int64_t rows, int64_t batc
   cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)ns};
   cuuint64_t strides[3] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2),
                            (cuuint64_t)(batch * rows * Kp * 2)};
-  cuuint32_t box[4] = {(cuuint32_t)BK, 128u, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)KS, 128u, 1, 1};   // 16 BF16 = 32-byte rows
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(TRG_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return m;
 }
 
-constexpr size_t kSmem = (size_t)STAGES * 2 * BM * BK * 2 + 1024 + 256;
+// stage ring + alignment slack + barriers and the TMEM address
+constexpr size_t kSmemMax = kStageBudget + 1024 + 256;
 
 }  // namespace oz
 
@@ -523,19 +543,22 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     }
   const int64_t gx = (M + BM - 1) / BM, gy = (N + BN - 1) / BN;
   if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: N too large");
-  const int nkb_total = (int)(Kp / BK);
+  const int nks_total = (int)(Kp / KS);
   int ksplit = 1;
   const int64_t tiles = gx * gy * batch;
-  if (tiles < 148 && nkb_total >= 2 * CHUNK_KB) {
+  if (tiles < 148 && nks_total >= 2 * CHUNK_KS) {
     ksplit = (int)std::min<int64_t>(std::min<int64_t>((2 * 148 + tiles - 1) / tiles,
-                                                      nkb_total / CHUNK_KB),
+                                                      nks_total / CHUNK_KS),
                                     65535 / batch);
     ksplit = std::max(ksplit, 1);
   }
-  int per = (nkb_total + ksplit - 1) / ksplit;
-  per = (per + CHUNK_KB - 1) / CHUNK_KB * CHUNK_KB;
-  ksplit = (nkb_total + per - 1) / per;
-  p.nkb = per;
+  int per = (nks_total + ksplit - 1) / ksplit;
+  per = (per + CHUNK_KS - 1) / CHUNK_KS * CHUNK_KS;
+  ksplit = (nks_total + per - 1) / per;
+  p.nks = per;
+  p.ns = ns;
+  p.stages = (int)std::min<size_t>(MAX_STAGES, kStageBudget / (2 * (size_t)ns * SLICE_TILE));
+  const size_t smem = (size_t)p.stages * 2 * ns * SLICE_TILE + 1024 + 256;
   if (ksplit > 1) {
     p.C = (double *)scr.alloc((size_t)ksplit * batch * M * N * sizeof(double));
     p.to_ws = 1;
@@ -550,11 +573,17 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   CUtensorMap ma = tmap(As, Kp, M, batch, ns), mb = tmap(Bs, Kp, N, batch, ns);
   static bool attr = false;
   if (!attr) {
-    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmem));
+    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemMax));
+    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemMax));
+    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemMax));
+    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemMax));
     attr = true;
     if (getenv("TRG_DEBUG_ATTR")) {
-      const void *fns[4] = {(const void *)oz_gemm_kernel, (const void *)oz_rowexp_kernel,
+      const void *fns[4] = {(const void *)oz_gemm_kernel<5>, (const void *)oz_rowexp_kernel,
                             (const void *)oz_split_kernel, (const void *)oz_ws_reduce};
       for (int i = 0; i < 4; ++i) {
         cudaFuncAttributes fa;
@@ -564,12 +593,17 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
                 fa.maxDynamicSharedSizeBytes, fa.localSizeBytes);
       }
       fprintf(stderr, "launch: grid %lld %lld %lld threads %d smem %zu params %zu\n", (long long)gx,
-              (long long)gy, (long long)(batch * ksplit), THREADS, kSmem, sizeof(Params));
+              (long long)gy, (long long)(batch * ksplit), THREADS, smem, sizeof(Params));
     }
   }
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
   if (timing) timing->before(s);
-  oz_gemm_kernel<<<grid, THREADS, kSmem, s>>>(ma, mb, p);
+  switch (ns) {
+    case 3: oz_gemm_kernel<3><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    case 4: oz_gemm_kernel<4><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    case 5: oz_gemm_kernel<5><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    default: oz_gemm_kernel<6><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+  }
   TRG_LAUNCH_CHECK();
   if (timing) timing->after(s, 2.0 * (double)M * N * K * batch * p.npairs);
   if (ksplit > 1) {

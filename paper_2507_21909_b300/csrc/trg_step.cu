@@ -7,6 +7,7 @@
 // host never waits on device data inside a step except for the final status read.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -158,6 +159,11 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
                  const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
   const double work = (double)M * N * K * batch;
+  static const bool dbg = getenv("TRG_DEBUG_GEMM") != nullptr;
+  if (dbg)
+    fprintf(stderr, "gemm phase %d M %lld N %lld K %lld batch %lld ta %d tb %d crit %d cheap %d\n",
+            c.phase, (long long)M, (long long)N, (long long)K, (long long)batch, (int)ta, (int)tb,
+            c.crit_depth, c.bulk_cheap);
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
       work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
       K >= 16 && !(c.b_upper && N < c.tc_min_max)) {
