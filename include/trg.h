@@ -156,6 +156,69 @@ trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long M, long lon
                             const double *B, long long ldb, double beta, double *C,
                             long long ldc, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * Learned sketch of the triad-isometry range finders (Sec. II B, eq. HOSVD: U^A, U^X,
+ * U^Y, U^D are ranges of the Grams rho over a leg pair (a, b), n = d_a d_b).  The paper
+ * draws a Gaussian sketch G (n x chi); the learned form keeps the same G and rescales
+ * its rows, Omega[(a b), m] = w1[a] w2[b] G[(a b), m], w_l[i] = 2^(round(16 u_l[i])/16)
+ * (clamped to 2^-8..2^8), with u_l[i] the output of a 3-layer MLP (5 -> 256 -> 256 -> 1,
+ * ReLU, FP32 weights, BF16 inference) on five statistics of index i of leg l: (i+0.5)/d_l,
+ * log2(m_i d_l)/8 with m_i the share of tr(rho) on index i's diagonal entries,
+ * log2(d_l)/8, log2(d_other)/8 and chi/n.  The learned range is kept unless its probe
+ * residual ||rho P - Q Q^T rho P||_F (8 Gaussian probe columns) exceeds 1.5x that of the
+ * plain range, which is then used instead.  Training targets are 0.5 log2(leverage d_l)
+ * of each leg index in the plain method's range.
+ *
+ * Parameters: one flat FP32 array of TRG_SKETCH_PARAMS values, in the order W1 (256 x 5,
+ * row-major), b1 (256), W2 (256 x 256), b2 (256), W3 (256), b3 (1).
+ * ------------------------------------------------------------------------------- */
+#define TRG_SKETCH_IN 5
+#define TRG_SKETCH_PARAMS 67585
+
+/* Load the network (host FP32 array of n = TRG_SKETCH_PARAMS values; copied). Resets
+ * the Adam moments.  Errors: TRG_ERR_ARG (wrong n or NULL), TRG_ERR_CUDA. */
+trg_status trg_sketch_set_net(const float *params, long long n);
+
+/* Copy the current network to the host (n = TRG_SKETCH_PARAMS).  TRG_ERR_NOINIT if none
+ * was loaded. */
+trg_status trg_sketch_get_net(float *params, long long n);
+
+/* u[r] for rows x TRG_SKETCH_IN host inputs X (row-major); bf16 != 0: the inference
+ * kernel used inside trg_step (BF16 inputs, weights and activations, FP32 sums),
+ * bf16 == 0: the FP32 training forward pass.  Host buffers; synchronous. */
+trg_status trg_sketch_forward(const float *X, long long rows, float *u, int bf16);
+
+/* Loss L = mean (u - t)^2 of the FP32 network over rows (X rows x 5, t rows; host) and
+ * its gradient (host, TRG_SKETCH_PARAMS floats, parameter order as above). */
+trg_status trg_sketch_grad(const float *X, const float *t, long long rows, double *loss,
+                           float *grad);
+
+/* Adam (beta 0.9, 0.999, eps 1e-8, rate lr) over `epochs` passes of shuffled minibatches
+ * of `batch` rows (host std::mt19937_64(seed) permutation; a ragged last batch is
+ * skipped); *loss = mean loss of the last epoch.  The network must be loaded. */
+trg_status trg_sketch_train(const float *X, const float *t, long long rows, int epochs,
+                            int batch, float lr, unsigned long long seed, double *loss);
+
+/* 0: Gaussian sketches (the paper's form, default); 1: learned sketch with the plain
+ * range as fallback.  TRG_ERR_NOINIT for 1 without a loaded network. */
+trg_status trg_set_sketch_mode(int mode);
+
+/* Collect training rows during trg_step: every triad range finder (with chi < n) appends
+ * d_a + d_b rows (inputs, target) computed from its plain range, up to `capacity` rows
+ * (later rows are counted as dropped).  capacity 0 stops collecting and frees the
+ * buffer; a new call discards earlier rows. */
+trg_status trg_sketch_collect(long long capacity);
+
+/* Copy the collected rows to the host: X (capacity x 5 floats), t (capacity floats);
+ * either may be NULL (then only *rows / *dropped are written).  TRG_ERR_ARG if
+ * capacity < the number of collected rows. */
+trg_status trg_sketch_fetch(float *X, float *t, long long capacity, long long *rows,
+                            long long *dropped);
+
+/* Range finders that kept the learned range / fell back to the plain one since the last
+ * reset (reset != 0 zeroes the counters after reading). */
+trg_status trg_sketch_stats(long long *learned, long long *fallback, int reset);
+
 /* Release every device buffer of the context. */
 trg_status trg_finalize(void);
 

@@ -358,7 +358,7 @@ def squeezer(rho_f: np.ndarray, rho_b: np.ndarray, D: int, chi: int, q_rho: int,
 # ----------------------------------------------------------------------------------
 # (c)-(f): the triad step in four dimensions
 # ----------------------------------------------------------------------------------
-def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None):
+def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, mlp=None):
     """One triad-ATRG step on the re-split factors.  Legs (per site):
     A (t=i1(n+1), p2,p3,p4, al)   C = A s  (x=i1(n), q2,q3,q4, be)
     B = Dm s (x=j1(n+1)=i1(n), P2,P3,P4, al)   Dm (w=j1(n), Q2,Q3,Q4, be)
@@ -381,9 +381,17 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None):
     rhoD = np.tensordot(np.tensordot(Dm, W_be, axes=([4], [0])), Dm, axes=([0, 3, 4], [0, 3, 4]))
     chi = min(D + p, chi_pair)
     U = {}
+    sketch_info = {}
     for name, rho in (("A", rhoA), ("X", rhoX), ("Y", rhoY), ("D", rhoD)):
-        U[name] = rsvd_range_sym(rho.reshape(chi_pair, chi_pair), chi, q_rho,
-                                 sketch_key(seed, step, TAG_RHO[name])).reshape(d2, d3, -1)
+        key = sketch_key(seed, step, TAG_RHO[name])
+        if mlp is None:
+            Q = rsvd_range_sym(rho.reshape(chi_pair, chi_pair), chi, q_rho, key)
+        else:  # learned sketch with the plain range as fallback (oracle/sketch_mlp.py)
+            from . import sketch_mlp as SM
+            Q, sketch_info[name] = SM.rsvd_learned(
+                mlp, rho.reshape(chi_pair, chi_pair), d2, d3, chi, q_rho, key,
+                sketch_key(seed, step, SM.TAG_PROBE[name]))
+        U[name] = Q.reshape(d2, d3, -1)
 
     # (d) triads, eqs. E-L
     E = np.einsum("tbcda,bck->tkda", A, U["A"])
@@ -462,6 +470,8 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None):
         psi_imp = 0.5 * (contract_lower(G_imp, H, K_, L_, Nsq) +
                          contract_lower(G, H_imp, K_, L_, Nsq))
     diag = {"gap_swap": gap_swap, "gap_sq": gaps, "sigma": sig, "s": s}
+    if sketch_info:
+        diag["sketch"] = sketch_info
     return phi, psi, psi_imp, diag
 
 
@@ -543,8 +553,10 @@ def _rotate(st: State, axis: int):
 
 
 def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
-         seed: int = 0x5EED, method: str = "triad") -> State:
-    """One coarse-graining step along physical `axis` (in place; returns st)."""
+         seed: int = 0x5EED, method: str = "triad", mlp: dict | None = None) -> State:
+    """One coarse-graining step along physical `axis` (in place; returns st).  `mlp`
+    (parameters of oracle/sketch_mlp.py) selects the learned sketch of the triad
+    isometries."""
     if D < 1 or p < 0:
         raise ValueError("need D >= 1 and p >= 0")
     _rotate(st, axis)
@@ -553,7 +565,8 @@ def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
         if st.d != 4:
             raise ValueError("triad-ATRG is defined for d = 4")
         imp = (st.phi, st.psi_imp) if st.psi_imp is not None else None
-        phi, psi, psi_imp, diag = _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, imp)
+        phi, psi, psi_imp, diag = _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, imp,
+                                              mlp)
     elif method == "atrg":
         phi, psi, psi_imp, diag = _atrg_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps)
     else:
@@ -589,11 +602,11 @@ def magnetisation(st: State) -> float:
 
 def run(model: str, d: int, beta: float, h: float, D: int, p: int, nsteps: int,
         q_swap: int = 4, q_rho: int = 4, seed: int = 0x5EED, method: str = "triad",
-        axes=None) -> State:
+        axes=None, mlp: dict | None = None) -> State:
     """Convenience driver: nsteps steps cycling the axes 0,1,..,d-1 (or `axes`)."""
     st = init_ising(d, beta, h) if model == "ising" else init_clock(d, 3, beta, h)
     for n in range(nsteps):
         ax = (n % d) if axes is None else axes[n]
-        step(st, ax, D, p, q_swap, q_rho, seed, method)
+        step(st, ax, D, p, q_swap, q_rho, seed, method, mlp)
     return st
 

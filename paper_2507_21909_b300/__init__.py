@@ -9,7 +9,10 @@ _NAMES = ("TRG_PREC_BF16X3", "TRG_PREC_BF16X10", "TRG_PREC_OZ4", "TRG_PREC_OZ5",
           "library_path", "trg_diag", "trg_finalize", "trg_free_energy", "trg_get_state",
           "trg_init_clock", "trg_init_ising", "trg_magnetisation_impurity", "trg_set_params",
           "trg_set_state", "trg_set_stream", "trg_step", "EXPORTED", "trg_step_timings",
-          "PHASES", "trg_gemm", "trg_kernel_stats", "trg_state_dims", "trg_mem_stats")
+          "PHASES", "trg_gemm", "trg_kernel_stats", "trg_state_dims", "trg_mem_stats",
+          "TRG_SKETCH_IN", "TRG_SKETCH_PARAMS", "trg_sketch_set_net", "trg_sketch_get_net",
+          "trg_sketch_forward", "trg_sketch_grad", "trg_sketch_train", "trg_set_sketch_mode",
+          "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats")
 
 
 def __getattr__(name):

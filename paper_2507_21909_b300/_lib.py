@@ -13,7 +13,11 @@ EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
             "trg_step_timings", "trg_gemm", "trg_kernel_stats", "trg_mem_stats",
-            "trg_gemm_noalloc"]
+            "trg_gemm_noalloc", "trg_sketch_set_net", "trg_sketch_get_net",
+            "trg_sketch_forward", "trg_sketch_grad", "trg_sketch_train", "trg_set_sketch_mode",
+            "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats"]
+
+TRG_SKETCH_IN, TRG_SKETCH_PARAMS = 5, 67585
 
 
 class TrgError(RuntimeError):
@@ -32,6 +36,8 @@ def _load():
     L = ctypes.CDLL(_PATH)
     d, i, ull, vp = ctypes.c_double, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p
     pd, pi = ctypes.POINTER(d), ctypes.POINTER(i)
+    ll, pf = ctypes.c_longlong, ctypes.POINTER(ctypes.c_float)
+    pll = ctypes.POINTER(ll)
     sig = {
         "trg_init_ising": [i, d, d], "trg_init_clock": [i, i, d, d], "trg_step": [i, i, i],
         "trg_free_energy": [pd, pd], "trg_magnetisation_impurity": [pd],
@@ -47,6 +53,11 @@ def _load():
                              ctypes.POINTER(ctypes.c_longlong), i],
         "trg_gemm": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d, pd,
                      ctypes.c_longlong, pd, ctypes.c_longlong, d, pd, ctypes.c_longlong],
+        "trg_sketch_set_net": [pf, ll], "trg_sketch_get_net": [pf, ll],
+        "trg_sketch_forward": [pf, ll, pf, i], "trg_sketch_grad": [pf, pf, ll, pd, pf],
+        "trg_sketch_train": [pf, pf, ll, i, i, ctypes.c_float, ull, pd],
+        "trg_set_sketch_mode": [i], "trg_sketch_collect": [ll],
+        "trg_sketch_fetch": [pf, pf, ll, pll, pll], "trg_sketch_stats": [pll, pll, i],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -182,3 +193,75 @@ def trg_mem_stats():
 
 def trg_finalize():
     _check(lib.trg_finalize())
+
+
+# ------------------------------------------------------------------ learned sketch
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _pf(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def trg_sketch_set_net(params):
+    """Load the sketch network (flat FP32 array of TRG_SKETCH_PARAMS values)."""
+    p = _f32(params).reshape(-1)
+    _check(lib.trg_sketch_set_net(_pf(p), p.size))
+
+
+def trg_sketch_get_net():
+    out = np.empty(TRG_SKETCH_PARAMS, dtype=np.float32)
+    _check(lib.trg_sketch_get_net(_pf(out), out.size))
+    return out
+
+
+def trg_sketch_forward(X, bf16=True):
+    X = _f32(X)
+    u = np.empty(X.shape[0], dtype=np.float32)
+    _check(lib.trg_sketch_forward(_pf(X), X.shape[0], _pf(u), int(bool(bf16))))
+    return u
+
+
+def trg_sketch_grad(X, t):
+    X, t = _f32(X), _f32(t)
+    g = np.empty(TRG_SKETCH_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(lib.trg_sketch_grad(_pf(X), _pf(t), X.shape[0], ctypes.byref(loss), _pf(g)))
+    return loss.value, g
+
+
+def trg_sketch_train(X, t, epochs, batch, lr, seed=0):
+    X, t = _f32(X), _f32(t)
+    loss = ctypes.c_double()
+    _check(lib.trg_sketch_train(_pf(X), _pf(t), X.shape[0], int(epochs), int(batch),
+                                float(lr), int(seed), ctypes.byref(loss)))
+    return loss.value
+
+
+def trg_set_sketch_mode(mode):
+    _check(lib.trg_set_sketch_mode(int(mode)))
+
+
+def trg_sketch_collect(capacity):
+    _check(lib.trg_sketch_collect(int(capacity)))
+
+
+def trg_sketch_fetch():
+    rows, dropped = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib.trg_sketch_fetch(None, None, 0, ctypes.byref(rows), ctypes.byref(dropped)))
+    n = rows.value
+    X = np.empty((max(n, 1), TRG_SKETCH_IN), dtype=np.float32)
+    t = np.empty(max(n, 1), dtype=np.float32)
+    _check(lib.trg_sketch_fetch(_pf(X), _pf(t), max(n, 1), ctypes.byref(rows),
+                                ctypes.byref(dropped)))
+    return X[:n], t[:n], dropped.value
+
+
+def trg_sketch_stats(reset=False):
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib.trg_sketch_stats(ctypes.byref(a), ctypes.byref(b), int(reset)))
+    return {"learned": a.value, "fallback": b.value}

@@ -16,6 +16,7 @@
 
 #include "gemm_oz.h"
 #include "gemm_tc.h"
+#include "sketch_mlp.h"
 #include "trg_internal.h"
 
 namespace trg {
@@ -26,7 +27,7 @@ constexpr double kPivotTol = 1e-13;    // dead-pivot threshold of the later pass
 
 // sketch tags of one step (same numbering in every implementation of the method)
 enum { TAG_SWAP_G1 = 1, TAG_SWAP_G2 = 2, TAG_RHO_A = 3, TAG_RHO_X = 4, TAG_RHO_Y = 5,
-       TAG_RHO_D = 6, TAG_SQ_F2 = 7, TAG_SQ_B2 = 10 };
+       TAG_RHO_D = 6, TAG_SQ_F2 = 7, TAG_SQ_B2 = 10, TAG_PROBE_A = 13 };
 
 struct Ctx {
   cudaStream_t stream = nullptr;
@@ -53,6 +54,12 @@ struct Ctx {
   int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   bool b_upper = false;        // the next GEMM's right factor is upper triangular (R^-1)
+  // learned sketch of the triad-isometry range finders
+  SketchNet net;
+  int sketch_mode = 0;                      // 0 Gaussian, 1 learned (plain as fallback)
+  unsigned long long *d_sketch_cnt = nullptr;  // [0] learned kept, [1] fell back
+  float *col_x = nullptr, *col_t = nullptr;    // collected (features, target) rows
+  long long col_cap = 0, col_rows = 0, col_dropped = 0;
   uint64_t seed = 0x5EED;
   double last_logc = 0.0, last_gap = INFINITY;
   static constexpr int kPhases = 8;
@@ -372,15 +379,85 @@ static Tensor identity(Ctx &c, int64_t n) {
   return t;
 }
 
+// orthonormal basis of range(rho^(q+1) Omega)
+static Tensor range_from(Ctx &c, const Tensor &rho, const Tensor &Om, int q) {
+  Tensor Q = orth_sc(c, mm(c, rho, Om, false, false));
+  for (int i = 0; i < q; ++i) Q = orth_sc(c, mm(c, rho, Q, false, false));
+  return Q;
+}
+
 // orthonormal basis (n x chi) of range(rho^(q+1) Omega), or the identity if chi >= n
 static Tensor rsvd_sym(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t key) {
   int64_t n = rho.dims[0];
   if (chi >= n) return identity(c, n);
   Tensor Om = c.alloc({n, chi});
   fill_gaussian(Om.p, n, chi, key, c.stream);
-  Tensor Q = orth_sc(c, mm(c, rho, Om, false, false));
-  for (int i = 0; i < q; ++i) Q = orth_sc(c, mm(c, rho, Q, false, false));
-  return Q;
+  return range_from(c, rho, Om, q);
+}
+
+// squared probe residual ||P - Q Q^T P||_F^2 into *out (device)
+static void probe_residual2(Ctx &c, const Tensor &Q, const Tensor &P, double *out) {
+  Arena::Mark mk = c.arena.mark();
+  Tensor T = mm(c, Q, P, true, false);
+  Tensor E = copy(c, P);
+  gemm(c, false, false, Q.dims[0], P.dims[1], Q.dims[1], -1.0, Q.p, Q.dims[1], 0, T.p,
+       P.dims[1], 0, 1.0, E.p, P.dims[1], 0, 1);
+  Tensor scratch = c.alloc({1024});
+  dot(E.p, E.p, E.size(), out, scratch.p, c.stream);
+  c.arena.release(mk);
+}
+
+// Range of a triad Gram rho over legs (da, db).  Plain form: the Gaussian sketch.  Learned
+// form: the same Gaussian with rows rescaled by the sketch network, kept unless its
+// probe residual exceeds 1.5x the plain range's (then the plain range).  With collection
+// on, the (features, leverage target) rows of both legs are appended from the plain range.
+static Tensor range_rho(Ctx &c, const Tensor &rho, int64_t da, int64_t db, int64_t chi, int q,
+                        uint64_t key, uint64_t key_probe) {
+  const int64_t n = rho.dims[0];
+  if (chi >= n) return identity(c, n);
+  const bool learned = c.sketch_mode == 1 && c.net.loaded;
+  const bool collect = c.col_cap > 0;
+  if (!learned && !collect) return rsvd_sym(c, rho, chi, q, key);
+  cudaStream_t s = c.stream;
+  Tensor out = c.alloc({n, chi});
+  Arena::Mark mk = c.arena.mark();
+  Tensor G = c.alloc({n, chi});
+  fill_gaussian(G.p, n, chi, key, s);
+  Tensor Qp = range_from(c, rho, G, q);
+  Tensor F = c.alloc({(da + db) * kMlpIn / 2 + 1});   // (da + db) x 5 floats
+  sketch_features(rho.p, (int)da, (int)db, (int)chi, reinterpret_cast<float *>(F.p), s);
+  if (collect) {
+    const long long r = da + db;
+    if (c.col_rows + r <= c.col_cap) {
+      TRG_CUDA(cudaMemcpyAsync(c.col_x + c.col_rows * kMlpIn, F.p, r * kMlpIn * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s));
+      leverage_targets(Qp.p, (int)da, (int)db, (int)chi, c.col_t + c.col_rows, s);
+      c.col_rows += r;
+    } else {
+      c.col_dropped += r;
+    }
+  }
+  if (!learned) {
+    TRG_CUDA(cudaMemcpyAsync(out.p, Qp.p, out.size() * 8, cudaMemcpyDeviceToDevice, s));
+    c.arena.release(mk);
+    return out;
+  }
+  Tensor U = c.alloc({(da + db) / 2 + 1});                 // da + db floats
+  float *u = reinterpret_cast<float *>(U.p);
+  mlp_forward(c.net, reinterpret_cast<const float *>(F.p), da + db, u, true, s);
+  Tensor w = c.alloc({n});
+  sketch_row_weights(u, (int)da, (int)db, w.p, s);
+  scale_rows(G.p, n, chi, w.p, s);
+  Tensor Ql = range_from(c, rho, G, q);
+  Tensor P0 = c.alloc({n, 8});
+  fill_gaussian(P0.p, n, 8, key_probe, s);
+  Tensor P = mm(c, rho, P0, false, false);
+  Tensor r2 = c.alloc({2});
+  probe_residual2(c, Ql, P, r2.p);
+  probe_residual2(c, Qp, P, r2.p + 1);
+  select_range(Ql.p, Qp.p, out.size(), r2.p, r2.p + 1, 1.5 * 1.5, out.p, c.d_sketch_cnt, s);
+  c.arena.release(mk);
+  return out;
 }
 
 // R (c' x n) with R^T R = Q Q^T rho Q Q^T, Q the rank-chi range of rho.  R = L Q^T with
@@ -672,7 +749,8 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   const int64_t chi = std::min<int64_t>(D + p, npair);
   auto iso = [&](Tensor &rho, int tag) {
     Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
-      return rsvd_sym(c, view(rho.p, {npair, npair}), chi, c.q_rho, key(tag));
+      return range_rho(c, view(rho.p, {npair, npair}), d2, d3, chi, c.q_rho, key(tag),
+                       key(TAG_PROBE_A + tag - TAG_RHO_A));
     });
     U.dims = {d2, d3, U.dims[1]};
     return U;
@@ -816,6 +894,8 @@ static void ensure_ctx(Ctx &c) {
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
+    TRG_CUDA(cudaMalloc(&c.d_sketch_cnt, 2 * sizeof(unsigned long long)));
+    TRG_CUDA(cudaMemset(c.d_sketch_cnt, 0, 2 * sizeof(unsigned long long)));
   }
   if (!c.stream && !c.own_stream) {
     TRG_CUDA(cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking));
@@ -1093,6 +1173,137 @@ trg_status trg_step_timings(double *ms, int n) {
     Ctx &c = ctx();
     if (!ms || n < 0) throw Error(TRG_ERR_ARG, "bad timing buffer");
     for (int i = 0; i < n && i < Ctx::kPhases; ++i) ms[i] = c.phase_ms[i];
+  });
+}
+
+// ------------------------------------------------------------ learned sketch (S15)
+namespace {
+struct DevF {  // device copy of a host float array, freed on scope exit
+  float *p = nullptr;
+  DevF(const float *h, int64_t n, cudaStream_t s) {
+    TRG_CUDA(cudaMalloc(&p, std::max<int64_t>(n, 1) * sizeof(float)));
+    if (h) TRG_CUDA(cudaMemcpyAsync(p, h, n * sizeof(float), cudaMemcpyHostToDevice, s));
+  }
+  ~DevF() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+trg_status trg_sketch_set_net(const float *params, long long n) {
+  return guarded([&] {
+    if (!params || n != kMlpParams) throw Error(TRG_ERR_ARG, "sketch net: need TRG_SKETCH_PARAMS floats");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    mlp_set(c.net, params, c.stream);
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+  });
+}
+
+trg_status trg_sketch_get_net(float *params, long long n) {
+  return guarded([&] {
+    if (!params || n != kMlpParams) throw Error(TRG_ERR_ARG, "sketch net: need TRG_SKETCH_PARAMS floats");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    mlp_get(c.net, params, c.stream);
+  });
+}
+
+trg_status trg_sketch_forward(const float *X, long long rows, float *u, int bf16) {
+  return guarded([&] {
+    if (!X || !u || rows < 1) throw Error(TRG_ERR_ARG, "sketch forward: bad arguments");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    DevF dX(X, rows * kMlpIn, c.stream), du(nullptr, rows, c.stream);
+    mlp_forward(c.net, dX.p, rows, du.p, bf16 != 0, c.stream);
+    TRG_CUDA(cudaMemcpyAsync(u, du.p, rows * sizeof(float), cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+  });
+}
+
+trg_status trg_sketch_grad(const float *X, const float *t, long long rows, double *loss,
+                           float *grad) {
+  return guarded([&] {
+    if (!X || !t || !grad || rows < 1) throw Error(TRG_ERR_ARG, "sketch grad: bad arguments");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    DevF dX(X, rows * kMlpIn, c.stream), dt(t, rows, c.stream), dg(nullptr, kMlpParams, c.stream);
+    const double L = mlp_grad(c.net, dX.p, dt.p, rows, dg.p, c.stream);
+    TRG_CUDA(cudaMemcpyAsync(grad, dg.p, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost,
+                             c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    if (loss) *loss = L;
+  });
+}
+
+trg_status trg_sketch_train(const float *X, const float *t, long long rows, int epochs,
+                            int batch, float lr, unsigned long long seed, double *loss) {
+  return guarded([&] {
+    if (!X || !t || rows < 1 || epochs < 1 || batch < 1 || !(lr > 0.f))
+      throw Error(TRG_ERR_ARG, "sketch train: bad arguments");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    DevF dX(X, rows * kMlpIn, c.stream), dt(t, rows, c.stream);
+    const double L = mlp_train(c.net, dX.p, dt.p, rows, epochs, batch, lr, seed, c.stream);
+    if (loss) *loss = L;
+  });
+}
+
+trg_status trg_set_sketch_mode(int mode) {
+  return guarded([&] {
+    if (mode != 0 && mode != 1) throw Error(TRG_ERR_ARG, "sketch mode must be 0 or 1");
+    Ctx &c = ctx();
+    if (mode == 1 && !c.net.loaded) throw Error(TRG_ERR_NOINIT, "no sketch network loaded");
+    c.sketch_mode = mode;
+  });
+}
+
+trg_status trg_sketch_collect(long long capacity) {
+  return guarded([&] {
+    if (capacity < 0) throw Error(TRG_ERR_ARG, "negative capacity");
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    if (c.col_x) cudaFree(c.col_x);
+    if (c.col_t) cudaFree(c.col_t);
+    c.col_x = c.col_t = nullptr;
+    c.col_cap = c.col_rows = c.col_dropped = 0;
+    if (capacity == 0) return;
+    if (cudaMalloc(&c.col_x, capacity * kMlpIn * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c.col_t, capacity * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(TRG_ERR_OOM, "collection buffer allocation failed");
+    }
+    c.col_cap = capacity;
+  });
+}
+
+trg_status trg_sketch_fetch(float *X, float *t, long long capacity, long long *rows,
+                            long long *dropped) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (rows) *rows = c.col_rows;
+    if (dropped) *dropped = c.col_dropped;
+    if (!X && !t) return;
+    if (capacity < c.col_rows) throw Error(TRG_ERR_ARG, "fetch buffer too small");
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    if (X && c.col_rows)
+      TRG_CUDA(cudaMemcpy(X, c.col_x, c.col_rows * kMlpIn * sizeof(float), cudaMemcpyDeviceToHost));
+    if (t && c.col_rows)
+      TRG_CUDA(cudaMemcpy(t, c.col_t, c.col_rows * sizeof(float), cudaMemcpyDeviceToHost));
+  });
+}
+
+trg_status trg_sketch_stats(long long *learned, long long *fallback, int reset) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    ensure_ctx(c);
+    unsigned long long h[2] = {0, 0};
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    TRG_CUDA(cudaMemcpy(h, c.d_sketch_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    if (learned) *learned = (long long)h[0];
+    if (fallback) *fallback = (long long)h[1];
+    if (reset) TRG_CUDA(cudaMemset(c.d_sketch_cnt, 0, sizeof(h)));
   });
 }
 
