@@ -163,7 +163,7 @@ trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long M, long lon
  * its rows, Omega[(a b), m] = w1[a] w2[b] G[(a b), m], w_l[i] = 2^(round(16 u_l[i])/16)
  * (clamped to 2^-8..2^8), with u_l[i] the output of a 3-layer MLP (5 -> 256 -> 256 -> 1,
  * ReLU, FP32 weights, BF16 inference) on five statistics of index i of leg l: (i+0.5)/d_l,
- * log2(m_i d_l)/8 with m_i the share of tr(rho) on index i's diagonal entries,
+ * log2(max(m_i d_l, 2^-40))/8 with m_i the share of tr(rho) on index i's diagonal entries,
  * log2(d_l)/8, log2(d_other)/8 and chi/n.  The learned range is kept unless its probe
  * residual ||rho P - Q Q^T rho P||_F (8 Gaussian probe columns) exceeds 1.5x that of the
  * plain range, which is then used instead.  Training targets are 0.5 log2(leverage d_l)

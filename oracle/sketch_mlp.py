@@ -12,7 +12,8 @@ clamped to [-8, 8] (a quantised code, so that the GPU and this oracle take the s
 integer decision).  w = 1 is the paper's plain sketch.  Readings (listed in the design doc):
 
   * Inputs per leg index i (NIN = 5): (i + 0.5)/d_l, log2(m_i d_l)/8 with m_i the share
-    of tr(rho) on the diagonal entries of index i (clipped at 2^-64), log2(d_l)/8,
+    of tr(rho) on the diagonal entries of index i (m_i d_l clipped at 2^-40, above the
+    rounding level of entries that vanish by symmetry), log2(d_l)/8,
     log2(d_other)/8, chi/n.  The leg bases are re-chosen by the squeezers between steps,
     so the previous step's isometry has no index-wise meaning here; the diagonal share of
     rho carries the same information about where the range lives.
@@ -150,7 +151,7 @@ def leg_features(rho: np.ndarray, da: int, db: int, chi: int) -> tuple[np.ndarra
     def feats(m, d, dother):
         F = np.empty((d, NIN))
         F[:, 0] = (np.arange(d) + 0.5) / d
-        F[:, 1] = np.log2(np.maximum(m * d, 2.0 ** -64)) / 8.0
+        F[:, 1] = np.log2(np.maximum(m * d, 2.0 ** -40)) / 8.0
         F[:, 2] = np.log2(d) / 8.0
         F[:, 3] = np.log2(dother) / 8.0
         F[:, 4] = chi / n

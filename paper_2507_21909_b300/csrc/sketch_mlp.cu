@@ -444,7 +444,7 @@ __global__ void features_kernel(const double *rho, int da, int db, int chi, floa
     m = tr > 0.0 ? m / tr : 0.0;
     float *f = F + (int64_t)row * kMlpIn;
     f[0] = (float)((i + 0.5) / d);
-    f[1] = (float)(log2(fmax(m * d, 0x1.0p-64)) / 8.0);
+    f[1] = (float)(log2(fmax(m * d, 0x1.0p-40)) / 8.0);  // floor above rounding noise
     f[2] = (float)(log2((double)d) / 8.0);
     f[3] = (float)(log2((double)dother) / 8.0);
     f[4] = (float)((double)chi / n);

@@ -1,0 +1,184 @@
+"""Learned sketch (S15) on the GPU against the oracle (oracle/sketch_mlp.py).
+
+* BF16 inference: bit-identical to the oracle's statement of the same arithmetic (the
+  quantised weight codes are integer decisions, so they must agree exactly).
+* FP32 forward and gradient: within 1e-5 / 1e-4 relative of the FP64 oracle.
+* Collected training rows (inputs and leverage targets) equal the oracle's for the same
+  run (float32 rounding).
+* Learned-sketch steps: f to 1e-10 of the oracle running the same network; the learned /
+  fallback decisions agree.
+* Gain: a network trained on the GPU, from rows the plain GPU method collected, judged
+  by the oracle's probe residual of one-pass range finders on a run it was not trained on.
+"""
+import numpy as np
+import pytest
+
+from oracle import sketch_mlp as SM
+from oracle import trg_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+@pytest.fixture(scope="module")
+def trg(require_gpu):
+    import paper_2507_21909_b300 as pkg
+    return pkg
+
+
+def to_flat(p):
+    return np.concatenate([p[k].reshape(-1) for k in ORDER]).astype(np.float32)
+
+
+def to_dict(flat):
+    flat = np.asarray(flat, dtype=np.float64)
+    shapes = {"W1": (SM.NHID, SM.NIN), "b1": (SM.NHID,), "W2": (SM.NHID, SM.NHID),
+              "b2": (SM.NHID,), "W3": (1, SM.NHID), "b3": (1,)}
+    out, o = {}, 0
+    for k in ORDER:
+        n = int(np.prod(shapes[k]))
+        out[k] = flat[o:o + n].reshape(shapes[k])
+        o += n
+    assert o == flat.size
+    return out
+
+
+def random_net(seed, bias=0.1):
+    p = SM.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    for k in ("b1", "b2", "b3"):
+        p[k] = (rng.standard_normal(p[k].shape) * bias).astype(np.float32).astype(np.float64)
+    return p
+
+
+def test_bf16_inference_bit_exact(trg):
+    p = random_net(7)
+    trg.trg_sketch_set_net(to_flat(p))
+    rng = np.random.default_rng(3)
+    X = np.concatenate([rng.standard_normal((70, SM.NIN)), rng.uniform(-1, 1, (33, SM.NIN))])
+    X = X.astype(np.float32)
+    got = trg.trg_sketch_forward(X, bf16=True)
+    ref = SM.forward_bf16(p, X.astype(np.float64)).astype(np.float32)
+    assert np.array_equal(got, ref), np.abs(got - ref).max()
+
+
+def test_fp32_forward_and_gradient(trg):
+    p = random_net(8)
+    trg.trg_sketch_set_net(to_flat(p))
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((300, SM.NIN)).astype(np.float32)
+    t = rng.standard_normal(300).astype(np.float32)
+    u = trg.trg_sketch_forward(X, bf16=False)
+    u_ref, _ = SM.forward(p, X.astype(np.float64))
+    assert np.abs(u - u_ref).max() <= 1e-5 * (1 + np.abs(u_ref).max())
+    loss, g = trg.trg_sketch_grad(X, t)
+    loss_ref, g_ref = SM.loss_and_grads(p, X.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    gr = to_flat(g_ref).astype(np.float64)
+    assert np.abs(g - gr).max() <= 1e-4 * np.abs(gr).max()
+
+
+def test_training_reduces_loss(trg):
+    teacher = random_net(9, bias=0.3)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (4096, SM.NIN)).astype(np.float32)
+    t = SM.forward(teacher, X.astype(np.float64))[0].astype(np.float32)
+    trg.trg_sketch_set_net(to_flat(random_net(10)))
+    l0, _ = trg.trg_sketch_grad(X, t)
+    l1 = trg.trg_sketch_train(X, t, epochs=30, batch=256, lr=1e-3, seed=1)
+    assert l1 < 0.2 * l0, (l0, l1)
+
+
+def _oracle_rows(beta, h, D, p, nsteps):
+    """Inputs and leverage targets of every range finder of an oracle run (order A, X, Y,
+    D per step; legs 1 then 2), from the oracle's own converged ranges."""
+    rows_x, rows_t = [], []
+    orig = O.rsvd_range_sym
+
+    def spy(rho, chi, q, key):
+        Q = orig(rho, chi, q, key)
+        f = __import__("sys")._getframe(1).f_locals
+        if "chi_pair" not in f:      # a squeezer's range finder, not a triad isometry
+            return Q
+        da, db = f["d2"], f["d3"]
+        if chi < rho.shape[0]:
+            F1, F2 = SM.leg_features(rho, da, db, chi)
+            t1, t2 = SM.leverage_targets(Q, da, db)
+            rows_x.append(np.concatenate([F1, F2]))
+            rows_t.append(np.concatenate([t1, t2]))
+        return Q
+
+    O.rsvd_range_sym = spy
+    try:
+        st = O.run("ising", 4, beta, h, D, p, nsteps)
+    finally:
+        O.rsvd_range_sym = orig
+    for dg in st.diag:   # rounding-level agreement needs non-degenerate cuts
+        assert min([dg["gap_swap"]] + list(dg["gap_sq"].values())) > 1e-8
+    return np.concatenate(rows_x), np.concatenate(rows_t)
+
+
+def test_collected_rows_match_oracle(trg):
+    """D = 6, beta = 0.16, h = 0.05: every cut of the run (swap, squeezers, triad ranges)
+    has a relative gap above 0.016, so both sides keep the same subspaces."""
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
+    trg.trg_set_sketch_mode(0)
+    trg.trg_sketch_collect(100000)
+    trg.trg_init_ising(4, 0.16, 0.05)
+    for n in range(6):
+        trg.trg_step(n % 4, 6, 12)
+    X, t, dropped = trg.trg_sketch_fetch()
+    trg.trg_sketch_collect(0)
+    Xr, tr = _oracle_rows(0.16, 0.05, 6, 12, 6)
+    assert dropped == 0 and X.shape == Xr.shape
+    assert np.abs(X - Xr).max() < 1e-6
+    assert np.abs(t - tr).max() < 1e-5
+
+
+def test_learned_step_parity(trg):
+    p = random_net(11, bias=0.2)
+    trg.trg_sketch_set_net(to_flat(p))
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
+    trg.trg_set_sketch_mode(1)
+    trg.trg_sketch_stats(reset=True)
+    trg.trg_init_ising(4, 0.16, 0.05)
+    st = O.init_ising(4, 0.16, 0.05)
+    try:
+        for n in range(6):
+            trg.trg_step(n % 4, 6, 12)
+            O.step(st, n % 4, 6, 12, 4, 4, 0x5EED, mlp=p)
+            dg = st.diag[-1]
+            assert min([dg["gap_swap"]] + list(dg["gap_sq"].values())) > 1e-8
+    finally:
+        trg.trg_set_sketch_mode(0)
+    _, lz = trg.trg_free_energy()
+    _, lz_ref = O.free_energy(st)
+    assert abs(lz - lz_ref) < 1e-10 * abs(lz_ref)
+    used = [v["used"] for d in st.diag for v in d.get("sketch", {}).values()]
+    stats = trg.trg_sketch_stats()
+    assert stats["learned"] == used.count("learned")
+    assert stats["fallback"] == used.count("plain")
+
+
+def test_trained_network_reduces_residual(trg):
+    """Train on rows the plain GPU method collects (D = 10, two couplings), then judge on
+    an oracle run at a third coupling with one-pass range finders (q_rho = 0): the
+    learned sketch's probe residual is smaller than the Gaussian's in the median."""
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
+    trg.trg_set_sketch_mode(0)
+    trg.trg_sketch_collect(200000)
+    for beta in (0.145, 0.152):
+        trg.trg_init_ising(4, beta, 0.0)
+        for n in range(7):
+            trg.trg_step(n % 4, 10, 20)
+    X, t, _ = trg.trg_sketch_fetch()
+    trg.trg_sketch_collect(0)
+    trg.trg_sketch_set_net(to_flat(SM.init_params(12)))
+    loss = trg.trg_sketch_train(X, t, epochs=200, batch=128, lr=1e-3, seed=2)
+    assert loss < 0.5 * float(np.var(t)), (loss, np.var(t))
+    p = to_dict(trg.trg_sketch_get_net())
+    st = O.run("ising", 4, 0.1555, 0.0, 10, 20, 6, q_rho=0, mlp=p)
+    ratios = [v["r_learned"] / v["r_plain"] for d in st.diag
+              for v in d.get("sketch", {}).values() if "r_plain" in v and v["r_plain"] > 0]
+    assert ratios and float(np.median(ratios)) < 0.95, ratios

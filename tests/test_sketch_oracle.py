@@ -81,7 +81,9 @@ def test_ideal_weights_reduce_one_pass_residual():
     orig = O.rsvd_range_sym
 
     def spy(rho, chi, q, key):
-        caught.append((rho.copy(), chi, key))
+        f = __import__("sys")._getframe(1).f_locals
+        if "chi_pair" in f:          # triad isometries only (not the squeezers)
+            caught.append((rho.copy(), chi, key, f["d2"], f["d3"]))
         return orig(rho, chi, q, key)
 
     O.rsvd_range_sym = spy
@@ -90,13 +92,12 @@ def test_ideal_weights_reduce_one_pass_residual():
     finally:
         O.rsvd_range_sym = orig
     ratios = []
-    for rho, chi, key in caught[-4:]:
+    for rho, chi, key, da, db in caught[-4:]:
         n = rho.shape[0]
-        d = int(round(np.sqrt(n)))
-        if d * d != n or chi >= n:
+        if chi >= n:
             continue
         Q = orig(rho, chi, 6, key)
-        t1, t2 = SM.leverage_targets(Q, d, d)
+        t1, t2 = SM.leverage_targets(Q, da, db)
         w = (np.exp2(t1)[:, None] * np.exp2(t2)[None, :]).reshape(-1)
         G = O.gaussian(key, n, chi)
         kp = O.sketch_key(0x5EED, st.nsteps - 1, 13)
