@@ -44,6 +44,9 @@ def args_():
     ap.add_argument("--fp64-form-steps", type=int, default=0,
                     help="also time this many steady-state steps of the FP64 form (slow)")
     ap.add_argument("--beta", type=float, default=0.1497)
+    ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "learned"],
+                    help="learned: train the sketch network on rows collected from plain "
+                         "runs (D = 16..32), then time the learned-sketch form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-check", action="store_true")
     return ap.parse_args()
@@ -170,12 +173,75 @@ def run_f(trg, prec, D, nsteps):
     return trg.trg_free_energy()[0]
 
 
-def precision_check(trg, prec):
+def net_dict(flat):
+    """Flat network parameters (library order) -> the oracle's dictionary."""
+    import numpy as np
+    shapes = (("W1", (256, 5)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)),
+              ("W3", (1, 256)), ("b3", (1,)))
+    out, o = {}, 0
+    for k, sh in shapes:
+        n = int(np.prod(sh))
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(sh)
+        o += n
+    return out
+
+
+def train_sketch(trg, prec, budget_s=120.0, pairs_goal=2000):
+    """Collect (inputs, leverage target) rows from plain runs (the bench's precision form)
+    at D = 16, 24, 32 and several couplings, then train the sketch network on the GPU."""
+    import numpy as np
+    t0 = time.time()
+    trg.trg_set_sketch_mode(0)
+    trg.trg_sketch_collect(4_000_000)
+    pairs, runs = 0, 0
+    for D in (16, 24, 32, 16, 24, 32, 16, 24):
+        for beta in (0.145, 0.15, 0.155):
+            trg.trg_set_params(4, 4, 0x5EED + runs, prec)
+            trg.trg_init_ising(4, beta, 0.0)
+            for n in range(10):
+                trg.trg_step(n % 4, D, 2 * D)
+            runs += 1
+            rows = trg.trg_sketch_fetch()[0].shape[0]
+            pairs = rows // (2 * D)      # rows per range finder = d_a + d_b ~ 2D
+            if pairs >= pairs_goal or time.time() - t0 > budget_s:
+                break
+        if pairs >= pairs_goal or time.time() - t0 > budget_s:
+            break
+    X, t, _ = trg.trg_sketch_fetch()
+    trg.trg_sketch_collect(0)
+    t1 = time.time()
+    rng = np.random.default_rng(0)
+    init = np.concatenate([rng.standard_normal(256 * 5) * np.sqrt(2 / 5), np.zeros(256),
+                           rng.standard_normal(256 * 256) * np.sqrt(2 / 256), np.zeros(256),
+                           rng.standard_normal(256) * np.sqrt(1 / 256), np.zeros(1)])
+    trg.trg_sketch_set_net(init.astype(np.float32))
+    loss = trg.trg_sketch_train(X, t, epochs=40, batch=512, lr=1e-3, seed=1)
+    t2 = time.time()
+    return {"runs": runs, "rows": int(X.shape[0]), "pairs_approx": int(pairs),
+            "collect_s": t1 - t0, "train_s": t2 - t1, "train_loss": loss,
+            "target_var": float(np.var(t)), "epochs": 40, "batch": 512}
+
+
+def learned_gain(trg):
+    """Oracle-judged effect of the trained network: median over the range finders of a
+    D = 10 oracle run (beta 0.1555, not in the training set) of the probe-residual ratio
+    learned / Gaussian with one-pass range finders (q_rho = 0)."""
+    import numpy as np
+    from oracle import trg_oracle as O
+    p = net_dict(trg.trg_sketch_get_net())
+    st = O.run("ising", 4, 0.1555, 0.0, 10, 20, 6, q_rho=0, mlp=p)
+    r = [v["r_learned"] / v["r_plain"] for d in st.diag for v in d.get("sketch", {}).values()
+         if v.get("r_plain", 0) > 0]
+    return float(np.median(r)) if r else None
+
+
+def precision_check(trg, prec, mlp=None):
     """ΔF/F of the mixed form: against the FP64 CPU oracle at D=14 (16 steps; no
     near-degenerate truncation there) and against this library's FP64 form at D=24
-    (12 steps; the FP64 form matches the oracle to 1e-10)."""
+    (12 steps; the FP64 form matches the oracle to 1e-10).  With a sketch network the
+    oracle runs the same learned sketch."""
     from oracle import trg_oracle as O
-    st = O.run("ising", 4, 0.1497, 0.0, D=14, p=28, nsteps=16, q_swap=4, q_rho=4)
+    st = O.run("ising", 4, 0.1497, 0.0, D=14, p=28, nsteps=16, q_swap=4, q_rho=4, mlp=mlp)
     f_or = O.free_energy(st)[0]
     f14 = run_f(trg, prec, 14, 16)
     f24_64 = run_f(trg, 0, 24, 12)
@@ -225,6 +291,12 @@ def run_ours(a):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+
+    learned = None
+    if a.sketch == "learned":
+        learned = train_sketch(trg, prec)
+        trg.trg_set_sketch_mode(1)
+        trg.trg_sketch_stats(reset=True)
 
     # ---- whole job, end to end from the host: init (H2D of T0), growth, warm-up, timed
     barrier()
@@ -301,8 +373,14 @@ def run_ours(a):
         "phases_ms": phases,
         "free_energy": f_last[0],
     }
+    if learned is not None:
+        learned.update(trg.trg_sketch_stats())
+        learned["oracle_residual_ratio_q0_D10"] = learned_gain(trg)
+        line["config"]["sketch"] = "learned (row-weighted Gaussian, plain fallback)"
+        line["learned_sketch"] = learned
     if not a.no_precision_check and prec != 0:
-        line["delta_f_rel"] = precision_check(trg, prec)
+        mlp = net_dict(trg.trg_sketch_get_net()) if learned is not None else None
+        line["delta_f_rel"] = precision_check(trg, prec, mlp)
     if a.fp64_form_steps > 0:
         r = fp64_form_rate(trg, D, a.fp64_form_steps, a.beta)
         line["fp64_form"] = {"value": r, "unit": "RG steps/s", "steps": a.fp64_form_steps,
