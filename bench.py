@@ -47,6 +47,11 @@ def args_():
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "learned"],
                     help="learned: train the sketch network on rows collected from plain "
                          "runs (D = 16..32), then time the learned-sketch form")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="N > 0: time a coupling sweep of N instances (Ising and Z3 clock "
+                         "1:1, beta ~ U[0.14, 0.16], h ~ U[0, 0.01], D ~ U{16,24,32,40}) "
+                         "on concurrent lanes instead of the single D=48 step")
+    ap.add_argument("--lanes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-check", action="store_true")
     return ap.parse_args()
@@ -271,6 +276,54 @@ def fp64_form_rate(trg, D, nsteps, beta):
     return nsteps / (time.time() - t)
 
 
+def run_batch(a):
+    """Coupling sweep (batching variant): instance-steps/s of N instances on lanes."""
+    import numpy as np
+    import torch
+    import paper_2507_21909_b300 as trg
+    rng = np.random.default_rng(1)
+    n = a.batch
+    model = [0 if i % 2 == 0 else 3 for i in range(n)]
+    beta = rng.uniform(0.14, 0.16, n)
+    h = rng.uniform(0.0, 0.01, n)
+    D = rng.choice([16, 24, 32, 40], n)
+    prec = PREC[a.precision]
+    t0 = time.time()
+    trg.trg_batch_create(model, beta, h, D, lanes=a.lanes, q_swap=4, q_rho=4, precision=prec)
+    grow_ms = trg.trg_batch_step(5)            # every leg reaches its D within 5 steps
+    warm_ms = trg.trg_batch_step(max(a.warmup - 2, 1))
+    clk = Clocks(0)
+    clk.start()
+    torch.cuda.synchronize()
+    ms = trg.trg_batch_step(a.steps)
+    clocks = clk.stop()
+    t_job = time.time() - t0
+    res = trg.trg_batch_results(n)
+    lane_of, scratch = trg.trg_batch_lanes(n, min(a.lanes, n))
+    trg.trg_batch_free()
+    value = n * a.steps / (ms / 1e3)
+    line = {
+        "metric": "batched triad-ATRG instance-steps/s (coupling sweep)", "value": value,
+        "unit": "instance-steps/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if prec else "f64", "data": "synthetic",
+        "config": {"workload": f"coupling sweep of {n} instances, Ising:Z3 = 1:1, beta ~ "
+                               "U[0.14,0.16], h ~ U[0,0.01], D ~ U{16,24,32,40}, p = 2D, "
+                               "seed 1", "instances": n, "lanes": int(min(a.lanes, n)),
+                   "precision": a.precision,
+                   "l2_flush": "none: per-instance state far larger than L2"},
+        "e2e": {"value": n * (5 + max(a.warmup - 2, 1) + a.steps) / t_job,
+                "unit": "instance-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "region": "whole job from the host: create (H2D of every T0), 5 growth, "
+                          "warm-up and timed steps"},
+        "clocks": clocks,
+        "per_D_instances": {int(d): int((D == d).sum()) for d in (16, 24, 32, 40)},
+        "lane_scratch_gb": [round(x / 2 ** 30, 2) for x in scratch],
+        "growth_ms": grow_ms, "finite": bool(np.all(np.isfinite(res["lnz"]))),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(a):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -400,5 +453,7 @@ if __name__ == "__main__":
     a = args_()
     if a.impl == "reference":
         run_reference(a)
+    elif a.batch > 0:
+        run_batch(a)
     else:
         run_ours(a)

@@ -157,6 +157,43 @@ trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long M, long lon
                             long long ldc, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Batched coupling sweep: many independent instances of the step (each its own model,
+ * beta, h, D, p and sketch seed), e.g. the sweep over couplings and bond dimensions that
+ * locates a transition.  The paper runs one lattice at a time; the instances share
+ * nothing but the GPU.  `lanes` engine contexts (each its own CUDA stream and scratch
+ * arena, driven by its own host thread) run concurrently; every instance is bound to one
+ * lane (longest-processing-time assignment with cost D^7 + 24^7), which steps its
+ * instances in index order.  Results do not depend on the lane count or schedule: each
+ * instance goes through exactly the kernels of trg_step.  The batch is independent of
+ * the single-instance context of trg_init_* / trg_step.
+ * ------------------------------------------------------------------------------- */
+
+/* Create n instances: model[i] = 0 (Ising) or q in 2..8 (Z_q clock), beta[i] >= 0, h[i],
+ * D[i] >= 1, p[i] >= 0 (NULL: 2 D[i]), seed[i] (NULL: 0x5EED); all in d = 4, with the
+ * common q_swap, q_rho and precision (TRG_PREC_*).  Replaces any earlier batch.  Host
+ * arrays of length n, read during the call.  Errors: TRG_ERR_ARG, TRG_ERR_OOM,
+ * TRG_ERR_CUDA. */
+trg_status trg_batch_create(int n, const int *model, const double *beta, const double *h,
+                            const int *D, const int *p, const unsigned long long *seed,
+                            int lanes, int q_swap, int q_rho, int precision);
+
+/* Every instance takes nsteps steps, each along the axis after its previous one
+ * (instance step k is along axis k mod 4).  *wall_ms (may be NULL) = host wall time of
+ * the call, all lanes synchronised.  Errors name the first failing lane. */
+trg_status trg_batch_step(int nsteps, double *wall_ms);
+
+/* Per instance (host arrays of length n, any may be NULL): f per site, ln Z/V, the
+ * one-site impurity observable (Ising: <s>, clock: <cos theta>), steps taken. */
+trg_status trg_batch_results(double *f, double *lnz, double *m, int *nsteps);
+
+/* lane_of[i] (length n) and the scratch bytes each lane has reserved (length lanes);
+ * either may be NULL. */
+trg_status trg_batch_lanes(int *lane_of, long long *scratch_bytes);
+
+/* Release every instance and lane. */
+trg_status trg_batch_free(void);
+
+/* ---------------------------------------------------------------------------------
  * Learned sketch of the triad-isometry range finders (Sec. II B, eq. HOSVD: U^A, U^X,
  * U^Y, U^D are ranges of the Grams rho over a leg pair (a, b), n = d_a d_b).  The paper
  * draws a Gaussian sketch G (n x chi); the learned form keeps the same G and rescales

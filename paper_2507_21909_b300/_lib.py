@@ -15,7 +15,8 @@ EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_step_timings", "trg_gemm", "trg_kernel_stats", "trg_mem_stats",
             "trg_gemm_noalloc", "trg_sketch_set_net", "trg_sketch_get_net",
             "trg_sketch_forward", "trg_sketch_grad", "trg_sketch_train", "trg_set_sketch_mode",
-            "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats"]
+            "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats", "trg_batch_create",
+            "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free"]
 
 TRG_SKETCH_IN, TRG_SKETCH_PARAMS = 5, 67585
 
@@ -58,6 +59,9 @@ def _load():
         "trg_sketch_train": [pf, pf, ll, i, i, ctypes.c_float, ull, pd],
         "trg_set_sketch_mode": [i], "trg_sketch_collect": [ll],
         "trg_sketch_fetch": [pf, pf, ll, pll, pll], "trg_sketch_stats": [pll, pll, i],
+        "trg_batch_create": [i, pi, pd, pd, pi, pi, ctypes.POINTER(ull), i, i, i, i],
+        "trg_batch_step": [i, pd], "trg_batch_results": [pd, pd, pd, pi],
+        "trg_batch_lanes": [pi, pll], "trg_batch_free": [],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -265,3 +269,52 @@ def trg_sketch_stats(reset=False):
     a, b = ctypes.c_longlong(), ctypes.c_longlong()
     _check(lib.trg_sketch_stats(ctypes.byref(a), ctypes.byref(b), int(reset)))
     return {"learned": a.value, "fallback": b.value}
+
+
+# ------------------------------------------------------------------ batched instances
+def trg_batch_create(model, beta, h, D, p=None, seed=None, lanes=4, q_swap=4, q_rho=4,
+                     precision=TRG_PREC_FP64):
+    """model[i]: 0 Ising or q (Z_q clock); arrays of equal length n."""
+    n = len(model)
+    md = np.ascontiguousarray(model, dtype=np.int32)
+    bt = np.ascontiguousarray(beta, dtype=np.float64)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    dd = np.ascontiguousarray(D, dtype=np.int32)
+    if not (len(bt) == len(hh) == len(dd) == n):
+        raise ValueError("arrays must have equal length")
+    pi_, pd_ = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    pp = None if p is None else np.ascontiguousarray(p, dtype=np.int32)
+    sd = None if seed is None else np.ascontiguousarray(seed, dtype=np.uint64)
+    _check(lib.trg_batch_create(
+        n, md.ctypes.data_as(pi_), bt.ctypes.data_as(pd_), hh.ctypes.data_as(pd_),
+        dd.ctypes.data_as(pi_), None if pp is None else pp.ctypes.data_as(pi_),
+        None if sd is None else sd.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)),
+        int(lanes), int(q_swap), int(q_rho), int(precision)))
+    return n
+
+
+def trg_batch_step(nsteps=1):
+    ms = ctypes.c_double()
+    _check(lib.trg_batch_step(int(nsteps), ctypes.byref(ms)))
+    return ms.value
+
+
+def trg_batch_results(n):
+    f, lz, m = (np.empty(n) for _ in range(3))
+    ns = np.empty(n, dtype=np.int32)
+    pd_ = ctypes.POINTER(ctypes.c_double)
+    _check(lib.trg_batch_results(f.ctypes.data_as(pd_), lz.ctypes.data_as(pd_),
+                                 m.ctypes.data_as(pd_), ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return {"f": f, "lnz": lz, "m": m, "nsteps": ns}
+
+
+def trg_batch_lanes(n, lanes):
+    lane_of = np.empty(n, dtype=np.int32)
+    scratch = np.empty(lanes, dtype=np.int64)
+    _check(lib.trg_batch_lanes(lane_of.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               scratch.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
+    return lane_of, scratch
+
+
+def trg_batch_free():
+    _check(lib.trg_batch_free())

@@ -2,6 +2,8 @@
 // C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b], row-major; 64x64 tiles, BK = 16,
 // 256 threads with 4x4 register tiles.  Ragged edges are zero-filled on load.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "trg_internal.h"
 
@@ -251,42 +253,51 @@ gemm_f64_tall_kernel(int64_t M, int N, int K, double alpha, const double *__rest
   }
 }
 
-static double *g_ws = nullptr;
-static size_t g_ws_cap = 0;
+// split-K workspace, one per stream (batched instances run on several streams at once)
+struct Workspace {
+  double *p = nullptr;
+  size_t cap = 0;
+};
+static std::mutex g_ws_mu;
+static std::map<cudaStream_t, Workspace> g_ws;
 
-static void ensure_ws(size_t need, cudaStream_t s) {
-  if (need <= g_ws_cap) return;
-  if (g_ws) {
+static double *ensure_ws(size_t need, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace &w = g_ws[s];
+  if (need <= w.cap) return w.p;
+  if (w.p) {
     TRG_CUDA(cudaStreamSynchronize(s));
-    TRG_CUDA(cudaFree(g_ws));
+    TRG_CUDA(cudaFree(w.p));
   }
-  g_ws = nullptr;
-  g_ws_cap = std::max(need, size_t(32) << 20);
-  if (cudaMalloc(&g_ws, g_ws_cap) != cudaSuccess) {
+  w.p = nullptr;
+  w.cap = std::max(need, size_t(32) << 20);
+  if (cudaMalloc(&w.p, w.cap) != cudaSuccess) {
     cudaGetLastError();
-    g_ws_cap = 0;
+    w.cap = 0;
     throw Error(TRG_ERR_OOM, "split-K workspace allocation failed");
   }
+  return w.p;
 }
 
 template <int R>
 static void launch_thin(bool ta, bool tb, int M, int N, int64_t K, const double *A,
                         int64_t lda, const double *B, int64_t ldb, int64_t kchunk, int nsplit,
-                        int sym, cudaStream_t s) {
+                        int sym, double *ws, cudaStream_t s) {
   gemm_f64_thin_kernel<R><<<nsplit, 256, 0, s>>>(ta, tb, M, N, K, A, lda, B, ldb, kchunk, sym,
-                                                 g_ws);
+                                                 ws);
 }
 template <int R>
 static void launch_tall(int64_t M, int N, int K, double alpha, const double *A, int64_t lda,
                         const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
                         int b_upper, cudaStream_t s) {
   constexpr int kSmem = 2 * 64 * 65 * (int)sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  // thread-safe one-time setup (function-local static initialisation)
+  static const bool attr_done = [&] {
     TRG_CUDA(cudaFuncSetAttribute(gemm_f64_tall_kernel<R>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr_done;
   const int64_t tiles = (M + 63) / 64;
   const int grid = (int)std::min<int64_t>(tiles, 148 * 3);
   gemm_f64_tall_kernel<R><<<grid, 256, kSmem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
@@ -303,17 +314,17 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
     const int nsplit = (int)std::min<int64_t>((K + 1023) / 1024, 148 * 4);
     int64_t kchunk = (K + nsplit - 1) / nsplit;
     kchunk = (kchunk + TBK - 1) / TBK * TBK;
-    ensure_ws((size_t)nsplit * M * N * sizeof(double), s);
+    double *ws = ensure_ws((size_t)nsplit * M * N * sizeof(double), s);
     const int R = (int)((std::max(M, N) + 15) / 16);
     switch (R) {
-      case 1: launch_thin<1>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, s); break;
-      case 2: launch_thin<2>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, s); break;
-      case 3: launch_thin<3>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, s); break;
-      default: launch_thin<4>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, s); break;
+      case 1: launch_thin<1>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, ws, s); break;
+      case 2: launch_thin<2>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, ws, s); break;
+      case 3: launch_thin<3>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, ws, s); break;
+      default: launch_thin<4>(ta, tb, (int)M, (int)N, K, A, lda, B, ldb, kchunk, nsplit, sym, ws, s); break;
     }
     TRG_LAUNCH_CHECK();
     const int blocks = (int)std::min<int64_t>((M * N + 255) / 256, 148);
-    thin_reduce<<<blocks, 256, 0, s>>>(g_ws, nsplit, (int)M, (int)N, alpha, beta, C, ldc, sym);
+    thin_reduce<<<blocks, 256, 0, s>>>(ws, nsplit, (int)M, (int)N, alpha, beta, C, ldc, sym);
     TRG_LAUNCH_CHECK();
     return;
   }
@@ -341,16 +352,16 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
   }
   int64_t kchunk = (K + nsplit - 1) / nsplit;
   kchunk = ((kchunk + BK - 1) / BK) * BK;
-  if (nsplit > 1) ensure_ws((size_t)nsplit * batch * M * N * sizeof(double), s);
+  double *ws = nsplit > 1 ? ensure_ws((size_t)nsplit * batch * M * N * sizeof(double), s) : nullptr;
   int64_t gz = std::min<int64_t>(batch * nsplit, 65535);
   dim3 grid((unsigned)gy, (unsigned)gx, (unsigned)gz);  // M tiles on x (up to 2^31 - 1)
   gemm_f64_kernel<<<grid, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta,
-                                       C, ldc, sC, batch, kchunk, nsplit, g_ws);
+                                       C, ldc, sC, batch, kchunk, nsplit, ws);
   TRG_LAUNCH_CHECK();
   if (nsplit > 1) {
     int64_t total = batch * M * N;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
-    splitk_reduce<<<blocks, 256, 0, s>>>(g_ws, nsplit, batch, M, N, alpha, beta, C, ldc, sC);
+    splitk_reduce<<<blocks, 256, 0, s>>>(ws, nsplit, batch, M, N, alpha, beta, C, ldc, sC);
     TRG_LAUNCH_CHECK();
   }
 }

@@ -571,30 +571,27 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     p.sC = sC;
   }
   CUtensorMap ma = tmap(As, Kp, M, batch, ns), mb = tmap(Bs, Kp, N, batch, ns);
-  static bool attr = false;
-  if (!attr) {
-    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmemMax));
-    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmemMax));
-    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmemMax));
-    TRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmemMax));
-    attr = true;
-    if (getenv("TRG_DEBUG_ATTR")) {
-      const void *fns[4] = {(const void *)oz_gemm_kernel<5>, (const void *)oz_rowexp_kernel,
-                            (const void *)oz_split_kernel, (const void *)oz_ws_reduce};
-      for (int i = 0; i < 4; ++i) {
-        cudaFuncAttributes fa;
-        cudaFuncGetAttributes(&fa, fns[i]);
-        fprintf(stderr, "oz kernel %d: regs %d maxThreads %d static smem %zu max dyn smem %d local %zu\n",
-                i, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
-                fa.maxDynamicSharedSizeBytes, fa.localSizeBytes);
-      }
-      fprintf(stderr, "launch: grid %lld %lld %lld threads %d smem %zu params %zu\n", (long long)gx,
-              (long long)gy, (long long)(batch * ksplit), THREADS, smem, sizeof(Params));
+  // thread-safe one-time setup (function-local static initialisation)
+  static const bool attr_done = [] {
+    for (const void *k : {(const void *)oz_gemm_kernel<3>, (const void *)oz_gemm_kernel<4>,
+                          (const void *)oz_gemm_kernel<5>, (const void *)oz_gemm_kernel<6>})
+      TRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemMax));
+    return true;
+  }();
+  (void)attr_done;
+  if (getenv("TRG_DEBUG_ATTR")) {
+    const void *fns[4] = {(const void *)oz_gemm_kernel<5>, (const void *)oz_rowexp_kernel,
+                          (const void *)oz_split_kernel, (const void *)oz_ws_reduce};
+    for (int i = 0; i < 4; ++i) {
+      cudaFuncAttributes fa;
+      cudaFuncGetAttributes(&fa, fns[i]);
+      fprintf(stderr, "oz kernel %d: regs %d maxThreads %d static smem %zu max dyn smem %d local %zu\n",
+              i, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
+              fa.maxDynamicSharedSizeBytes, fa.localSizeBytes);
     }
+    fprintf(stderr, "launch: grid %lld %lld %lld threads %d smem %zu params %zu\n", (long long)gx,
+            (long long)gy, (long long)(batch * ksplit), THREADS, smem, sizeof(Params));
   }
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
   if (timing) timing->before(s);

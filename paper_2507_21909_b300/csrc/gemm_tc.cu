@@ -344,19 +344,20 @@ static size_t smem_bytes() {
 template <int BN>
 static void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, dim3 grid,
                    cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  // thread-safe one-time setup (function-local static initialisation)
+  static const bool attr_done = [&] {
     TRG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<BN>()));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr_done;
   tc_gemm_kernel<BN><<<grid, THREADS, smem_bytes<BN>(), s>>>(ma, mb, p);
   TRG_LAUNCH_CHECK();
 }
 
 }  // namespace tc
 
-static int64_t g_tc_launches = 0;
+static std::atomic<int64_t> g_tc_launches{0};
 int64_t tc_launch_count() { return g_tc_launches; }
 
 int tc_error_flag(bool reset) {

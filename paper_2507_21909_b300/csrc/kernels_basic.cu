@@ -3,7 +3,7 @@
 
 namespace trg {
 
-int64_t g_kernel_launches = 0;
+std::atomic<int64_t> g_kernel_launches{0};
 
 // ------------------------------------------------------------------ permutation
 constexpr int kMaxDims = 10;

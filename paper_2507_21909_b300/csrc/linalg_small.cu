@@ -343,12 +343,13 @@ void svd_jacobi(const double *A, int m, int n, double *U, double *S, double *V, 
   if (n == 0 || batch == 0) return;
   if (m < n) throw Error(TRG_ERR_ARG, "svd_jacobi needs m >= n");
   if (n > 1024) throw Error(TRG_ERR_ARG, "svd_jacobi: n > 1024");
-  static bool attr_set = false;
-  if (!attr_set) {
+  // thread-safe one-time setup (function-local static initialisation)
+  static const bool attr_set_done = [&] {
     TRG_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSvdSmemMax));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set_done;
   if (batch == 1 && n >= 24) {
     // cooperative form: work = [at | vt | norms | sync words]
     double *nrm_end = work + (size_t)n * m + (size_t)n * n + n;

@@ -331,12 +331,13 @@ void mlp_forward(const SketchNet &net, const float *X, int64_t rows, float *u, b
     TRG_CUDA(cudaMemcpyAsync(u, U, rows * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return;
   }
-  static bool attr = false;
-  if (!attr) {
+  // thread-safe one-time setup (function-local static initialisation)
+  static const bool attr_done = [&] {
     TRG_CUDA(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kInferSmem));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr_done;
   const int grid = (int)std::min<int64_t>((rows + kInferRows - 1) / kInferRows, 148);
   mlp_infer_kernel<<<grid, kMlpHid, kInferSmem, s>>>(net.wb, net.w, X, rows, u);
   TRG_LAUNCH_CHECK();

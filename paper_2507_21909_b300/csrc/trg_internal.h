@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -24,7 +25,8 @@ struct Error : std::runtime_error {
       throw ::trg::Error(TRG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 // every kernel launch of the library is followed by this check, which also counts it
-extern int64_t g_kernel_launches;
+// (atomic: batched instances launch from several host threads)
+extern std::atomic<int64_t> g_kernel_launches;
 #define TRG_LAUNCH_CHECK()        \
   do {                            \
     ++::trg::g_kernel_launches;   \

@@ -6,6 +6,8 @@
 // linalg_small.cu.  Shapes are structural (fixed by D, p and the step history), so the
 // host never waits on device data inside a step except for the final status read.
 #include <algorithm>
+#include <thread>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -120,7 +122,7 @@ static Ctx &ctx() {
   static Ctx c;
   return c;
 }
-static std::string g_err = "ok";
+static thread_local std::string g_err = "ok";  // per host thread (batched lanes)
 void set_last_error(const std::string &msg) { g_err = msg; }
 
 static Tensor view(double *p, std::vector<int64_t> d) {
@@ -953,6 +955,210 @@ static void init_cp(Ctx &c, double beta, const std::vector<double> &W, int nstat
   c.init = true;
 }
 
+static void init_ising_ctx(Ctx &c, double beta, double h) {
+  double cb = std::sqrt(std::cosh(beta)), sb = std::sqrt(std::sinh(beta));
+  init_cp(c, beta, {cb, sb, cb, -sb}, 2, 2, {std::exp(h), std::exp(-h)}, {1.0, -1.0});
+}
+
+static void init_clock_ctx(Ctx &c, int q, double beta, double h) {
+  // real Fourier basis diagonalises the circulant bond matrix exp(beta cos(th - th'))
+  std::vector<std::vector<double>> F;
+  std::vector<double> th(q);
+  for (int k = 0; k < q; ++k) th[k] = 2.0 * M_PI * k / q;
+  F.push_back(std::vector<double>(q, 1.0 / std::sqrt((double)q)));
+  for (int m = 1; m <= (q - 1) / 2; ++m) {
+    std::vector<double> cc(q), ss(q);
+    for (int k = 0; k < q; ++k) {
+      cc[k] = std::cos(m * th[k]) * std::sqrt(2.0 / q);
+      ss[k] = std::sin(m * th[k]) * std::sqrt(2.0 / q);
+    }
+    F.push_back(cc);
+    F.push_back(ss);
+  }
+  if (q % 2 == 0) {
+    std::vector<double> alt(q);
+    for (int k = 0; k < q; ++k) alt[k] = std::cos(M_PI * k) / std::sqrt((double)q);
+    F.push_back(alt);
+  }
+  std::vector<double> W(q * q), wt(q), obs(q);
+  for (int m = 0; m < q; ++m) {
+    double lam = 0.0;
+    for (int a = 0; a < q; ++a)
+      for (int b = 0; b < q; ++b)
+        lam += F[m][a] * std::exp(beta * std::cos(th[a] - th[b])) * F[m][b];
+    if (lam < 0.0) lam = 0.0;
+    for (int a = 0; a < q; ++a) W[a * q + m] = F[m][a] * std::sqrt(lam);
+  }
+  for (int a = 0; a < q; ++a) {
+    obs[a] = std::cos(th[a]);
+    wt[a] = std::exp(h * obs[a]);
+  }
+  init_cp(c, beta, W, q, q, wt, obs);
+}
+
+// ln Z/V and f of the current state (synchronises the stream)
+static void free_energy_ctx(Ctx &c, double *f_per_site, double *lnZ_per_site) {
+  if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
+  int64_t n = prod(c.dims);
+  dot(c.phi, c.psi, n, c.dscal + 3, c.scratch(), c.stream);
+  double h[4];
+  TRG_CUDA(cudaMemcpyAsync(h, c.dscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TRG_CUDA(cudaStreamSynchronize(c.stream));
+  double lz = h[0] + std::log(std::fabs(h[3])) * std::ldexp(1.0, -c.nsteps);
+  if (lnZ_per_site) *lnZ_per_site = lz;
+  if (f_per_site) *f_per_site = c.beta > 0.0 ? -lz / c.beta : NAN;
+}
+
+static double magnetisation_ctx(Ctx &c) {
+  if (!c.init || !c.have_imp) throw Error(TRG_ERR_NOINIT, "no impurity state");
+  int64_t n = prod(c.dims);
+  dot(c.phi, c.psi, n, c.dscal + 3, c.scratch(), c.stream);
+  dot(c.phi, c.psi_imp, n, c.dscal + 4, c.scratch(), c.stream);
+  double h[2];
+  TRG_CUDA(cudaMemcpyAsync(h, c.dscal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TRG_CUDA(cudaStreamSynchronize(c.stream));
+  return h[1] / h[0];
+}
+
+// one step with the error context of the phase that failed
+static void step_ctx(Ctx &c, int axis, int D, int p) {
+  try {
+    step_impl(c, axis, D, p);
+  } catch (const Error &e) {
+    cudaStreamSynchronize(c.stream);
+    c.arena.reset();
+    throw Error(e.code, std::string(e.what()) + " [step phase " + std::to_string(c.phase) + "]");
+  }
+}
+
+// ------------------------------------------------------------ batched instances (S14)
+// A coupling sweep: many independent instances (model, beta, h, D, seed), each with its
+// own persistent state.  `lanes` engine contexts, each with its own CUDA stream and
+// scratch arena, run concurrently (one host thread per lane); every instance is bound to
+// one lane, which swaps its state in, runs its steps and swaps it out.  Instances do not
+// interact, so the results do not depend on the lane count or schedule.
+struct InstState {
+  int model = 0;  // 0: Ising, q >= 2: Z_q clock
+  double beta = 0.0, h = 0.0;
+  int D = 0, p = 0;
+  uint64_t seed = 0;
+  bool init = false, have_imp = false;
+  double *phi = nullptr, *psi = nullptr, *psi_imp = nullptr;
+  std::vector<int64_t> dims;
+  int axes[4] = {0, 1, 2, 3};
+  int nsteps = 0;
+  double *dscal = nullptr;
+  int *dflag = nullptr;
+  double last_logc = 0.0, last_gap = INFINITY;
+};
+
+struct Lane {
+  std::unique_ptr<Ctx> c;
+  double *own_dscal = nullptr;
+  int *own_dflag = nullptr;
+  std::vector<int> members;
+  double cost = 0.0;
+};
+
+static void swap_in(Lane &L, InstState &s) {
+  Ctx &c = *L.c;
+  c.init = s.init;
+  c.have_imp = s.have_imp;
+  c.beta = s.beta;
+  c.phi = s.phi;
+  c.psi = s.psi;
+  c.psi_imp = s.psi_imp;
+  c.dims = s.dims;
+  std::memcpy(c.axes, s.axes, sizeof(c.axes));
+  c.nsteps = s.nsteps;
+  c.dscal = s.dscal;
+  c.dflag = s.dflag;
+  c.seed = s.seed;
+  c.last_logc = s.last_logc;
+  c.last_gap = s.last_gap;
+}
+
+static void swap_out(Lane &L, InstState &s) {
+  Ctx &c = *L.c;
+  s.init = c.init;
+  s.have_imp = c.have_imp;
+  s.beta = c.beta;
+  s.phi = c.phi;
+  s.psi = c.psi;
+  s.psi_imp = c.psi_imp;
+  s.dims = c.dims;
+  std::memcpy(s.axes, c.axes, sizeof(s.axes));
+  s.nsteps = c.nsteps;
+  s.last_logc = c.last_logc;
+  s.last_gap = c.last_gap;
+  c.phi = c.psi = c.psi_imp = nullptr;
+  c.init = false;
+  c.dscal = L.own_dscal;
+  c.dflag = L.own_dflag;
+}
+
+struct Batch {
+  std::vector<InstState> inst;
+  std::vector<Lane> lanes;
+  int device = 0;
+};
+static std::unique_ptr<Batch> g_batch;
+
+// run f(lane, instance) for every instance, lanes in parallel host threads
+template <class F>
+static void for_each_lane(Batch &B, F &&f) {
+  std::vector<std::string> errs(B.lanes.size());
+  std::vector<int> codes(B.lanes.size(), TRG_OK);
+  std::vector<std::thread> th;
+  for (size_t l = 0; l < B.lanes.size(); ++l) {
+    th.emplace_back([&, l] {
+      Lane &L = B.lanes[l];
+      try {
+        TRG_CUDA(cudaSetDevice(B.device));
+        for (int id : L.members) {
+          swap_in(L, B.inst[id]);
+          try {
+            f(L, B.inst[id]);
+          } catch (...) {
+            swap_out(L, B.inst[id]);
+            throw;
+          }
+          swap_out(L, B.inst[id]);
+        }
+      } catch (const Error &e) {
+        errs[l] = e.what();
+        codes[l] = e.code;
+      } catch (const std::exception &e) {
+        errs[l] = e.what();
+        codes[l] = TRG_ERR_CUDA;
+      }
+    });
+  }
+  for (auto &t : th) t.join();
+  for (size_t l = 0; l < errs.size(); ++l)
+    if (codes[l] != TRG_OK) throw Error(codes[l], "lane " + std::to_string(l) + ": " + errs[l]);
+}
+
+static void batch_free_all() {
+  if (!g_batch) return;
+  for (Lane &L : g_batch->lanes)
+    if (L.c && L.c->stream) cudaStreamSynchronize(L.c->stream);
+  for (InstState &s : g_batch->inst) {
+    for (double *b : {s.phi, s.psi, s.psi_imp, s.dscal})
+      if (b) cudaFree(b);
+    if (s.dflag) cudaFree(s.dflag);
+  }
+  for (Lane &L : g_batch->lanes) {
+    if (!L.c) continue;
+    L.c->arena.release();
+    if (L.own_dscal) cudaFree(L.own_dscal);
+    if (L.own_dflag) cudaFree(L.own_dflag);
+    if (L.c->d_sketch_cnt) cudaFree(L.c->d_sketch_cnt);
+    if (L.c->own_stream) cudaStreamDestroy(L.c->own_stream);
+  }
+  g_batch.reset();
+}
+
 }  // namespace trg
 
 // ================================================================== C ABI
@@ -980,8 +1186,7 @@ trg_status trg_init_ising(int d, double beta, double h) {
     if (d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 4");
     if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
       throw Error(TRG_ERR_ARG, "need finite beta >= 0 and finite h");
-    double cb = std::sqrt(std::cosh(beta)), sb = std::sqrt(std::sinh(beta));
-    init_cp(ctx(), beta, {cb, sb, cb, -sb}, 2, 2, {std::exp(h), std::exp(-h)}, {1.0, -1.0});
+    init_ising_ctx(ctx(), beta, h);
   });
 }
 
@@ -990,39 +1195,7 @@ trg_status trg_init_clock(int d, int q, double beta, double h) {
     if (d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 4");
     if (q < 2 || q > 8 || !(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
       throw Error(TRG_ERR_ARG, "need 2 <= q <= 8, finite beta >= 0 and finite h");
-    // real Fourier basis diagonalises the circulant bond matrix exp(beta cos(th - th'))
-    std::vector<std::vector<double>> F;
-    std::vector<double> th(q);
-    for (int k = 0; k < q; ++k) th[k] = 2.0 * M_PI * k / q;
-    F.push_back(std::vector<double>(q, 1.0 / std::sqrt((double)q)));
-    for (int m = 1; m <= (q - 1) / 2; ++m) {
-      std::vector<double> cc(q), ss(q);
-      for (int k = 0; k < q; ++k) {
-        cc[k] = std::cos(m * th[k]) * std::sqrt(2.0 / q);
-        ss[k] = std::sin(m * th[k]) * std::sqrt(2.0 / q);
-      }
-      F.push_back(cc);
-      F.push_back(ss);
-    }
-    if (q % 2 == 0) {
-      std::vector<double> alt(q);
-      for (int k = 0; k < q; ++k) alt[k] = std::cos(M_PI * k) / std::sqrt((double)q);
-      F.push_back(alt);
-    }
-    std::vector<double> W(q * q), wt(q), obs(q);
-    for (int m = 0; m < q; ++m) {
-      double lam = 0.0;
-      for (int a = 0; a < q; ++a)
-        for (int b = 0; b < q; ++b)
-          lam += F[m][a] * std::exp(beta * std::cos(th[a] - th[b])) * F[m][b];
-      if (lam < 0.0) lam = 0.0;
-      for (int a = 0; a < q; ++a) W[a * q + m] = F[m][a] * std::sqrt(lam);
-    }
-    for (int a = 0; a < q; ++a) {
-      obs[a] = std::cos(th[a]);
-      wt[a] = std::exp(h * obs[a]);
-    }
-    init_cp(ctx(), beta, W, q, q, wt, obs);
+    init_clock_ctx(ctx(), q, beta, h);
   });
 }
 
@@ -1032,43 +1205,18 @@ trg_status trg_step(int axis, int D, int sketch_oversample) {
     if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
     if (axis < 0 || axis > 3 || D < 1 || sketch_oversample < 0)
       throw Error(TRG_ERR_ARG, "need 0 <= axis < 4, D >= 1, p >= 0");
-    try {
-      step_impl(c, axis, D, sketch_oversample);
-    } catch (const Error &e) {
-      cudaStreamSynchronize(c.stream);
-      c.arena.reset();
-      throw Error(e.code, std::string(e.what()) + " [step phase " + std::to_string(c.phase) + "]");
-    }
+    step_ctx(c, axis, D, sketch_oversample);
   });
 }
 
 trg_status trg_free_energy(double *f_per_site, double *lnZ_per_site) {
-  return guarded([&] {
-    Ctx &c = ctx();
-    if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
-    int64_t n = prod(c.dims);
-    dot(c.phi, c.psi, n, c.dscal + 3, c.scratch(), c.stream);
-    double h[4];
-    TRG_CUDA(cudaMemcpyAsync(h, c.dscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    TRG_CUDA(cudaStreamSynchronize(c.stream));
-    double lz = h[0] + std::log(std::fabs(h[3])) * std::ldexp(1.0, -c.nsteps);
-    if (lnZ_per_site) *lnZ_per_site = lz;
-    if (f_per_site) *f_per_site = c.beta > 0.0 ? -lz / c.beta : NAN;
-  });
+  return guarded([&] { free_energy_ctx(ctx(), f_per_site, lnZ_per_site); });
 }
 
 trg_status trg_magnetisation_impurity(double *m) {
   return guarded([&] {
-    Ctx &c = ctx();
-    if (!c.init || !c.have_imp) throw Error(TRG_ERR_NOINIT, "no impurity state");
     if (!m) throw Error(TRG_ERR_ARG, "m is NULL");
-    int64_t n = prod(c.dims);
-    dot(c.phi, c.psi, n, c.dscal + 3, c.scratch(), c.stream);
-    dot(c.phi, c.psi_imp, n, c.dscal + 4, c.scratch(), c.stream);
-    double h[2];
-    TRG_CUDA(cudaMemcpyAsync(h, c.dscal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    TRG_CUDA(cudaStreamSynchronize(c.stream));
-    *m = h[1] / h[0];
+    *m = magnetisation_ctx(ctx());
   });
 }
 
@@ -1174,6 +1322,118 @@ trg_status trg_step_timings(double *ms, int n) {
     if (!ms || n < 0) throw Error(TRG_ERR_ARG, "bad timing buffer");
     for (int i = 0; i < n && i < Ctx::kPhases; ++i) ms[i] = c.phase_ms[i];
   });
+}
+
+// ------------------------------------------------------------ batched instances (S14)
+trg_status trg_batch_create(int n, const int *model, const double *beta, const double *h,
+                            const int *D, const int *p, const unsigned long long *seed,
+                            int lanes, int q_swap, int q_rho, int precision) {
+  return guarded([&] {
+    if (n < 1 || !model || !beta || !h || !D || lanes < 1 || q_swap < 1 || q_rho < 0 ||
+        precision < 0 || precision > 6)
+      throw Error(TRG_ERR_ARG, "trg_batch_create: bad arguments");
+    for (int i = 0; i < n; ++i)
+      if (!(model[i] == 0 || (model[i] >= 2 && model[i] <= 8)) || !(beta[i] >= 0.0) ||
+          !std::isfinite(beta[i]) || !std::isfinite(h[i]) || D[i] < 1 || (p && p[i] < 0))
+        throw Error(TRG_ERR_ARG, "trg_batch_create: bad instance " + std::to_string(i));
+    batch_free_all();
+    auto B = std::make_unique<Batch>();
+    TRG_CUDA(cudaGetDevice(&B->device));
+    lanes = std::min(lanes, n);
+    B->lanes.resize(lanes);
+    for (Lane &L : B->lanes) {
+      L.c = std::make_unique<Ctx>();
+      L.c->q_swap = q_swap;
+      L.c->q_rho = q_rho;
+      L.c->precision = precision;
+      ensure_ctx(*L.c);
+      L.own_dscal = L.c->dscal;
+      L.own_dflag = L.c->dflag;
+    }
+    B->inst.resize(n);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) {
+      InstState &s = B->inst[i];
+      s.model = model[i];
+      s.beta = beta[i];
+      s.h = h[i];
+      s.D = D[i];
+      s.p = p ? p[i] : 2 * D[i];
+      s.seed = seed ? seed[i] : 0x5EED;
+      TRG_CUDA(cudaMalloc(&s.dscal, 512 * sizeof(double)));
+      TRG_CUDA(cudaMalloc(&s.dflag, sizeof(int)));
+      order[i] = i;
+    }
+    // longest-processing-time assignment: cost ~ D^7 plus a latency floor of a small step
+    auto cost = [&](int i) { return std::pow((double)B->inst[i].D, 7.0) + std::pow(24.0, 7.0); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    for (int i : order) {
+      Lane *best = &B->lanes[0];
+      for (Lane &L : B->lanes)
+        if (L.cost < best->cost) best = &L;
+      best->members.push_back(i);
+      best->cost += cost(i);
+    }
+    for (Lane &L : B->lanes) std::sort(L.members.begin(), L.members.end());
+    g_batch = std::move(B);
+    for_each_lane(*g_batch, [](Lane &L, InstState &s) {
+      if (s.model == 0)
+        init_ising_ctx(*L.c, s.beta, s.h);
+      else
+        init_clock_ctx(*L.c, s.model, s.beta, s.h);
+    });
+  });
+}
+
+trg_status trg_batch_step(int nsteps, double *wall_ms) {
+  return guarded([&] {
+    if (!g_batch) throw Error(TRG_ERR_NOINIT, "no batch");
+    if (nsteps < 1) throw Error(TRG_ERR_ARG, "nsteps must be >= 1");
+    const auto t0 = std::chrono::steady_clock::now();
+    for_each_lane(*g_batch, [&](Lane &L, InstState &s) {
+      for (int k = 0; k < nsteps; ++k) step_ctx(*L.c, L.c->nsteps % 4, s.D, s.p);
+      TRG_CUDA(cudaStreamSynchronize(L.c->stream));
+    });
+    if (wall_ms)
+      *wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                     .count();
+  });
+}
+
+trg_status trg_batch_results(double *f, double *lnz, double *m, int *nsteps) {
+  return guarded([&] {
+    if (!g_batch) throw Error(TRG_ERR_NOINIT, "no batch");
+    const int n = (int)g_batch->inst.size();
+    std::vector<double> hf(n), hl(n), hm(n);
+    std::vector<int> hn(n);
+    for_each_lane(*g_batch, [&](Lane &L, InstState &s) {
+      const int i = (int)(&s - g_batch->inst.data());
+      free_energy_ctx(*L.c, &hf[i], &hl[i]);
+      hm[i] = magnetisation_ctx(*L.c);
+      hn[i] = L.c->nsteps;
+    });
+    for (int i = 0; i < n; ++i) {
+      if (f) f[i] = hf[i];
+      if (lnz) lnz[i] = hl[i];
+      if (m) m[i] = hm[i];
+      if (nsteps) nsteps[i] = hn[i];
+    }
+  });
+}
+
+trg_status trg_batch_lanes(int *lane_of, long long *scratch_bytes) {
+  return guarded([&] {
+    if (!g_batch) throw Error(TRG_ERR_NOINIT, "no batch");
+    for (size_t l = 0; l < g_batch->lanes.size(); ++l) {
+      for (int i : g_batch->lanes[l].members)
+        if (lane_of) lane_of[i] = (int)l;
+      if (scratch_bytes) scratch_bytes[l] = (long long)g_batch->lanes[l].c->arena.reserved();
+    }
+  });
+}
+
+trg_status trg_batch_free(void) {
+  return guarded([&] { batch_free_all(); });
 }
 
 // ------------------------------------------------------------ learned sketch (S15)
@@ -1350,11 +1610,11 @@ trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launch
     if (tc_ms) *tc_ms = c.tc_ms;
     if (tc_flop) *tc_flop = c.tc_flop;
     if (tc_launches) *tc_launches = c.tc_launches;
-    if (all_launches) *all_launches = g_kernel_launches;
+    if (all_launches) *all_launches = g_kernel_launches.load();
     if (reset) {
       c.tc_ms = c.tc_flop = 0.0;
       c.tc_launches = 0;
-      g_kernel_launches = 0;
+      g_kernel_launches.store(0);
     }
   });
 }
