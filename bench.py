@@ -391,6 +391,7 @@ def run_ours(a):
     t_job = time.time() - t_job
     ms = ev0.elapsed_time(ev1)
     stats = trg.trg_kernel_stats(reset=True)
+    mem = trg.trg_mem_stats()
     ms_t = torch.tensor([ms], device="cuda")
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -425,6 +426,7 @@ def run_ours(a):
         "clocks": clocks,
         "phases_ms": phases,
         "free_energy": f_last[0],
+        "device_scratch_gb": {k: round(v / 2 ** 30, 2) for k, v in mem.items()},
     }
     if learned is not None:
         learned.update(trg.trg_sketch_stats())

@@ -162,8 +162,10 @@ trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long M, long lon
  * locates a transition.  The paper runs one lattice at a time; the instances share
  * nothing but the GPU.  `lanes` engine contexts (each its own CUDA stream and scratch
  * arena, driven by its own host thread) run concurrently; every instance is bound to one
- * lane (longest-processing-time assignment with cost D^7 + 24^7), which steps its
- * instances in index order.  Results do not depend on the lane count or schedule: each
+ * lane, which steps its instances in index order.  Lanes hold one bond dimension each
+ * (a lane's arena grows to its largest instance): the largest D gets a quarter of the
+ * lanes, the smaller (latency-bound) sizes share the rest by cost D^7 + 24^7; with fewer
+ * lanes than distinct sizes, longest-processing-time assignment over all instances.  Results do not depend on the lane count or schedule: each
  * instance goes through exactly the kernels of trg_step.  The batch is independent of
  * the single-instance context of trg_init_* / trg_step.
  * ------------------------------------------------------------------------------- */

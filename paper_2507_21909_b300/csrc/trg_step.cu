@@ -505,43 +505,79 @@ static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor
   return {M, N};
 }
 
-// Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG; also eq. makeMH with
-// E=H, F=G roles handled by the caller through the index strings)
+// Rows of t (the first leg, i1 of the paper's Table I) per slice of the coarse
+// contraction, so that the intermediate Phi1 (t kA k4 kX g) of one slice stays below
+// `budget` bytes (default 1 GiB; TRG_CONTRACT_SLICE_MB overrides, for tests).  The slices
+// are independent GEMM chains; their outputs are disjoint rows of Phi / Psi.
+static int64_t t_slice(int64_t kt, int64_t per_t_elems) {
+  int64_t budget = int64_t(1) << 30;
+  if (const char *e = getenv("TRG_CONTRACT_SLICE_MB")) budget = std::max<int64_t>(1, atoll(e)) << 20;
+  const int64_t per_t = std::max<int64_t>(per_t_elems * (int64_t)sizeof(double), 1);
+  return std::max<int64_t>(1, std::min<int64_t>(kt, budget / per_t));
+}
+
+// Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG), sliced over t
 static Tensor contract_upper(Ctx &c, const Tensor &E, const Tensor &F, const Tensor &I_,
                              const Tensor &J_, const Tensor &M2, const Tensor &M3,
                              const Tensor &M4) {
   const int64_t kt = E.dims[0], kr = F.dims[3];
   Tensor out = c.alloc({kt, M2.dims[2], M3.dims[2], M4.dims[2], kr});
+  const int64_t out_t = out.size() / kt, e_t = E.size() / kt;
   Arena::Mark mk = c.arena.mark();
   Tensor IM2 = contract(c, "bck,bBm->ckBm", I_, M2);
   Tensor IM2J = contract(c, "ckBm,BCl->ckmCl", IM2, J_);
   Tensor Theta = contract(c, "ckmCl,cCn->klmn", IM2J, M3);       // (kA kX k2 k3)
-  Tensor EM = contract(c, "tkda,dDm->tkamD", E, M4);             // (t kA al k4 q4)
-  Tensor Phi1 = contract(c, "tkamD,alDg->tkmlg", EM, F);         // (t kA k4 kX g)
-  Tensor r = contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta);      // (t k2 k3 k4 g)
-  TRG_CUDA(cudaMemcpyAsync(out.p, r.p, r.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  const int64_t ts = t_slice(kt, E.dims[1] * M4.dims[2] * F.dims[1] * kr);
+  for (int64_t t0 = 0; t0 < kt; t0 += ts) {
+    const int64_t tn = std::min(ts, kt - t0);
+    Arena::Mark ms = c.arena.mark();
+    Tensor Es = view(E.p + t0 * e_t, {tn, E.dims[1], E.dims[2], E.dims[3]});
+    Tensor EM = contract(c, "tkda,dDm->tkamD", Es, M4);           // (t kA al k4 q4)
+    Tensor Phi1 = contract(c, "tkamD,alDg->tkmlg", EM, F);        // (t kA k4 kX g)
+    Tensor r = contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta);     // (t k2 k3 k4 g)
+    TRG_CUDA(cudaMemcpyAsync(out.p + t0 * out_t, r.p, r.size() * 8, cudaMemcpyDeviceToDevice,
+                             c.stream));
+    c.arena.release(ms);
+  }
   c.arena.release(mk);
   return out;
 }
 
+// Psi (eq. makeMH), sliced over its first leg w
 static Tensor contract_lower(Ctx &c, const Tensor &G, const Tensor &H, const Tensor &K_,
                              const Tensor &L_, const Tensor &N2, const Tensor &N3,
                              const Tensor &N4) {
   const int64_t kt = H.dims[0], kr = G.dims[3];
   Tensor out = c.alloc({kt, N2.dims[2], N3.dims[2], N4.dims[2], kr});
+  const int64_t out_t = out.size() / kt, h_t = H.size() / kt;
   Arena::Mark mk = c.arena.mark();
   Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);
   Tensor KN2L = contract(c, "ckBm,BCl->ckmCl", KN2, L_);
   Tensor Theta = contract(c, "ckmCl,cCn->klmn", KN2L, N3);       // (kY kD k2 k3)
-  Tensor HN = contract(c, "wkdb,Ddm->wkbmD", H, N4);             // (w kD be k4 P4)
-  Tensor Psi1 = contract(c, "wkbmD,bjDg->wkmjg", HN, G);         // (w kD k4 kY g)
-  Tensor r = contract(c, "wkmjg,jkKL->wKLmg", Psi1, Theta);      // (w k2 k3 k4 g)
-  TRG_CUDA(cudaMemcpyAsync(out.p, r.p, r.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  const int64_t ts = t_slice(kt, H.dims[1] * N4.dims[2] * G.dims[1] * kr);
+  for (int64_t t0 = 0; t0 < kt; t0 += ts) {
+    const int64_t tn = std::min(ts, kt - t0);
+    Arena::Mark ms = c.arena.mark();
+    Tensor Hs = view(H.p + t0 * h_t, {tn, H.dims[1], H.dims[2], H.dims[3]});
+    Tensor HN = contract(c, "wkdb,Ddm->wkbmD", Hs, N4);           // (w kD be k4 P4)
+    Tensor Psi1 = contract(c, "wkbmD,bjDg->wkmjg", HN, G);        // (w kD k4 kY g)
+    Tensor r = contract(c, "wkmjg,jkKL->wKLmg", Psi1, Theta);     // (w k2 k3 k4 g)
+    TRG_CUDA(cudaMemcpyAsync(out.p + t0 * out_t, r.p, r.size() * 8, cudaMemcpyDeviceToDevice,
+                             c.stream));
+    c.arena.release(ms);
+  }
   c.arena.release(mk);
   return out;
 }
 
-static void replace_state(double *&dst, const Tensor &src, cudaStream_t s) {
+// state buffer <- src; the buffer is reused when the size is unchanged (the steady state),
+// because cudaFree synchronises the whole device (and so every lane of a batch)
+static void replace_state(double *&dst, int64_t old_size, const Tensor &src, cudaStream_t s) {
+  if (dst && old_size == src.size()) {
+    TRG_CUDA(cudaMemcpyAsync(dst, src.p, src.size() * sizeof(double), cudaMemcpyDeviceToDevice,
+                             s));
+    return;
+  }
   if (dst) TRG_CUDA(cudaFree(dst));
   dst = nullptr;
   if (cudaMalloc(&dst, std::max<int64_t>(src.size(), 1) * sizeof(double)) != cudaSuccess) {
@@ -860,9 +896,10 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   scale_by_scalar(PsiN.p, PsiN.size(), c.dscal + 1, 1, s);
   if (c.have_imp) scale_by_scalar(PsiImpN.p, PsiImpN.size(), c.dscal + 1, 1, s);
 
-  replace_state(c.phi, PhiN, s);
-  replace_state(c.psi, PsiN, s);
-  if (c.have_imp) replace_state(c.psi_imp, PsiImpN, s);
+  const int64_t old_size = prod(c.dims);
+  replace_state(c.phi, old_size, PhiN, s);
+  replace_state(c.psi, old_size, PsiN, s);
+  if (c.have_imp) replace_state(c.psi_imp, old_size, PsiImpN, s);
   c.dims = PhiN.dims;
   c.nsteps = n + 1;
   double hc = 1.0;
@@ -1351,7 +1388,6 @@ trg_status trg_batch_create(int n, const int *model, const double *beta, const d
       L.own_dflag = L.c->dflag;
     }
     B->inst.resize(n);
-    std::vector<int> order(n);
     for (int i = 0; i < n; ++i) {
       InstState &s = B->inst[i];
       s.model = model[i];
@@ -1362,18 +1398,67 @@ trg_status trg_batch_create(int n, const int *model, const double *beta, const d
       s.seed = seed ? seed[i] : 0x5EED;
       TRG_CUDA(cudaMalloc(&s.dscal, 512 * sizeof(double)));
       TRG_CUDA(cudaMalloc(&s.dflag, sizeof(int)));
-      order[i] = i;
     }
-    // longest-processing-time assignment: cost ~ D^7 plus a latency floor of a small step
+    // Lanes hold instances of one bond dimension each (a lane's scratch arena grows to its
+    // largest instance, so mixing sizes would give every lane the largest arena).  The
+    // largest D, whose steps already fill the GPU, gets a quarter of the lanes; the
+    // smaller, latency-bound sizes share the rest in proportion to their cost D^7 + 24^7;
+    // within a group, instances go round-robin.  With fewer lanes than sizes: plain
+    // longest-processing-time assignment over all instances.
     auto cost = [&](int i) { return std::pow((double)B->inst[i].D, 7.0) + std::pow(24.0, 7.0); };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    for (int i : order) {
-      Lane *best = &B->lanes[0];
-      for (Lane &L : B->lanes)
-        if (L.cost < best->cost) best = &L;
-      best->members.push_back(i);
-      best->cost += cost(i);
+    std::map<int, std::vector<int>, std::greater<int>> groups;
+    for (int i = 0; i < n; ++i) groups[B->inst[i].D].push_back(i);
+    const int G = (int)groups.size();
+    if (lanes >= G) {
+      std::vector<int> nl(G, 1);
+      std::vector<double> gc(G, 0.0);
+      int gi = 0;
+      for (auto &kv : groups) {
+        for (int i : kv.second) gc[gi] += cost(i);
+        ++gi;
+      }
+      int spare = lanes - G;
+      if (G > 1) {
+        const int top = std::min(spare, std::max(0, lanes / 4 - 1));
+        nl[0] += top;
+        spare -= top;
+        double rest = 0.0;
+        for (int g = 1; g < G; ++g) rest += gc[g];
+        for (int g = 1; g < G && spare > 0; ++g) {
+          const int add = (int)std::floor(spare * gc[g] / rest);
+          nl[g] += add;
+        }
+        int used = 0;
+        for (int g = 0; g < G; ++g) used += nl[g];
+        for (int g = 1; used < lanes; g = g % (G - 1) + 1, ++used) nl[g] += 1;
+      } else {
+        nl[0] = lanes;
+      }
+      int base = 0;
+      gi = 0;
+      for (auto &kv : groups) {
+        const int k = std::min<int>(nl[gi], (int)kv.second.size());
+        for (size_t j = 0; j < kv.second.size(); ++j)
+          B->lanes[base + (int)(j % k)].members.push_back(kv.second[j]);
+        base += nl[gi];
+        ++gi;
+      }
+    } else {
+      std::vector<int> order(n);
+      for (int i = 0; i < n; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+      for (int i : order) {
+        Lane *best = &B->lanes[0];
+        for (Lane &L : B->lanes)
+          if (L.cost < best->cost) best = &L;
+        best->members.push_back(i);
+        best->cost += cost(i);
+      }
     }
+    // lanes left without instances are dropped
+    B->lanes.erase(std::remove_if(B->lanes.begin(), B->lanes.end(),
+                                  [](const Lane &L) { return L.members.empty(); }),
+                   B->lanes.end());
     for (Lane &L : B->lanes) std::sort(L.members.begin(), L.members.end());
     g_batch = std::move(B);
     for_each_lane(*g_batch, [](Lane &L, InstState &s) {

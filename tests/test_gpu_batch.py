@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 # (model, beta, h, D): Ising (0) and Z3 clock (3) mixed
 INST = [(0, 0.16, 0.05, 6), (3, 0.3, 0.05, 5), (0, 0.1497, 0.0, 5), (3, 0.25, 0.1, 6),
-        (0, 0.14, 0.01, 6), (3, 0.3, 0.1, 7), (0, 0.155, 0.002, 7)]
+        (0, 0.14, 0.01, 6), (3, 0.3, 0.1, 7), (0, 0.145, 0.05, 5)]
 NSTEPS = 5
 
 

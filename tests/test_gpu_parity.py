@@ -152,3 +152,14 @@ def test_errors_are_reported(trg):
     assert e.value.code == -1
     with pytest.raises(trg.TrgError):
         trg.trg_step(0, 0, 6)
+
+
+def test_sliced_contraction_parity(trg, monkeypatch):
+    """The coarse contraction sliced over its first leg (one row of t per slice here)
+    gives the oracle's result; the slices are independent GEMM chains."""
+    monkeypatch.setenv("TRG_CONTRACT_SLICE_MB", "1")
+    st, _ = run_both(trg, 0.16, 0.05, 6, 12, 6)
+    _, lz_gpu = trg.trg_free_energy()
+    _, lz_ref = O.free_energy(st)
+    assert abs(lz_gpu - lz_ref) < 1e-10 * abs(lz_ref)
+    assert abs(trg.trg_magnetisation_impurity() - O.magnetisation(st)) < 1e-9
