@@ -72,6 +72,10 @@ struct Ctx {
     phase = i;
     if (!ev[i]) TRG_CUDA(cudaEventCreate(&ev[i]));
     TRG_CUDA(cudaEventRecord(ev[i], stream));
+    static const bool dbg = getenv("TRG_DEBUG_MEM") != nullptr;
+    if (dbg)
+      fprintf(stderr, "phase %d: scratch in use %.2f GB, high water %.2f GB\n", i,
+              arena.in_use() / 1073741824.0, arena.high_water() / 1073741824.0);
   }
 
   // CUDA-event timing of the tensor-core kernel launches inside a step
@@ -524,9 +528,11 @@ static Tensor contract_upper(Ctx &c, const Tensor &E, const Tensor &F, const Ten
   Tensor out = c.alloc({kt, M2.dims[2], M3.dims[2], M4.dims[2], kr});
   const int64_t out_t = out.size() / kt, e_t = E.size() / kt;
   Arena::Mark mk = c.arena.mark();
-  Tensor IM2 = contract(c, "bck,bBm->ckBm", I_, M2);
-  Tensor IM2J = contract(c, "ckBm,BCl->ckmCl", IM2, J_);
-  Tensor Theta = contract(c, "ckmCl,cCn->klmn", IM2J, M3);       // (kA kX k2 k3)
+  // Theta = (I M2)(J M3) over the inner legs (b, B) pairs: intermediates stay D^3 chi
+  // (the order (I M2 J) M3 would hold D^3 chi^2)
+  Tensor IM2 = contract(c, "bck,bBm->ckBm", I_, M2);              // (c kA B k2)
+  Tensor JM3 = contract(c, "BCl,cCn->Blcn", J_, M3);              // (B kX c k3)
+  Tensor Theta = contract(c, "ckBm,Blcn->klmn", IM2, JM3);        // (kA kX k2 k3)
   const int64_t ts = t_slice(kt, E.dims[1] * M4.dims[2] * F.dims[1] * kr);
   for (int64_t t0 = 0; t0 < kt; t0 += ts) {
     const int64_t tn = std::min(ts, kt - t0);
@@ -551,9 +557,9 @@ static Tensor contract_lower(Ctx &c, const Tensor &G, const Tensor &H, const Ten
   Tensor out = c.alloc({kt, N2.dims[2], N3.dims[2], N4.dims[2], kr});
   const int64_t out_t = out.size() / kt, h_t = H.size() / kt;
   Arena::Mark mk = c.arena.mark();
-  Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);
-  Tensor KN2L = contract(c, "ckBm,BCl->ckmCl", KN2, L_);
-  Tensor Theta = contract(c, "ckmCl,cCn->klmn", KN2L, N3);       // (kY kD k2 k3)
+  Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);              // (c kY B k2)
+  Tensor LN3 = contract(c, "BCl,cCn->Blcn", L_, N3);              // (B kD c k3)
+  Tensor Theta = contract(c, "ckBm,Blcn->klmn", KN2, LN3);        // (kY kD k2 k3)
   const int64_t ts = t_slice(kt, H.dims[1] * N4.dims[2] * G.dims[1] * kr);
   for (int64_t t0 = 0; t0 < kt; t0 += ts) {
     const int64_t tn = std::min(ts, kt - t0);
@@ -626,13 +632,21 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
   Tensor P2 = view(c.phi, {Nf, r}), S2 = view(c.psi, {Nf, r});
   std::unique_ptr<Crit> crit_resplit(new Crit(c));
-  auto [Qp, Rp] = orth_qr(c, P2);
-  auto [Qs, Rs] = orth_qr(c, S2);
-  Svd rs = svd_small(c, mm(c, Rp, Rs, false, true));
   const int64_t k = std::min<int64_t>(D, r);
-  Tensor A = mm_cols(c, Qp, rs.U, k), Dm = mm_cols(c, Qs, rs.V, k);
+  // only A, D and s outlive the re-split (its orthonormal factors are released)
+  Tensor A = c.alloc({Nf, k}), Dm = c.alloc({Nf, k}), svT = c.alloc({r});
+  {
+    Arena::Mark mk = c.arena.mark();
+    auto [Qp, Rp] = orth_qr(c, P2);
+    auto [Qs, Rs] = orth_qr(c, S2);
+    Svd rs = svd_small(c, mm(c, Rp, Rs, false, true));
+    gemm(c, false, false, Nf, k, r, 1.0, Qp.p, r, 0, rs.U.p, r, 0, 0.0, A.p, k, 0, 1);
+    gemm(c, false, false, Nf, k, r, 1.0, Qs.p, r, 0, rs.V.p, r, 0, 0.0, Dm.p, k, 0, 1);
+    TRG_CUDA(cudaMemcpyAsync(svT.p, rs.S.p, r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    c.arena.release(mk);
+  }
   sign_gauge(A.p, Nf, Dm.p, Nf, k, s);
-  double *sv = rs.S.p;  // first k entries used
+  double *sv = svT.p;  // first k entries used
   kill_dead(sv, k, kRankTol, A.p, Nf, Dm.p, Nf, s);
   A.dims = {d1, d2, d3, d4, k};
   Dm.dims = {d1, d2, d3, d4, k};
@@ -648,9 +662,6 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   //         Y^T Y = Y'^T (G^C (x) 1) Y',        V^T V = W^T (G^B (x) 1) W,
   //     with P the swap of the two bond legs.  Only the two Grams and the final
   //     X = (C (x) 1) X', Y = (B (x) 1) Y' cost D^7; the power rounds cost D^6.
-  Tensor C = copy(c, A), B = copy(c, Dm);
-  scale_last(c, C, sv);
-  scale_last(c, B, sv);
   const int64_t x = d1, I = d2 * d3 * d4, J = I;
   const int64_t w = std::min<int64_t>(D + p, k * I);
   const int64_t xk = x * k, rows = x * k * k;     // coordinate rows (x, leg, leg)
@@ -659,6 +670,9 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor sigT = c.alloc({w});
   double *sig = sigT.p;
   Arena::Mark mk_swap = c.arena.mark();
+  Tensor C = copy(c, A), B = copy(c, Dm);         // C = A s, B = D s (released after)
+  scale_last(c, C, sv);
+  scale_last(c, B, sv);
   Tensor Cq = permuted(c, view(C.p, {x, I, k}), {0, 2, 1});   // (x, be, I)
   Tensor Bq = permuted(c, view(B.p, {x, J, k}), {0, 2, 1});   // (x, al, J)
   Tensor GC = c.alloc({xk, xk}), GB = c.alloc({xk, xk});
@@ -872,7 +886,9 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     Tensor PA = mm(c, view(c.phi, {Nf, r}), view(A.p, {Nf, k}), true, false);
     Tensor Bimp = mm(c, view(c.psi_imp, {Nf, r}), PA, false, false);
     Bimp.dims = {x, d2, d3, d4, k};
-    Tensor CX = contract(c, "xIJKb,aIJKg->xbag", view(C.p, {x, d2, d3, d4, k}), X);
+    // C = A s: contract A with X, then scale the b leg by s
+    Tensor CX = contract(c, "xIJKb,aIJKg->xbag", A, X);
+    scale_axis(CX.p, CX.size(), (int64_t)CX.dims[2] * CX.dims[3], k, sv, 0, nullptr, 0.0, s);
     Tensor Ytil = contract(c, "xPQRa,xbag->bPQRg", Bimp, CX);
     scale_last(c, Ytil, sig, 1, sig, 0.0);
     Tensor Gimp = contract(c, "bPQRg,PQk->bkRg", Ytil, UY);
