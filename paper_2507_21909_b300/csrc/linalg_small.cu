@@ -76,12 +76,112 @@ __global__ void chol_rinv_kernel(const double *G, double *R, double *Rinv, int n
   }
 }
 
+// Same factorisation and inverse, held in shared memory as packed upper triangles (row a
+// starts at a n - a (a - 1) / 2): the per-column updates run at shared-memory latency
+// instead of L2 latency.  Every entry sees the same operations in the same order as in
+// chol_rinv_kernel, so the results are identical.  R^-1 lives in shared memory too when
+// both triangles fit, else in the output buffer.
+__device__ __forceinline__ int pk(int a, int b, int n) { return a * n - (a * (a - 1)) / 2 + (b - a); }
+
+__global__ void __launch_bounds__(512)
+chol_rinv_smem_kernel(const double *G, double *R, double *Rinv, int n, double rel_tol,
+                      double shift_rel, int x_in_smem) {
+  extern __shared__ double S[];
+  double *X = S + (size_t)n * (n + 1) / 2;   // used when x_in_smem
+  const int64_t off = (int64_t)blockIdx.x * n * n;
+  const double *g = G + off;
+  double *r = R + off;
+  double *x = Rinv + off;
+  __shared__ double s_scale, s_shift, s_piv;
+  __shared__ int s_dead;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) {
+    double mx = 0.0, tr = 0.0;
+    for (int i = 0; i < n; ++i) {
+      mx = fmax(mx, g[(int64_t)i * n + i]);
+      tr += g[(int64_t)i * n + i];
+    }
+    s_scale = mx;
+    s_shift = shift_rel * tr;
+  }
+  __syncthreads();
+  for (int a = warp; a < n; a += nw)
+    for (int b = a + lane; b < n; b += 32)
+      S[pk(a, b, n)] = g[(int64_t)a * n + b] + (a == b ? s_shift : 0.0);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double p = S[pk(j, j, n)];
+      s_dead = !(p > rel_tol * s_scale && p > 0.0);
+      s_piv = s_dead ? 0.0 : sqrt(p);
+    }
+    __syncthreads();
+    const double piv = s_piv;
+    if (s_dead) {
+      for (int i = j + tid; i < n; i += blockDim.x) S[pk(j, i, n)] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) S[pk(j, i, n)] /= piv;
+    __syncthreads();
+    if (tid == 0) S[pk(j, j, n)] = piv;
+    for (int a = j + 1 + warp; a < n; a += nw) {
+      const double ra = S[pk(j, a, n)];
+      const int rowa = pk(a, 0, n), rowj = pk(j, 0, n);
+      for (int b = a + lane; b < n; b += 32) S[rowa + b] -= ra * S[rowj + b];
+    }
+    __syncthreads();
+  }
+  for (int a = warp; a < n; a += nw)
+    for (int b = lane; b < n; b += 32) r[(int64_t)a * n + b] = b >= a ? S[pk(a, b, n)] : 0.0;
+  // inverse of the upper-triangular R, one thread per column; dead rows give zeros
+  for (int c = tid; c < n; c += blockDim.x) {
+    for (int i = c + 1; i < n; ++i) x[(int64_t)i * n + c] = 0.0;
+    for (int i = c; i >= 0; --i) {
+      const double rii = S[pk(i, i, n)];
+      double v;
+      if (rii == 0.0) {
+        v = 0.0;
+      } else if (i == c) {
+        v = 1.0 / rii;
+      } else {
+        double sum = 0.0;
+        const int rowi = pk(i, 0, n);
+        if (x_in_smem) {
+          for (int k = i + 1; k <= c; ++k) sum += S[rowi + k] * X[pk(k, c, n)];
+        } else {
+          for (int k = i + 1; k <= c; ++k) sum += S[rowi + k] * x[(int64_t)k * n + c];
+        }
+        v = -sum / rii;
+      }
+      if (x_in_smem) X[pk(i, c, n)] = v;
+      x[(int64_t)i * n + c] = v;
+    }
+  }
+}
+
 void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, double rel_tol,
                double shift_rel, cudaStream_t s) {
   if (n == 0 || batch == 0) return;
+  constexpr size_t kMaxSmem = 220 * 1024;
+  const size_t tri = (size_t)n * (n + 1) / 2 * sizeof(double);
+  if (tri <= kMaxSmem) {
+    static const bool attr_done = [] {
+      TRG_CUDA(cudaFuncSetAttribute(chol_rinv_smem_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem));
+      return true;
+    }();
+    (void)attr_done;
+    const int x_in_smem = 2 * tri <= kMaxSmem;
+    chol_rinv_smem_kernel<<<batch, 512, x_in_smem ? 2 * tri : tri, s>>>(G, R, Rinv, n, rel_tol,
+                                                                       shift_rel, x_in_smem);
+    TRG_LAUNCH_CHECK();
+    return;
+  }
   chol_rinv_kernel<<<batch, 256, 0, s>>>(G, R, Rinv, n, rel_tol, shift_rel);
   TRG_LAUNCH_CHECK();
 }
+
 
 // ------------------------------------------------------------ one-sided Jacobi
 constexpr int kSvdThreads = 1024;
