@@ -122,11 +122,23 @@ gemm_f64_thin_kernel(bool ta, bool tb, int M, int N, int64_t K, const double *__
                      int sym, double *__restrict__ ws) {
   __shared__ double As[TBK][64 + 1];
   __shared__ double Bs[TBK][64 + 1];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x;
   const int64_t kbeg = (int64_t)blockIdx.x * kchunk, kend = min(K, kbeg + kchunk);
+  // micro-tile (ty, tx) of this thread.  A symmetric Gram needs only the 136 tiles with
+  // ty <= tx; they go to the first threads, so that whole warps (not single lanes, which
+  // would still cost their warp a slot) fall idle.
+  int tx = tid % 16, ty = tid / 16;
+  if (sym) {
+    int q = tid, cg = 0;
+    while (cg < 16 && q > cg) {
+      q -= cg + 1;
+      ++cg;
+    }
+    tx = cg;
+    ty = cg < 16 ? q : 16;   // threads past the triangle get an empty tile
+  }
   const int r0 = ty * R, c0 = tx * R;
-  // a symmetric Gram needs only micro-tiles that reach the upper triangle
-  const bool active = r0 < M && c0 < N && !(sym && r0 > c0 + R - 1);
+  const bool active = r0 < M && c0 < N && ty < 16;
   double acc[R][R];
 #pragma unroll
   for (int i = 0; i < R; ++i)
@@ -205,7 +217,9 @@ gemm_f64_tall_kernel(int64_t M, int N, int K, double alpha, const double *__rest
   extern __shared__ double tall_smem[];  // B (64 x 65) then the A tile (64 x 65)
   double(*Bs)[65] = reinterpret_cast<double(*)[65]>(tall_smem);
   double(*As)[65] = reinterpret_cast<double(*)[65]>(tall_smem + 64 * 65);
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  // column group per half-warp (tx), row group per lane (ty): with an upper-triangular B
+  // the loop over k stops at the group's last column for the whole half-warp
+  const int tid = threadIdx.x, tx = tid / 16, ty = tid % 16;
   for (int idx = tid; idx < 64 * 64; idx += 256) {
     const int kk = idx / 64, nn = idx % 64;
     Bs[kk][nn] = (kk < K && nn < N) ? B[(int64_t)kk * ldb + nn] : 0.0;
