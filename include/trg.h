@@ -108,6 +108,14 @@ trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launch
 /* Device scratch of the step engine in bytes: in use now, high-water mark, reserved. */
 trg_status trg_mem_stats(long long *in_use, long long *high_water, long long *reserved);
 
+/* Gu-Wen ratio of the current coarse tensor (Sec. IV, eq. X):
+ * X = (Tr A)^2 / Tr(A^2) with A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l], the open leg being the
+ * slot of the last physical axis (t) and the other three traced pairwise.  X counts the
+ * ground-state degeneracy: -> 1 in the disordered phase, -> 2 in the Z2-ordered phase;
+ * for the initial Ising tensor at h = 0, X = 2 / (1 + exp(-4 beta)).  Synchronises.
+ * Errors: TRG_ERR_NOINIT, TRG_ERR_ARG (X NULL). */
+trg_status trg_gu_wen_ratio(double *X);
+
 /* Copy a state factor to the host.  which: 0 = Phi, 1 = Psi, 2 = Psi_imp.
  * dims_out[0..4] receives (d1, d2, d3, d4, r); host may be NULL (query only), else it
  * must hold `capacity` doubles >= d1 d2 d3 d4 r.  axes_out[0..3] (may be NULL) gets
@@ -194,6 +202,9 @@ trg_status trg_batch_lanes(int *lane_of, long long *scratch_bytes);
 
 /* Release every instance and lane. */
 trg_status trg_batch_free(void);
+
+/* Gu-Wen ratio of every instance (host array of length n); see trg_gu_wen_ratio. */
+trg_status trg_batch_gu_wen(double *X);
 
 /* ---------------------------------------------------------------------------------
  * Learned sketch of the triad-isometry range finders (Sec. II B, eq. HOSVD: U^A, U^X,

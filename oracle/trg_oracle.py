@@ -610,3 +610,17 @@ def run(model: str, d: int, beta: float, h: float, D: int, p: int, nsteps: int,
         step(st, ax, D, p, q_swap, q_rho, seed, method, mlp)
     return st
 
+
+
+def gu_wen_ratio(st: State) -> float:
+    """X = (Tr A)^2 / Tr(A^2) with A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l]  (Sec. IV, eq. X;
+    the ratio of Gu and Wen, which counts the ground-state degeneracy: 1 disordered,
+    2 in the Z2-ordered phase).  The open leg is the one of the last physical axis; the
+    other legs are traced pairwise (forward index = backward index)."""
+    d = st.d
+    slot = st.axes.index(d - 1)
+    legs = "abcdefgh"[:d]
+    fa = "".join("k" if i == slot else legs[i] for i in range(d)) + "z"
+    fb = "".join("l" if i == slot else legs[i] for i in range(d)) + "z"
+    A = np.einsum(f"{fa},{fb}->kl", st.phi, st.psi)
+    return float(np.trace(A) ** 2 / np.trace(A @ A))

@@ -16,7 +16,8 @@ EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_gemm_noalloc", "trg_sketch_set_net", "trg_sketch_get_net",
             "trg_sketch_forward", "trg_sketch_grad", "trg_sketch_train", "trg_set_sketch_mode",
             "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats", "trg_batch_create",
-            "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free"]
+            "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free",
+            "trg_gu_wen_ratio", "trg_batch_gu_wen"]
 
 TRG_SKETCH_IN, TRG_SKETCH_PARAMS = 5, 67585
 
@@ -62,6 +63,7 @@ def _load():
         "trg_batch_create": [i, pi, pd, pd, pi, pi, ctypes.POINTER(ull), i, i, i, i],
         "trg_batch_step": [i, pd], "trg_batch_results": [pd, pd, pd, pi],
         "trg_batch_lanes": [pi, pll], "trg_batch_free": [],
+        "trg_gu_wen_ratio": [pd], "trg_batch_gu_wen": [pd],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -318,3 +320,15 @@ def trg_batch_lanes(n, lanes):
 
 def trg_batch_free():
     _check(lib.trg_batch_free())
+
+
+def trg_gu_wen_ratio():
+    x = ctypes.c_double()
+    _check(lib.trg_gu_wen_ratio(ctypes.byref(x)))
+    return x.value
+
+
+def trg_batch_gu_wen(n):
+    x = np.empty(n)
+    _check(lib.trg_batch_gu_wen(x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return x

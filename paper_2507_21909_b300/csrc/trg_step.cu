@@ -1073,6 +1073,33 @@ static double magnetisation_ctx(Ctx &c) {
   return h[1] / h[0];
 }
 
+// Gu-Wen ratio X = (Tr A)^2 / Tr(A^2), A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l] (Sec. IV,
+// eq. X): the open leg is the slot of the last physical axis, the others are traced
+// pairwise.  A = Phi' Psi'^T over the three traced legs and the bond (one GEMM).
+static double gu_wen_ctx(Ctx &c) {
+  if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
+  int slot = 0;
+  for (int i = 0; i < 4; ++i)
+    if (c.axes[i] == 3) slot = i;
+  std::string fa = "abcdg", fb = "abcdg";
+  fa[slot] = 'k';
+  fb[slot] = 'l';
+  Arena::Mark mk = c.arena.mark();
+  Tensor A = contract(c, fa + "," + fb + "->kl", view(c.phi, c.dims), view(c.psi, c.dims));
+  const int64_t n = A.dims[0];
+  std::vector<double> h(n * n);
+  TRG_CUDA(cudaMemcpyAsync(h.data(), A.p, n * n * sizeof(double), cudaMemcpyDeviceToHost,
+                           c.stream));
+  TRG_CUDA(cudaStreamSynchronize(c.stream));
+  c.arena.release(mk);
+  double tr = 0.0, tr2 = 0.0;
+  for (int64_t k = 0; k < n; ++k) {
+    tr += h[k * n + k];
+    for (int64_t l = 0; l < n; ++l) tr2 += h[k * n + l] * h[l * n + k];
+  }
+  return tr * tr / tr2;
+}
+
 // one step with the error context of the phase that failed
 static void step_ctx(Ctx &c, int axis, int D, int p) {
   try {
@@ -1530,6 +1557,25 @@ trg_status trg_batch_lanes(int *lane_of, long long *scratch_bytes) {
         if (lane_of) lane_of[i] = (int)l;
       if (scratch_bytes) scratch_bytes[l] = (long long)g_batch->lanes[l].c->arena.reserved();
     }
+  });
+}
+
+trg_status trg_gu_wen_ratio(double *X) {
+  return guarded([&] {
+    if (!X) throw Error(TRG_ERR_ARG, "X is NULL");
+    *X = gu_wen_ctx(ctx());
+  });
+}
+
+trg_status trg_batch_gu_wen(double *X) {
+  return guarded([&] {
+    if (!g_batch) throw Error(TRG_ERR_NOINIT, "no batch");
+    if (!X) throw Error(TRG_ERR_ARG, "X is NULL");
+    std::vector<double> hx(g_batch->inst.size());
+    for_each_lane(*g_batch, [&](Lane &L, InstState &s) {
+      hx[&s - g_batch->inst.data()] = gu_wen_ctx(*L.c);
+    });
+    for (size_t i = 0; i < hx.size(); ++i) X[i] = hx[i];
   });
 }
 

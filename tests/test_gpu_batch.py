@@ -85,3 +85,17 @@ def test_batch_rejects_bad_arguments(trg):
         trg.trg_batch_create([1], [0.1], [0.0], [4])      # q = 1 is not a model
     with pytest.raises(trg.TrgError):
         trg.trg_batch_step(1)                              # no batch
+
+
+def test_batch_gu_wen_matches_single_instance(trg):
+    model, beta, h, D = (list(x) for x in zip(*INST))
+    n = trg.trg_batch_create(model, beta, h, D, lanes=3, precision=0)
+    trg.trg_batch_step(NSTEPS)
+    X = trg.trg_batch_gu_wen(n)
+    trg.trg_batch_free()
+    for i in (0, 1):
+        m, b, hh, d = INST[i]
+        st = O.init_ising(4, b, hh) if m == 0 else O.init_clock(4, m, b, hh)
+        for k in range(NSTEPS):
+            O.step(st, k % 4, d, 2 * d, 4, 4, 0x5EED)
+        assert abs(X[i] - O.gu_wen_ratio(st)) < 1e-10

@@ -163,3 +163,13 @@ def test_sliced_contraction_parity(trg, monkeypatch):
     _, lz_ref = O.free_energy(st)
     assert abs(lz_gpu - lz_ref) < 1e-10 * abs(lz_ref)
     assert abs(trg.trg_magnetisation_impurity() - O.magnetisation(st)) < 1e-9
+
+
+def test_gu_wen_ratio_parity(trg):
+    """Gu-Wen X of the GPU state against the oracle's at every step, plus the initial
+    tensor's closed form 2 / (1 + e^{-4 beta})."""
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
+    trg.trg_init_ising(4, 0.3, 0.0)
+    assert abs(trg.trg_gu_wen_ratio() - 2.0 / (1.0 + math.exp(-1.2))) < 1e-13
+    st, _ = run_both(trg, 0.16, 0.05, 6, 12, 6)
+    assert abs(trg.trg_gu_wen_ratio() - O.gu_wen_ratio(st)) < 1e-10

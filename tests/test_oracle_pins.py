@@ -238,3 +238,20 @@ def test_bond_swap_matches_direct_svd_of_BC():
     assert np.allclose(Xm.T @ Xm, np.eye(D), atol=1e-12)
     assert np.allclose(Ym.T @ Ym, np.eye(D), atol=1e-12)
     assert np.allclose(Xm.T @ M @ Ym, np.diag(sig), atol=1e-10 * sig[0])
+
+
+def test_gu_wen_ratio_closed_form_and_limits():
+    """X of the initial Ising tensor at h = 0: A = e^{3 beta} sum_a W_a W_a^T gives
+    X = 2 / (1 + e^{-4 beta}); the flow goes to 1 at beta = 0 and to 2 deep in the
+    ordered phase (two ground states)."""
+    for beta in (0.0, 0.1, 0.3, 1.0):
+        st = O.init_ising(4, beta, 0.0)
+        assert abs(O.gu_wen_ratio(st) - 2.0 / (1.0 + math.exp(-4.0 * beta))) < 1e-13
+    st = O.init_ising(4, 0.0, 0.0)
+    for n in range(4):
+        O.step(st, n % 4, 4, 8, 4, 4)
+        assert abs(O.gu_wen_ratio(st) - 1.0) < 1e-14
+    st = O.init_ising(4, 1.0, 0.0)
+    for n in range(6):
+        O.step(st, n % 4, 4, 8, 4, 4)
+    assert abs(O.gu_wen_ratio(st) - 2.0) < 1e-9
