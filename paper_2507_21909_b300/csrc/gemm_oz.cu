@@ -11,9 +11,12 @@
 //     L1 = sum ^a_0 ^b_1 + ^a_1 ^b_0 (integers x 2^7)
 //     H  = sum over i + j in [2, ns-1] of ^a_i ^b_j   (carries 2^-14 of the result)
 // Over a chunk of 256 K the FP32 sums L0 / L1 are exact integers (|L0 2^-14| and
-// |L1 2^-7| <= 2^22), so they are drained every chunk into int64 registers; H stays in
-// FP32 for the whole K (its rounding is 2^-38 of the result).  The epilogue forms
-// C = alpha 2^(e_r + e_c - 28) (S + H) + beta C in FP64.
+// |L1 2^-7| <= 2^22); every chunk they and that chunk's H are drained into one int64
+// fixed-point accumulator per output with 12 fractional bits (integer units on the
+// ALU: B300 issues few FP64 adds), so only H carries the FP32 rounding of one chunk.
+// |acc| <= K 2^41, so K per split stays below 2^21.  H is double-buffered in tensor
+// memory (two accumulators, alternating chunks) so the next chunk's products do not
+// wait for the drain.  The epilogue forms C = alpha 2^(e_r + e_c - 40) acc + beta C.
 //
 // CTA = 12 warps: warp 0 TMA producer, warp 1 MMA issuer (M = 128, N = 128, K = 16),
 // warps 2..9 drain TMEM (two warps per 32-lane quadrant, 64 columns each).  A pipeline
@@ -48,7 +51,7 @@ constexpr int MAX_STAGES = 8;
 // as much as 12; warps 10 and 11 only take part in the block-wide barriers
 constexpr int NWARPS = 12, THREADS = NWARPS * 32;
 constexpr int MAX_PAIRS = 36;
-constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 (power of two)
+constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 / @384 (alternating)
 
 struct Params {
   int64_t M, N, Kp, batch;
@@ -226,13 +229,15 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint64_t da = sdesc(su32(smem + (size_t)st * STAGE));
           const uint64_t db = da + (uint64_t)ns * kTileStep;
-          // lower levels (i + j >= 2) into H, which is never drained before the end
+          // lower levels (i + j >= 2) into this chunk's H buffer (H of chunk ch - 2 was
+          // drained before chunk ch - 1 started, so the buffer is free)
+          const uint32_t acc_h = tmem + (uint32_t)((2 + (ch & 1)) * BN);
 #pragma unroll
           for (int t = 2; t < ns; ++t)
 #pragma unroll
             for (int i = 0; i <= t; ++i)
-              umma(tmem + 2 * BN, da + i * kTileStep, db + (t - i) * kTileStep,
-                   (it > 0 || t > 2 || i > 0) ? 1u : 0u);
+              umma(acc_h, da + i * kTileStep, db + (t - i) * kTileStep,
+                   (ks > kbeg || t > 2 || i > 0) ? 1u : 0u);
           // levels 0 / 1 restart every chunk; the previous chunk must be drained first
           if (ks == kbeg && ch > 0) {
             if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
@@ -264,26 +269,38 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int quad = warp & 3;                // TMEM lane quadrant of this warp
     const int half = ew >> 2;                 // columns [64 half, 64 half + 64)
     const int64_t row = m0 + quad * 32 + lane;
-    long long S[64];
+    long long acc[64];   // fixed point, 12 fractional bits
 #pragma unroll
-    for (int j = 0; j < 64; ++j) S[j] = 0;
+    for (int j = 0; j < 64; ++j) acc[j] = 0;
     bool ok = true;
     for (int ch = 0; ch < nchunks; ++ch) {
       if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // L0 and L1 always have pairs (ns >= 3): exact integers of this chunk into S
+      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        uint32_t r0[16], r1[16];
-        const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64 + c * 16);
-        tld16(base, r0);
-        tld16(base + BN, r1);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const uint32_t col = (uint32_t)(half * 64 + c * 16);
+        {
+          // levels 0 and 1 (ns >= 3, so both have pairs): exact integers of this chunk
+          uint32_t r0[16], r1[16];
+          tld16(lane_base + col, r0);
+          tld16(lane_base + BN + col, r1);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int i0 = exact_int(__uint_as_float(r0[j]) * 0x1.0p-14f);
-          const int i1 = exact_int(__uint_as_float(r1[j]) * 0x1.0p-7f);
-          S[c * 16 + j] += ((long long)i0 << 14) + ((long long)i1 << 7);
+          for (int j = 0; j < 16; ++j) {
+            const int i0 = exact_int(__uint_as_float(r0[j]) * 0x1.0p-14f);
+            const int i1 = exact_int(__uint_as_float(r1[j]) * 0x1.0p-7f);
+            acc[c * 16 + j] += ((long long)i0 << 26) + ((long long)i1 << 19);
+          }
+        }
+        {
+          // this chunk's lower levels, rounded to 2^-12
+          uint32_t rh[16];
+          tld16(lane_base + (uint32_t)((2 + (ch & 1)) * BN) + col, rh);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * 4096.0f);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -294,27 +311,18 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
     const int64_t ldc = p.to_ws ? p.N : p.ldc;
     const int er = row < p.M ? decode_exp(p.ea[b * p.M + row]) : 0;
+    if (row < p.M) {
+      double *crow = Cbase + row * ldc;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      uint32_t r[16];
-      tld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN + half * 64 + c * 16), r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < p.M) {
-        double *crow = Cbase + row * ldc;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int64_t col = n0 + half * 64 + c * 16 + j;
-          if (col >= p.N) continue;
-          double v = 0.0;
-          if (done) {
-            const double h = (double)__uint_as_float(r[j]);
-            v = ldexp((double)S[c * 16 + j] + h, er + decode_exp(p.eb[b * p.N + col]) - 28);
-          }
-          if (p.to_ws)
-            crow[col] = v;
-          else
-            crow[col] = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * crow[col];
-        }
+      for (int j = 0; j < 64; ++j) {
+        const int64_t col = n0 + half * 64 + j;
+        if (col >= p.N) continue;
+        const double v =
+            done ? ldexp((double)acc[j], er + decode_exp(p.eb[b * p.N + col]) - 40) : 0.0;
+        if (p.to_ws)
+          crow[col] = v;
+        else
+          crow[col] = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * crow[col];
       }
     }
   }
@@ -552,6 +560,8 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
                                     65535 / batch);
     ksplit = std::max(ksplit, 1);
   }
+  // the fixed-point accumulator holds K 2^41 < 2^63: at most 2^21 K per split
+  ksplit = std::max<int>(ksplit, (int)((Kp + (int64_t(1) << 21) - 1) >> 21));
   int per = (nks_total + ksplit - 1) / ksplit;
   per = (per + CHUNK_KS - 1) / CHUNK_KS * CHUNK_KS;
   ksplit = (nks_total + per - 1) / per;

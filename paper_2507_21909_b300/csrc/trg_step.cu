@@ -56,6 +56,11 @@ struct Ctx {
   int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
   bool b_upper = false;        // the next GEMM's right factor is upper triangular (R^-1)
+  int ortho = 0;               // > 0: Grams and R^-1 products of an orthonormalisation (FP64)
+  int digits_override = 0;     // > 0: digit count of the next digit-form GEMMs
+  // digits of the bond swap's compression Grams G^C, G^B in the digit forms (0: the
+  // form's own; 64: FP64), for precision studies (TRG_SWAP_GRAM_DIGITS)
+  int swap_gram_digits = 0;
   // learned sketch of the triad-isometry range finders
   SketchNet net;
   int sketch_mode = 0;                      // 0 Gaussian, 1 learned (plain as fallback)
@@ -171,13 +176,16 @@ static int slices_of(int precision) {
 static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
                  const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
                  int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
-  const double work = (double)M * N * K * batch;
+  // per-matrix work decides the route, so that batching independent problems does not
+  // change how each one is computed
+  const double work = (double)M * N * K;
   static const bool dbg = getenv("TRG_DEBUG_GEMM") != nullptr;
   if (dbg)
     fprintf(stderr, "gemm phase %d M %lld N %lld K %lld batch %lld ta %d tb %d crit %d cheap %d\n",
             c.phase, (long long)M, (long long)N, (long long)K, (long long)batch, (int)ta, (int)tb,
             c.crit_depth, c.bulk_cheap);
   if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
+      c.ortho == 0 &&
       work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
       K >= 16 && !(c.b_upper && N < c.tc_min_max)) {
     Arena::Mark mk = c.arena.mark();
@@ -188,7 +196,8 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
     const bool cheap = c.precision >= TRG_PREC_OZ4 && c.bulk_cheap > 0 && c.crit_depth == 0;
     if (c.precision >= TRG_PREC_OZ4 && !cheap)
       gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-              c.precision, scr, c.stream, &c.timing);
+              c.digits_override > 0 ? c.digits_override : c.precision, scr, c.stream,
+              &c.timing);
     else
       gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
               cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing);
@@ -198,6 +207,15 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
              c.b_upper && !tb);
   }
 }
+
+// Grams that feed a Cholesky factor, and the products with its inverse, stay FP64 in the
+// mixed forms: a Gram squares the spectrum, and a digit error of 2^-35 of the largest
+// entry would swamp the eigenvalues near the truncation cut
+struct Ortho {
+  Ctx &c;
+  explicit Ortho(Ctx &cc) : c(cc) { ++c.ortho; }
+  ~Ortho() { --c.ortho; }
+};
 
 // ------------------------------------------------------------------ tensor helpers
 static Tensor copy(Ctx &c, const Tensor &a) {
@@ -327,6 +345,7 @@ static void scale_last(Ctx &c, Tensor &t, const double *v, int mode = 0,
 // each pass Q <- Q R^{-1} keeps the span, so the span error stays O(eps * cond(Y)) like
 // Householder QR; directions at the rounding level come out as zero columns.
 static Tensor orth_sc(Ctx &c, const Tensor &Y) {
+  Ortho og(c);
   int64_t w = Y.dims[1];
   Tensor out = c.alloc(Y.dims);
   Arena::Mark mk = c.arena.mark();
@@ -401,6 +420,73 @@ static Tensor rsvd_sym(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t k
   return range_from(c, rho, Om, q);
 }
 
+// nb independent shifted CholeskyQR3 (as orth_sc) on stacked Y [nb][rows][w]: every
+// Gram, Cholesky and product of a pass is one batched launch
+static Tensor orth_sc_batched(Ctx &c, const Tensor &Y) {
+  Ortho og(c);
+  const int64_t nb = Y.dims[0], rows = Y.dims[1], w = Y.dims[2];
+  Tensor out = c.alloc(Y.dims);
+  Arena::Mark mk = c.arena.mark();
+  Tensor Q = Y;
+  for (int pass = 0; pass < 3; ++pass) {
+    Tensor G = c.alloc({nb, w, w}), R = c.alloc({nb, w, w}), Ri = c.alloc({nb, w, w});
+    gemm(c, true, false, w, w, rows, 1.0, Q.p, w, rows * w, Q.p, w, rows * w, 0.0, G.p, w, w * w,
+         nb);
+    chol_rinv(G.p, R.p, Ri.p, (int)w, (int)nb, pass == 0 ? 0.0 : kPivotTol,
+              pass == 0 ? kShiftRel : 0.0, c.stream);
+    Tensor Qn = pass == 2 ? out : c.alloc({nb, rows, w});
+    c.b_upper = true;
+    gemm(c, false, false, rows, w, w, 1.0, Q.p, w, rows * w, Ri.p, w, w * w, 0.0, Qn.p, w,
+         rows * w, nb);
+    c.b_upper = false;
+    Q = Qn;
+  }
+  c.arena.release(mk);
+  return out;
+}
+
+// nb range finders (as rsvd_sym, chi < n) on stacked symmetric rho [nb][n][n]
+static Tensor rsvd_sym_batched(Ctx &c, const Tensor &rho, int64_t chi, int q,
+                               const std::vector<uint64_t> &keys) {
+  const int64_t nb = rho.dims[0], n = rho.dims[1];
+  Tensor out = c.alloc({nb, n, chi});
+  Arena::Mark mk = c.arena.mark();
+  Tensor Om = c.alloc({nb, n, chi});
+  for (int64_t b = 0; b < nb; ++b) fill_gaussian(Om.p + b * n * chi, n, chi, keys[b], c.stream);
+  auto apply = [&](const Tensor &V) {
+    Tensor Yb = c.alloc({nb, n, chi});
+    gemm(c, false, false, n, chi, n, 1.0, rho.p, n, n * n, V.p, chi, n * chi, 0.0, Yb.p, chi,
+         n * chi, nb);
+    return Yb;
+  };
+  Tensor Q = orth_sc_batched(c, apply(Om));
+  for (int i = 0; i < q; ++i) Q = orth_sc_batched(c, apply(Q));
+  TRG_CUDA(cudaMemcpyAsync(out.p, Q.p, out.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  c.arena.release(mk);
+  return out;
+}
+
+// Range finder of rho = F F^T from the factor F (n x m) alone: range((F F^T)^(q+1) Omega)
+// = range(F (F^T F)^q F^T Omega), the same sketch and the same subspace as rsvd_sym(rho),
+// but every product is with F, whose spectrum is the square root of rho's, so the digit
+// forms keep the eigenvalues near the cut (forming rho would square the spectrum).
+static Tensor rsvd_factor(Ctx &c, const Tensor &F, int64_t chi, int q, uint64_t key) {
+  const int64_t n = F.dims[0], m = F.dims[1];
+  Tensor out = c.alloc({n, chi});
+  Arena::Mark mk = c.arena.mark();
+  Tensor Om = c.alloc({n, chi});
+  fill_gaussian(Om.p, n, chi, key, c.stream);
+  auto apply = [&](const Tensor &V) {
+    Tensor Z = mm(c, F, V, true, false);          // F^T V   (m x chi)
+    return mm(c, F, Z, false, false);             // F F^T V (n x chi)
+  };
+  Tensor Q = orth_sc(c, apply(Om));
+  for (int i = 0; i < q; ++i) Q = orth_sc(c, apply(Q));
+  TRG_CUDA(cudaMemcpyAsync(out.p, Q.p, out.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  c.arena.release(mk);
+  return out;
+}
+
 // squared probe residual ||P - Q Q^T P||_F^2 into *out (device)
 static void probe_residual2(Ctx &c, const Tensor &Q, const Tensor &P, double *out) {
   Arena::Mark mk = c.arena.mark();
@@ -472,6 +558,7 @@ static Tensor range_rho(Ctx &c, const Tensor &rho, int64_t da, int64_t db, int64
 // invariant under R -> O R.
 static Tensor gram_root(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t key) {
   Crit cr(c);
+  Ortho og(c);   // all FP64: rho's range near the cut is what the squeezer keeps
   Tensor Q = rsvd_sym(c, rho, chi, q, key);
   Tensor Bm = mm(c, Q, mm(c, rho, Q, false, false), true, false);
   const int64_t cc = Bm.dims[0];
@@ -480,17 +567,12 @@ static Tensor gram_root(Ctx &c, const Tensor &rho, int64_t chi, int q, uint64_t 
   return mm(c, L, Q, false, true);                  // c' x n
 }
 
-// oblique squeezer pair on one pair bond: M (n x k) on the forward side, N on the backward
-static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor &rb, int64_t D,
-                                          int64_t chi, int q, uint64_t kf, uint64_t kb,
-                                          double *gap_out) {
-  int64_t n = rf.dims[0];
-  if (n <= D) {
-    *gap_out = INFINITY;
-    return {identity(c, n), identity(c, n)};
-  }
+// oblique squeezer pair from the Gram roots R1 (forward) and R2 (backward), chi x n each
+static std::pair<Tensor, Tensor> squeezer_from_roots(Ctx &c, const Tensor &R1, const Tensor &R2,
+                                                     int64_t D, double *gap_out) {
+  const int64_t n = R1.dims[1];
   Crit cr(c);
-  Tensor R1 = gram_root(c, rf, chi, q, kf), R2 = gram_root(c, rb, chi, q, kb);
+  Ortho og(c);
   Tensor K = mm(c, R1, R2, false, true);
   Svd sv = svd_small(c, K);
   int64_t k = std::min<int64_t>(D, K.dims[1]);
@@ -507,6 +589,43 @@ static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor
   *gap_out = ((int64_t)hs.size() > k && hs[k - 1] > 0) ? (hs[k - 1] - hs[k]) / hs[k - 1]
                                                         : INFINITY;
   return {M, N};
+}
+
+// oblique squeezer pair on one pair bond: M (n x k) on the forward side, N on the backward
+static std::pair<Tensor, Tensor> squeezer(Ctx &c, const Tensor &rf, const Tensor &rb, int64_t D,
+                                          int64_t chi, int q, uint64_t kf, uint64_t kb,
+                                          double *gap_out) {
+  int64_t n = rf.dims[0];
+  if (n <= D) {
+    *gap_out = INFINITY;
+    return {identity(c, n), identity(c, n)};
+  }
+  Crit cr(c);
+  Tensor R1 = gram_root(c, rf, chi, q, kf), R2 = gram_root(c, rb, chi, q, kb);
+  return squeezer_from_roots(c, R1, R2, D, gap_out);
+}
+
+// gram_root of nb Grams of one shape (stacked [nb][n][n], chi < n) as one batch:
+// R[b] = L_b Q_b^T, stacked [nb][chi][n]
+static Tensor gram_root_batched(Ctx &c, const Tensor &rho, int64_t chi, int q,
+                                const std::vector<uint64_t> &keys) {
+  Crit cr(c);
+  Ortho og(c);   // all FP64, as gram_root
+  const int64_t nb = rho.dims[0], n = rho.dims[1];
+  Tensor R = c.alloc({nb, chi, n});
+  Arena::Mark mk = c.arena.mark();
+  Tensor Q = rsvd_sym_batched(c, rho, chi, q, keys);
+  Tensor T = c.alloc({nb, n, chi}), Bm = c.alloc({nb, chi, chi});
+  gemm(c, false, false, n, chi, n, 1.0, rho.p, n, n * n, Q.p, chi, n * chi, 0.0, T.p, chi,
+       n * chi, nb);
+  gemm(c, true, false, chi, chi, n, 1.0, Q.p, chi, n * chi, T.p, chi, n * chi, 0.0, Bm.p, chi,
+       chi * chi, nb);
+  Tensor L = c.alloc({nb, chi, chi}), Li = c.alloc({nb, chi, chi});
+  chol_rinv(Bm.p, L.p, Li.p, (int)chi, (int)nb, kPivotTol, 0.0, c.stream);
+  gemm(c, false, true, chi, n, chi, 1.0, L.p, chi, chi * chi, Q.p, chi, n * chi, 0.0, R.p, n,
+       chi * n, nb);
+  c.arena.release(mk);
+  return R;
 }
 
 // Rows of t (the first leg, i1 of the paper's Table I) per slice of the coarse
@@ -676,8 +795,16 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor Cq = permuted(c, view(C.p, {x, I, k}), {0, 2, 1});   // (x, be, I)
   Tensor Bq = permuted(c, view(B.p, {x, J, k}), {0, 2, 1});   // (x, al, J)
   Tensor GC = c.alloc({xk, xk}), GB = c.alloc({xk, xk});
-  gemm(c, false, true, xk, xk, I, 1.0, Cq.p, I, 0, Cq.p, I, 0, 0.0, GC.p, xk, 0, 1);
-  gemm(c, false, true, xk, xk, J, 1.0, Bq.p, J, 0, Bq.p, J, 0, 0.0, GB.p, xk, 0, 1);
+  {
+    // the compression Grams square the spectra of C and B: more digits (or FP64)
+    const int gd = c.swap_gram_digits;
+    if (gd >= 64) ++c.ortho;
+    else if (c.precision >= TRG_PREC_OZ4) c.digits_override = std::max(gd, c.precision);
+    gemm(c, false, true, xk, xk, I, 1.0, Cq.p, I, 0, Cq.p, I, 0, 0.0, GC.p, xk, 0, 1);
+    gemm(c, false, true, xk, xk, J, 1.0, Bq.p, J, 0, Bq.p, J, 0, 0.0, GB.p, xk, 0, 1);
+    if (gd >= 64) --c.ortho;
+    c.digits_override = 0;
+  }
   // G (x) 1 applied to coordinates [(x leg) rows][(leg m)], then the two bond legs swapped
   auto apply_g = [&](const Tensor &G, const Tensor &Yc) {
     Tensor Z = c.alloc({x, k, k, w});
@@ -701,6 +828,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     for (int pass = 0; pass < 3; ++pass) {
       Tensor Z = apply_g(G, Qc);
       Tensor S = c.alloc({w, w}), R = c.alloc({w, w}), Ri = c.alloc({w, w});
+      Ortho og(c);   // the metric Gram and its R^-1 product in FP64
       gemm(c, true, false, w, w, rows, 1.0, Qc.p, w, 0, Z.p, w, 0, 0.0, S.p, w, 0, 1);
       chol_rinv(S.p, R.p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
                 pass == 0 ? kShiftRel : 0.0, c.stream);
@@ -789,26 +917,57 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   scale_last(c, Ys, sig);
   Tensor Wal = mm(c, view(Xs.p, {k, I * Dg}), view(Xs.p, {k, I * Dg}), false, true);
   Tensor Wbe = mm(c, view(Ys.p, {k, J * Dg}), view(Ys.p, {k, J * Dg}), false, true);
-  Tensor AW = mm(c, view(A.p, {Nf, k}), Wal, false, false);
-  AW.dims = A.dims;
-  Tensor DW = mm(c, view(Dm.p, {Nf, k}), Wbe, false, false);
-  DW.dims = Dm.dims;
   const int64_t npair = d2 * d3;
-  Tensor rhoA = contract(c, "tbcda,tBCda->bcBC", A, AW);
-  Tensor rhoX = contract(c, "abcdg,aBCdg->bcBC", Xs, Xs);
-  Tensor rhoY = contract(c, "bPQRg,bSTRg->PQST", Ys, Ys);
-  Tensor rhoD = contract(c, "wPQRb,wSTRb->PQST", Dm, DW);
   const int64_t chi = std::min<int64_t>(D + p, npair);
-  auto iso = [&](Tensor &rho, int tag) {
-    Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
-      return range_rho(c, view(rho.p, {npair, npair}), d2, d3, chi, c.q_rho, key(tag),
-                       key(TAG_PROBE_A + tag - TAG_RHO_A));
-    });
-    U.dims = {d2, d3, U.dims[1]};
-    return U;
-  };
-  Tensor UA = iso(rhoA, TAG_RHO_A), UX = iso(rhoX, TAG_RHO_X), UY = iso(rhoY, TAG_RHO_Y),
-         UD = iso(rhoD, TAG_RHO_D);
+  Tensor UA, UX, UY, UD;
+  if (chi < npair && c.sketch_mode == 0 && c.col_cap == 0) {
+    // rho = F F^T for each of the four: the range finders run on the factors F
+    // (rho^X: Xs over (al, q4, g); rho^Y: Ys; rho^A = A W_al A^T: F = A R^T with
+    // R^T R = W_al; rho^D likewise with W_be)
+    auto factor_w = [&](const Tensor &T, const Tensor &W) {   // T (t b c d a), W (a a')
+      Tensor R = c.alloc({k, k}), Ri = c.alloc({k, k});
+      {
+        Ortho og(c);
+        chol_rinv(W.p, R.p, Ri.p, (int)k, 1, kPivotTol, 0.0, s);
+      }
+      Tensor TR = mm(c, view(T.p, {Nf, k}), R, false, true);  // (t b c d l)
+      TR.dims = {d1, d2, d3, d4, k};
+      return permuted(c, TR, {1, 2, 0, 3, 4});
+    };
+    auto range = [&](int tag, auto &&make_factor) {
+      Tensor U = keep(c, {npair, chi}, [&] {
+        Tensor F = make_factor();
+        return rsvd_factor(c, view(F.p, {npair, F.size() / npair}), chi, c.q_rho, key(tag));
+      });
+      U.dims = {d2, d3, chi};
+      return U;
+    };
+    UA = range(TAG_RHO_A, [&] { return factor_w(A, Wal); });
+    UX = range(TAG_RHO_X, [&] { return permuted(c, Xs, {1, 2, 0, 3, 4}); });
+    UY = range(TAG_RHO_Y, [&] { return permuted(c, Ys, {1, 2, 0, 3, 4}); });
+    UD = range(TAG_RHO_D, [&] { return factor_w(Dm, Wbe); });
+  } else {
+    Tensor AW = mm(c, view(A.p, {Nf, k}), Wal, false, false);
+    AW.dims = A.dims;
+    Tensor DW = mm(c, view(Dm.p, {Nf, k}), Wbe, false, false);
+    DW.dims = Dm.dims;
+    Tensor rhoA = contract(c, "tbcda,tBCda->bcBC", A, AW);
+    Tensor rhoX = contract(c, "abcdg,aBCdg->bcBC", Xs, Xs);
+    Tensor rhoY = contract(c, "bPQRg,bSTRg->PQST", Ys, Ys);
+    Tensor rhoD = contract(c, "wPQRb,wSTRb->PQST", Dm, DW);
+    auto iso = [&](Tensor &rho, int tag) {
+      Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
+        return range_rho(c, view(rho.p, {npair, npair}), d2, d3, chi, c.q_rho, key(tag),
+                         key(TAG_PROBE_A + tag - TAG_RHO_A));
+      });
+      U.dims = {d2, d3, U.dims[1]};
+      return U;
+    };
+    UA = iso(rhoA, TAG_RHO_A);
+    UX = iso(rhoX, TAG_RHO_X);
+    UY = iso(rhoY, TAG_RHO_Y);
+    UD = iso(rhoD, TAG_RHO_D);
+  }
 
   c.mark(3);
   // (d) triads, eqs. E-L
@@ -861,12 +1020,36 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   const int64_t dmu[5] = {0, 0, d2, d3, d4};
   std::map<int, Tensor> Msq, Nsq;
   double gap_sq = INFINITY;
+  // the six Gram roots (forward and backward of mu = 2, 3, 4) are independent: when the
+  // three pair bonds have one size, they run as one batch
+  const int64_t nn0 = d2 * d2;
+  const bool same = d3 * d3 == nn0 && d4 * d4 == nn0 && nn0 > D;
+  const int64_t chi_s = std::min<int64_t>(D + p, nn0);
+  Tensor R6;
+  if (same && chi_s < nn0) {
+    Tensor rho6 = c.alloc({6, nn0, nn0});
+    std::vector<uint64_t> keys6;
+    for (int mu : {2, 3, 4}) {
+      const int b = 2 * (mu - 2);
+      TRG_CUDA(cudaMemcpyAsync(rho6.p + b * nn0 * nn0, rf[mu].p, nn0 * nn0 * 8,
+                               cudaMemcpyDeviceToDevice, s));
+      TRG_CUDA(cudaMemcpyAsync(rho6.p + (b + 1) * nn0 * nn0, rb[mu].p, nn0 * nn0 * 8,
+                               cudaMemcpyDeviceToDevice, s));
+      keys6.push_back(key(TAG_SQ_F2 + mu - 2));
+      keys6.push_back(key(TAG_SQ_B2 + mu - 2));
+    }
+    R6 = gram_root_batched(c, rho6, chi_s, c.q_rho, keys6);
+  }
   for (int mu : {2, 3, 4}) {
     int64_t nn = dmu[mu] * dmu[mu];
     double g;
-    auto [M, N] = squeezer(c, view(rf[mu].p, {nn, nn}), view(rb[mu].p, {nn, nn}), D,
-                           std::min<int64_t>(D + p, nn), c.q_rho, key(TAG_SQ_F2 + mu - 2),
-                           key(TAG_SQ_B2 + mu - 2), &g);
+    auto [M, N] = R6.p
+        ? squeezer_from_roots(c, view(R6.p + 2 * (mu - 2) * chi_s * nn0, {chi_s, nn0}),
+                              view(R6.p + (2 * (mu - 2) + 1) * chi_s * nn0, {chi_s, nn0}), D,
+                              &g)
+        : squeezer(c, view(rf[mu].p, {nn, nn}), view(rb[mu].p, {nn, nn}), D,
+                   std::min<int64_t>(D + p, nn), c.q_rho, key(TAG_SQ_F2 + mu - 2),
+                   key(TAG_SQ_B2 + mu - 2), &g);
     gap_sq = std::min(gap_sq, g);
     M.dims = {dmu[mu], dmu[mu], M.dims[1]};
     N.dims = {dmu[mu], dmu[mu], N.dims[1]};
@@ -946,6 +1129,7 @@ static void ensure_ctx(Ctx &c) {
   if (const char *e = getenv("TRG_TC_PHASES")) c.phase_mask = (unsigned)strtoul(e, nullptr, 0);
   if (const char *e = getenv("TRG_EXACT_EVERYWHERE")) c.cheap_policy = e[0] != '1';
   if (const char *e = getenv("TRG_TC_MIN_MAX")) c.tc_min_max = atoll(e);
+  if (const char *e = getenv("TRG_SWAP_GRAM_DIGITS")) c.swap_gram_digits = atoi(e);
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
