@@ -43,6 +43,9 @@ def args_():
     ap.add_argument("--precision", default="oz5", choices=list(PREC))
     ap.add_argument("--fp64-form-steps", type=int, default=0,
                     help="also time this many steady-state steps of the FP64 form (slow)")
+    ap.add_argument("--precision-steps", type=int, default=0,
+                    help="N > 0: also run N steps of the FP64 form and of the mixed form at "
+                         "the bench's D and report dF/F per step (slow: FP64 form)")
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "learned"],
                     help="learned: train the sketch network on rows collected from plain "
@@ -436,6 +439,20 @@ def run_ours(a):
     if not a.no_precision_check and prec != 0:
         mlp = net_dict(trg.trg_sketch_get_net()) if learned is not None else None
         line["delta_f_rel"] = precision_check(trg, prec, mlp)
+    if a.precision_steps > 0:
+        per = []
+        fs = {}
+        for pr in (prec, 0):
+            trg.trg_set_params(4, 4, 0x5EED, pr)
+            trg.trg_init_ising(4, a.beta, 0.0)
+            fs[pr] = []
+            for k in range(a.precision_steps):
+                trg.trg_step(k % 4, D, p)
+                fs[pr].append(trg.trg_free_energy()[0])
+        per = [abs(x - y) / abs(y) for x, y in zip(fs[prec], fs[0])]
+        dfr = line.setdefault("delta_f_rel", {})
+        dfr[f"vs_fp64_form_D{D}_per_step"] = per
+        dfr[f"vs_fp64_form_D{D}_max"] = max(per)
     if a.fp64_form_steps > 0:
         r = fp64_form_rate(trg, D, a.fp64_form_steps, a.beta)
         line["fp64_form"] = {"value": r, "unit": "RG steps/s", "steps": a.fp64_form_steps,
