@@ -327,6 +327,17 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def reduce_timing(ms, steps, world, dist=None, device="cpu"):
+    """Replicas: the slowest rank's timed region counts (max over ranks), and the value is
+    the steps all ranks completed in that time."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1e3)
+
+
 def run_ours(a):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -395,11 +406,7 @@ def run_ours(a):
     ms = ev0.elapsed_time(ev1)
     stats = trg.trg_kernel_stats(reset=True)
     mem = trg.trg_mem_stats()
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = world * a.steps / (ms / 1e3)
+    ms, value = reduce_timing(ms, a.steps, world, dist, "cuda")
     e2e = world * (n - n_grow) / t_job   # full-size steps per second of the whole job
     if rank != 0:
         if dist:
