@@ -492,6 +492,13 @@ void *Arena::alloc(size_t bytes) {
       return p;
     }
   }
+  // the empty chunks above the top are all too small for this request: give their
+  // memory back before asking for a bigger chunk (cudaFree waits for the device, so no
+  // kernel still reads them); otherwise a step that grows in size piles up idle chunks
+  if (chunks_.size() > top_ + 1 && !chunks_.empty()) {
+    for (size_t i = top_ + 1; i < chunks_.size(); ++i) cudaFree(chunks_[i].p);
+    chunks_.resize(top_ + 1);
+  }
   // new chunks are sized to the request (at least 1 GiB); reset() merges them into one
   size_t cap = bytes;
   if (cap < (size_t(1) << 30)) cap = size_t(1) << 30;
