@@ -423,12 +423,15 @@ double mlp_train(SketchNet &net, const float *X, const float *t, int64_t rows, i
 }
 
 // ------------------------------------------------------------------ step helpers
-__global__ void features_kernel(const double *rho, int da, int db, int chi, float *F) {
+// diag[i * stride] is rho's diagonal entry i (stride n + 1 for rho itself, 1 for a
+// vector of row norms^2 of a factor F with rho = F F^T)
+__global__ void features_kernel(const double *diag, int64_t stride, int da, int db, int chi,
+                                float *F) {
   __shared__ double s_tr;
   const int n = da * db;
   if (threadIdx.x == 0) {
     double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += rho[(int64_t)i * n + i];
+    for (int i = 0; i < n; ++i) tr += diag[(int64_t)i * stride];
     s_tr = tr;
   }
   __syncthreads();
@@ -440,7 +443,7 @@ __global__ void features_kernel(const double *rho, int da, int db, int chi, floa
     double m = 0.0;
     for (int o = 0; o < dother; ++o) {
       const int64_t idx = first ? (int64_t)i * db + o : (int64_t)o * db + i;
-      m += rho[idx * n + idx];
+      m += diag[idx * stride];
     }
     m = tr > 0.0 ? m / tr : 0.0;
     float *f = F + (int64_t)row * kMlpIn;
@@ -453,7 +456,33 @@ __global__ void features_kernel(const double *rho, int da, int db, int chi, floa
 }
 
 void sketch_features(const double *rho, int da, int db, int chi, float *F, cudaStream_t s) {
-  features_kernel<<<1, 256, 0, s>>>(rho, da, db, chi, F);
+  features_kernel<<<1, 256, 0, s>>>(rho, (int64_t)da * db + 1, da, db, chi, F);
+  TRG_LAUNCH_CHECK();
+}
+
+// one warp per row: out[r] = sum_m F[r, m]^2
+__global__ void row_sumsq_kernel(const double *F, int64_t n, int64_t m, double *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nw) {
+    double acc = 0.0;
+    for (int64_t k = lane; k < m; k += 32) {
+      const double v = F[r * m + k];
+      acc += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[r] = acc;
+  }
+}
+
+void sketch_features_factor(const double *Fm, int64_t m, int da, int db, int chi,
+                            double *diag_scratch, float *F, cudaStream_t s) {
+  const int64_t n = (int64_t)da * db;
+  const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, 148 * 8);
+  row_sumsq_kernel<<<blocks, 256, 0, s>>>(Fm, n, m, diag_scratch);
+  TRG_LAUNCH_CHECK();
+  features_kernel<<<1, 256, 0, s>>>(diag_scratch, 1, da, db, chi, F);
   TRG_LAUNCH_CHECK();
 }
 

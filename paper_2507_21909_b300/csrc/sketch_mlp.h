@@ -38,6 +38,10 @@ double mlp_train(SketchNet &net, const float *X, const float *t, int64_t rows, i
 
 // inputs of every index of the two legs of rho (n x n, n = da db): F rows da + db
 void sketch_features(const double *rho, int da, int db, int chi, float *F, cudaStream_t s);
+// the same from a factor Fm (n x m, rho = Fm Fm^T): diag(rho) = row norms^2 of Fm
+// (diag_scratch: n doubles)
+void sketch_features_factor(const double *Fm, int64_t m, int da, int db, int chi,
+                            double *diag_scratch, float *F, cudaStream_t s);
 // row weights of the sketch, w[(a b)] = 2^(code(u[a]) / 16) 2^(code(u[da + b]) / 16)
 void sketch_row_weights(const float *u, int da, int db, double *w, cudaStream_t s);
 // training targets t[i] = 0.5 log2(lev_i d) of both legs from an orthonormal Q (n x c)

@@ -467,21 +467,26 @@ static Tensor rsvd_sym_batched(Ctx &c, const Tensor &rho, int64_t chi, int q,
 }
 
 // Range finder of rho = F F^T from the factor F (n x m) alone: range((F F^T)^(q+1) Omega)
-// = range(F (F^T F)^q F^T Omega), the same sketch and the same subspace as rsvd_sym(rho),
-// but every product is with F, whose spectrum is the square root of rho's, so the digit
+// = range(F (F^T F)^q F^T Omega), the same sketch and the same subspace as on rho, but
+// every product is with F, whose spectrum is the square root of rho's, so the digit
 // forms keep the eigenvalues near the cut (forming rho would square the spectrum).
-static Tensor rsvd_factor(Ctx &c, const Tensor &F, int64_t chi, int q, uint64_t key) {
-  const int64_t n = F.dims[0], m = F.dims[1];
-  Tensor out = c.alloc({n, chi});
-  Arena::Mark mk = c.arena.mark();
-  Tensor Om = c.alloc({n, chi});
-  fill_gaussian(Om.p, n, chi, key, c.stream);
+static Tensor range_from_factor(Ctx &c, const Tensor &F, const Tensor &Om, int q) {
   auto apply = [&](const Tensor &V) {
     Tensor Z = mm(c, F, V, true, false);          // F^T V   (m x chi)
     return mm(c, F, Z, false, false);             // F F^T V (n x chi)
   };
   Tensor Q = orth_sc(c, apply(Om));
   for (int i = 0; i < q; ++i) Q = orth_sc(c, apply(Q));
+  return Q;
+}
+
+static Tensor rsvd_factor(Ctx &c, const Tensor &F, int64_t chi, int q, uint64_t key) {
+  const int64_t n = F.dims[0];
+  Tensor out = c.alloc({n, chi});
+  Arena::Mark mk = c.arena.mark();
+  Tensor Om = c.alloc({n, chi});
+  fill_gaussian(Om.p, n, chi, key, c.stream);
+  Tensor Q = range_from_factor(c, F, Om, q);
   TRG_CUDA(cudaMemcpyAsync(out.p, Q.p, out.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
   c.arena.release(mk);
   return out;
@@ -499,29 +504,33 @@ static void probe_residual2(Ctx &c, const Tensor &Q, const Tensor &P, double *ou
   c.arena.release(mk);
 }
 
-// Range of a triad Gram rho over legs (da, db).  Plain form: the Gaussian sketch.  Learned
-// form: the same Gaussian with rows rescaled by the sketch network, kept unless its
-// probe residual exceeds 1.5x the plain range's (then the plain range).  With collection
-// on, the (features, leverage target) rows of both legs are appended from the plain range.
-static Tensor range_rho(Ctx &c, const Tensor &rho, int64_t da, int64_t db, int64_t chi, int q,
-                        uint64_t key, uint64_t key_probe) {
-  const int64_t n = rho.dims[0];
+// Range of a triad Gram rho = F F^T over legs (da, db), from its factor F (n x m).
+// Plain form: the Gaussian sketch.  Learned form: the same Gaussian with rows rescaled by
+// the sketch network, kept unless its probe residual exceeds 1.5x the plain range's
+// (then the plain range).  With collection on, the (features, leverage target) rows of
+// both legs are appended from the plain range.  diag(rho) = row norms^2 of F, and the
+// probes rho P = F (F^T P).
+static Tensor range_factor_full(Ctx &c, const Tensor &F, int64_t da, int64_t db, int64_t chi,
+                                int q, uint64_t key, uint64_t key_probe) {
+  const int64_t n = F.dims[0], m = F.dims[1];
   if (chi >= n) return identity(c, n);
   const bool learned = c.sketch_mode == 1 && c.net.loaded;
   const bool collect = c.col_cap > 0;
-  if (!learned && !collect) return rsvd_sym(c, rho, chi, q, key);
+  if (!learned && !collect) return rsvd_factor(c, F, chi, q, key);
   cudaStream_t s = c.stream;
   Tensor out = c.alloc({n, chi});
   Arena::Mark mk = c.arena.mark();
   Tensor G = c.alloc({n, chi});
   fill_gaussian(G.p, n, chi, key, s);
-  Tensor Qp = range_from(c, rho, G, q);
-  Tensor F = c.alloc({(da + db) * kMlpIn / 2 + 1});   // (da + db) x 5 floats
-  sketch_features(rho.p, (int)da, (int)db, (int)chi, reinterpret_cast<float *>(F.p), s);
+  Tensor Qp = range_from_factor(c, F, G, q);
+  Tensor Fe = c.alloc({(da + db) * kMlpIn / 2 + 1});   // (da + db) x 5 floats
+  Tensor dg = c.alloc({n});
+  sketch_features_factor(F.p, m, (int)da, (int)db, (int)chi, dg.p,
+                         reinterpret_cast<float *>(Fe.p), s);
   if (collect) {
     const long long r = da + db;
     if (c.col_rows + r <= c.col_cap) {
-      TRG_CUDA(cudaMemcpyAsync(c.col_x + c.col_rows * kMlpIn, F.p, r * kMlpIn * sizeof(float),
+      TRG_CUDA(cudaMemcpyAsync(c.col_x + c.col_rows * kMlpIn, Fe.p, r * kMlpIn * sizeof(float),
                                cudaMemcpyDeviceToDevice, s));
       leverage_targets(Qp.p, (int)da, (int)db, (int)chi, c.col_t + c.col_rows, s);
       c.col_rows += r;
@@ -536,14 +545,14 @@ static Tensor range_rho(Ctx &c, const Tensor &rho, int64_t da, int64_t db, int64
   }
   Tensor U = c.alloc({(da + db) / 2 + 1});                 // da + db floats
   float *u = reinterpret_cast<float *>(U.p);
-  mlp_forward(c.net, reinterpret_cast<const float *>(F.p), da + db, u, true, s);
+  mlp_forward(c.net, reinterpret_cast<const float *>(Fe.p), da + db, u, true, s);
   Tensor w = c.alloc({n});
   sketch_row_weights(u, (int)da, (int)db, w.p, s);
   scale_rows(G.p, n, chi, w.p, s);
-  Tensor Ql = range_from(c, rho, G, q);
+  Tensor Ql = range_from_factor(c, F, G, q);
   Tensor P0 = c.alloc({n, 8});
   fill_gaussian(P0.p, n, 8, key_probe, s);
-  Tensor P = mm(c, rho, P0, false, false);
+  Tensor P = mm(c, F, mm(c, F, P0, true, false), false, false);
   Tensor r2 = c.alloc({2});
   probe_residual2(c, Ql, P, r2.p);
   probe_residual2(c, Qp, P, r2.p + 1);
@@ -920,53 +929,31 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   const int64_t npair = d2 * d3;
   const int64_t chi = std::min<int64_t>(D + p, npair);
   Tensor UA, UX, UY, UD;
-  if (chi < npair && c.sketch_mode == 0 && c.col_cap == 0) {
-    // rho = F F^T for each of the four: the range finders run on the factors F
+  {
+    // rho = F F^T for each of the four; the range finders run on the factors F
     // (rho^X: Xs over (al, q4, g); rho^Y: Ys; rho^A = A W_al A^T: F = A R^T with
-    // R^T R = W_al; rho^D likewise with W_be)
+    // R^T R = W_al; rho^D likewise with W_be).  chi >= pair dimension: identity.
     auto factor_w = [&](const Tensor &T, const Tensor &W) {   // T (t b c d a), W (a a')
       Tensor R = c.alloc({k, k}), Ri = c.alloc({k, k});
-      {
-        Ortho og(c);
-        chol_rinv(W.p, R.p, Ri.p, (int)k, 1, kPivotTol, 0.0, s);
-      }
+      chol_rinv(W.p, R.p, Ri.p, (int)k, 1, kPivotTol, 0.0, s);
       Tensor TR = mm(c, view(T.p, {Nf, k}), R, false, true);  // (t b c d l)
       TR.dims = {d1, d2, d3, d4, k};
       return permuted(c, TR, {1, 2, 0, 3, 4});
     };
     auto range = [&](int tag, auto &&make_factor) {
-      Tensor U = keep(c, {npair, chi}, [&] {
+      Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
+        if (chi >= npair) return identity(c, npair);
         Tensor F = make_factor();
-        return rsvd_factor(c, view(F.p, {npair, F.size() / npair}), chi, c.q_rho, key(tag));
+        return range_factor_full(c, view(F.p, {npair, F.size() / npair}), d2, d3, chi,
+                                 c.q_rho, key(tag), key(TAG_PROBE_A + tag - TAG_RHO_A));
       });
-      U.dims = {d2, d3, chi};
+      U.dims = {d2, d3, U.dims[1]};
       return U;
     };
     UA = range(TAG_RHO_A, [&] { return factor_w(A, Wal); });
     UX = range(TAG_RHO_X, [&] { return permuted(c, Xs, {1, 2, 0, 3, 4}); });
     UY = range(TAG_RHO_Y, [&] { return permuted(c, Ys, {1, 2, 0, 3, 4}); });
     UD = range(TAG_RHO_D, [&] { return factor_w(Dm, Wbe); });
-  } else {
-    Tensor AW = mm(c, view(A.p, {Nf, k}), Wal, false, false);
-    AW.dims = A.dims;
-    Tensor DW = mm(c, view(Dm.p, {Nf, k}), Wbe, false, false);
-    DW.dims = Dm.dims;
-    Tensor rhoA = contract(c, "tbcda,tBCda->bcBC", A, AW);
-    Tensor rhoX = contract(c, "abcdg,aBCdg->bcBC", Xs, Xs);
-    Tensor rhoY = contract(c, "bPQRg,bSTRg->PQST", Ys, Ys);
-    Tensor rhoD = contract(c, "wPQRb,wSTRb->PQST", Dm, DW);
-    auto iso = [&](Tensor &rho, int tag) {
-      Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
-        return range_rho(c, view(rho.p, {npair, npair}), d2, d3, chi, c.q_rho, key(tag),
-                         key(TAG_PROBE_A + tag - TAG_RHO_A));
-      });
-      U.dims = {d2, d3, U.dims[1]};
-      return U;
-    };
-    UA = iso(rhoA, TAG_RHO_A);
-    UX = iso(rhoX, TAG_RHO_X);
-    UY = iso(rhoY, TAG_RHO_Y);
-    UD = iso(rhoD, TAG_RHO_D);
   }
 
   c.mark(3);
