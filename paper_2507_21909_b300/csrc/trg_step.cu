@@ -1553,12 +1553,23 @@ trg_status trg_set_state(double beta, const int *dims, const double *phi, const 
 
 trg_status trg_finalize(void) {
   return guarded([&] {
+    batch_free_all();
     Ctx &c = ctx();
     if (c.stream) cudaStreamSynchronize(c.stream);
     free_state(c);
     c.arena.release();
     if (c.dscal) cudaFree(c.dscal);
     if (c.dflag) cudaFree(c.dflag);
+    if (c.d_sketch_cnt) cudaFree(c.d_sketch_cnt);
+    if (c.col_x) cudaFree(c.col_x);
+    if (c.col_t) cudaFree(c.col_t);
+    for (void *q : {(void *)c.net.w, (void *)c.net.m, (void *)c.net.v, (void *)c.net.wb})
+      if (q) cudaFree(q);
+    c.net = SketchNet{};
+    c.sketch_mode = 0;
+    c.col_x = c.col_t = nullptr;
+    c.col_cap = c.col_rows = c.col_dropped = 0;
+    c.d_sketch_cnt = nullptr;
     c.dscal = nullptr;
     c.dflag = nullptr;
     if (c.own_stream) cudaStreamDestroy(c.own_stream);
@@ -1669,7 +1680,14 @@ trg_status trg_batch_create(int n, const int *model, const double *beta, const d
         best->cost += cost(i);
       }
     }
-    // lanes left without instances are dropped
+    // lanes left without instances are dropped (their stream and buffers released)
+    for (Lane &L : B->lanes) {
+      if (!L.members.empty()) continue;
+      if (L.own_dscal) cudaFree(L.own_dscal);
+      if (L.own_dflag) cudaFree(L.own_dflag);
+      if (L.c->d_sketch_cnt) cudaFree(L.c->d_sketch_cnt);
+      if (L.c->own_stream) cudaStreamDestroy(L.c->own_stream);
+    }
     B->lanes.erase(std::remove_if(B->lanes.begin(), B->lanes.end(),
                                   [](const Lane &L) { return L.members.empty(); }),
                    B->lanes.end());
