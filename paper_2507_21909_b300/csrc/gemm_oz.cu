@@ -6,7 +6,7 @@
 //     a' = sum_s d_s 2^(-7(s+1)) + O(2^(-7 ns - 1)).
 // Slices are stored pre-scaled as BF16 values  ^a_s = d_s 2^(-7(s-1))  (exact: 8-bit
 // integers times powers of two), so that  a' b' = 2^-28 sum_{i,j} ^a_i ^b_j  and the
-// digit products fall into three tensor-memory accumulators:
+// digit products fall into three levels of tensor-memory accumulators:
 //     L0 = sum ^a_0 ^b_0            (integers x 2^14,  |chunk sum| <= 2^36)
 //     L1 = sum ^a_0 ^b_1 + ^a_1 ^b_0 (integers x 2^7)
 //     H  = sum over i + j in [2, ns-1] of ^a_i ^b_j   (carries 2^-14 of the result)
