@@ -173,3 +173,26 @@ def test_gu_wen_ratio_parity(trg):
     assert abs(trg.trg_gu_wen_ratio() - 2.0 / (1.0 + math.exp(-1.2))) < 1e-13
     st, _ = run_both(trg, 0.16, 0.05, 6, 12, 6)
     assert abs(trg.trg_gu_wen_ratio() - O.gu_wen_ratio(st)) < 1e-10
+
+
+def test_bench_configuration_full_size(trg):
+    """The bench's launch configuration (D = 48, p = 2D, OZ5 form, beta = 0.1497): the
+    first three steps (FP64 by the mixed forms' policy; still small enough for the oracle)
+    match the oracle, and the steps that follow at full size keep every leg at D with a
+    finite free energy and impurity observable (properties that hold at any size)."""
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_OZ5)
+    trg.trg_init_ising(4, 0.1497, 0.0)
+    st = O.init_ising(4, 0.1497, 0.0)
+    for n in range(3):
+        trg.trg_step(n % 4, 48, 96)
+        O.step(st, n % 4, 48, 96, 4, 4, 0x5EED)
+        dg = st.diag[-1]
+        assert min([dg["gap_swap"]] + list(dg["gap_sq"].values())) > 1e-8
+        f, lz = trg.trg_free_energy()
+        f_ref, lz_ref = O.free_energy(st)
+        assert abs(lz - lz_ref) < 1e-10 * abs(lz_ref), (n, lz, lz_ref)
+    for n in range(3, 5):
+        trg.trg_step(n % 4, 48, 96)
+        f, lz = trg.trg_free_energy()
+        assert math.isfinite(f) and math.isfinite(trg.trg_magnetisation_impurity())
+    assert list(trg.trg_state_dims(0)) == [48] * 5
