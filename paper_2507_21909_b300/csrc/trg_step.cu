@@ -1524,13 +1524,20 @@ trg_status trg_set_state(double beta, const int *dims, const double *phi, const 
                          const double *psi_imp, const int *axes, int nsteps, double logsum) {
   return guarded([&] {
     if (!dims || !phi || !psi || !axes || nsteps < 0) throw Error(TRG_ERR_ARG, "bad state");
+    // everything is checked before the current state is released
+    for (int i = 0; i < 5; ++i)
+      if (dims[i] < 1) throw Error(TRG_ERR_ARG, "dims must be >= 1");
+    int seen = 0;
+    for (int i = 0; i < 4; ++i)
+      if (axes[i] >= 0 && axes[i] < 4) seen |= 1 << axes[i];
+    if (seen != 0xF) throw Error(TRG_ERR_ARG, "axes must be a permutation of 0..3");
+    if (!std::isfinite(beta) || !(beta >= 0.0) || !std::isfinite(logsum))
+      throw Error(TRG_ERR_ARG, "need finite beta >= 0 and finite logsum");
     Ctx &c = ctx();
     ensure_ctx(c);
     TRG_CUDA(cudaStreamSynchronize(c.stream));
     free_state(c);
     c.dims.assign(dims, dims + 5);
-    for (auto d : c.dims)
-      if (d < 1) throw Error(TRG_ERR_ARG, "dims must be >= 1");
     for (int i = 0; i < 4; ++i) c.axes[i] = axes[i];
     int64_t n = prod(c.dims);
     for (auto pr : {std::make_pair(&c.phi, phi), std::make_pair(&c.psi, psi),

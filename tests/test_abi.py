@@ -49,3 +49,23 @@ def test_argument_errors_without_gpu(lib):
     assert lib.trg_set_params(4, 4, 0x5EED, 0) == 0
     lib.trg_last_error.restype = ctypes.c_char_p
     assert lib.trg_last_error() == b"ok"
+
+
+def test_set_state_rejects_bad_state_without_gpu(lib):
+    """The state is validated before anything touches the device."""
+    lib.trg_set_state.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double]
+    lib.trg_last_error.restype = ctypes.c_char_p
+    buf = (ctypes.c_double * 32)()
+    dims = (ctypes.c_int * 5)(2, 2, 2, 2, 2)
+    good_axes = (ctypes.c_int * 4)(1, 2, 3, 0)
+    for axes in ((0, 1, 2, 2), (0, 1, 2, 4), (-1, 1, 2, 3)):
+        a = (ctypes.c_int * 4)(*axes)
+        assert lib.trg_set_state(0.1, dims, buf, buf, None, a, 0, 0.0) == -1
+        assert b"permutation" in lib.trg_last_error()
+    bad_dims = (ctypes.c_int * 5)(2, 0, 2, 2, 2)
+    assert lib.trg_set_state(0.1, bad_dims, buf, buf, None, good_axes, 0, 0.0) == -1
+    assert lib.trg_set_state(float("nan"), dims, buf, buf, None, good_axes, 0, 0.0) == -1
+    assert lib.trg_set_state(0.1, dims, buf, buf, None, good_axes, -1, 0.0) == -1
+    assert lib.trg_set_state(0.1, dims, None, buf, None, good_axes, 0, 0.0) == -1
