@@ -34,6 +34,10 @@ Readings where the paper is silent (each is listed in the design doc):
     backward environments), identity when the pair dimension is <= D.
   * Normalisation c_n = ||T||_F; lnZ/V = sum_n ln(c_n)/2^n + 2^-N ln Tr(T_N).
   * Field h and the one-site impurity (magnetisation) with frozen pure projectors.
+  * ILO form (r_bond > 1, Sec. II E and Appendix A): the re-split bonds and the swapped
+    bond keep r_bond D values; the bond-swap sketch has r_bond D + p columns, so that
+    p = D gives the (r_bond + 1) D of the appendix's footnote; the triad isometries,
+    squeezers and pair legs are as in the plain form.
 """
 from __future__ import annotations
 
@@ -255,7 +259,7 @@ def resplit(phi: np.ndarray, psi: np.ndarray, D: int):
 
 
 # ----------------------------------------------------------------------------------
-# (b) bond swap: sum_{i1(n)} B C ~ X sigma Y  (eq. bond-swapping; Appendix A, r_bond = 1)
+# (b) bond swap: sum_{i1(n)} B C ~ X sigma Y  (eq. bond-swapping; Appendix A)
 # ----------------------------------------------------------------------------------
 def bond_swap(B: np.ndarray, C: np.ndarray, D: int, p: int, q_swap: int, seed: int,
               step: int):
@@ -358,14 +362,17 @@ def squeezer(rho_f: np.ndarray, rho_b: np.ndarray, D: int, chi: int, q_rho: int,
 # ----------------------------------------------------------------------------------
 # (c)-(f): the triad step in four dimensions
 # ----------------------------------------------------------------------------------
-def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, mlp=None):
+def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, mlp=None,
+                Db=None):
     """One triad-ATRG step on the re-split factors.  Legs (per site):
     A (t=i1(n+1), p2,p3,p4, al)   C = A s  (x=i1(n), q2,q3,q4, be)
     B = Dm s (x=j1(n+1)=i1(n), P2,P3,P4, al)   Dm (w=j1(n), Q2,Q3,Q4, be)
+    Db: width kept on the bond-swap line gamma (r_bond D for the ILO form, Sec. II E and
+    Appendix A; D by default).  The pair legs are still cut to D by the squeezers.
     """
     C = A * s
     B = Dm * s
-    X, sig, Y, gap_swap = bond_swap(B, C, D, p, q_swap, seed, step)
+    X, sig, Y, gap_swap = bond_swap(B, C, D if Db is None else Db, p, q_swap, seed, step)
     d2, d3, d4 = A.shape[1:4]
     chi_pair = d2 * d3
 
@@ -496,11 +503,11 @@ def contract_lower(G, H, K_, L_, Nsq):
 # ----------------------------------------------------------------------------------
 # Plain ATRG coarse graining in d dimensions (eqs. makeG / makeH), same squeezer rule
 # ----------------------------------------------------------------------------------
-def _atrg_step(A, Dm, s, D, p, q_swap, q_rho, seed, step):
+def _atrg_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, Db=None):
     d = A.ndim - 1
     C = A * s
     B = Dm * s
-    X, sig, Y, gap_swap = bond_swap(B, C, D, p, q_swap, seed, step)
+    X, sig, Y, gap_swap = bond_swap(B, C, D if Db is None else Db, p, q_swap, seed, step)
     # Up[t, p2..pd, q2..qd, g] = sum_al A[t p al] X[al q g] sigma_g ;  Lo[w, P.., Q.., g]
     Up = np.tensordot(A, X * sig, axes=([d], [0]))
     Lo = np.moveaxis(np.tensordot(Y, Dm, axes=([0], [d])), d - 1, -1)   # (P.., w, Q.., g)
@@ -553,22 +560,27 @@ def _rotate(st: State, axis: int):
 
 
 def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
-         seed: int = 0x5EED, method: str = "triad", mlp: dict | None = None) -> State:
+         seed: int = 0x5EED, method: str = "triad", mlp: dict | None = None,
+         r_bond: int = 1) -> State:
     """One coarse-graining step along physical `axis` (in place; returns st).  `mlp`
     (parameters of oracle/sketch_mlp.py) selects the learned sketch of the triad
-    isometries."""
-    if D < 1 or p < 0:
-        raise ValueError("need D >= 1 and p >= 0")
+    isometries.  r_bond > 1 is the internal-line overspanning of the bond swap (ILO,
+    Sec. II E, Appendix A): the re-split bonds alpha, beta and the swapped bond gamma
+    keep r_bond D values instead of D; the sketch of the bond swap has r_bond D + p
+    columns."""
+    if D < 1 or p < 0 or r_bond < 1:
+        raise ValueError("need D >= 1, p >= 0 and r_bond >= 1")
+    Db = r_bond * D
     _rotate(st, axis)
-    A, Dm, s = resplit(st.phi, st.psi, D)
+    A, Dm, s = resplit(st.phi, st.psi, Db)
     if method == "triad":
         if st.d != 4:
             raise ValueError("triad-ATRG is defined for d = 4")
         imp = (st.phi, st.psi_imp) if st.psi_imp is not None else None
         phi, psi, psi_imp, diag = _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, imp,
-                                              mlp)
+                                              mlp, Db)
     elif method == "atrg":
-        phi, psi, psi_imp, diag = _atrg_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps)
+        phi, psi, psi_imp, diag = _atrg_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, Db)
     else:
         raise ValueError(method)
     c = frob_norm(phi, psi)
@@ -602,12 +614,12 @@ def magnetisation(st: State) -> float:
 
 def run(model: str, d: int, beta: float, h: float, D: int, p: int, nsteps: int,
         q_swap: int = 4, q_rho: int = 4, seed: int = 0x5EED, method: str = "triad",
-        axes=None, mlp: dict | None = None) -> State:
+        axes=None, mlp: dict | None = None, r_bond: int = 1) -> State:
     """Convenience driver: nsteps steps cycling the axes 0,1,..,d-1 (or `axes`)."""
     st = init_ising(d, beta, h) if model == "ising" else init_clock(d, 3, beta, h)
     for n in range(nsteps):
         ax = (n % d) if axes is None else axes[n]
-        step(st, ax, D, p, q_swap, q_rho, seed, method, mlp)
+        step(st, ax, D, p, q_swap, q_rho, seed, method, mlp, r_bond)
     return st
 
 
