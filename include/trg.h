@@ -85,6 +85,17 @@ trg_status trg_magnetisation_impurity(double *m);
  * rounds of the triad / squeezer range finders. */
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision);
 
+/* Internal-line overspanning of the bond swap, the ILO form (Sec. II E; Appendix A with
+ * r_bond > 1): from the next trg_step on, the re-split bonds alpha, beta and the swapped
+ * bond gamma keep r_bond D singular values instead of D, and the bond-swap sketch has
+ * r_bond D + p columns (p = sketch_oversample; p = D gives the appendix's (r_bond + 1) D).
+ * The triad isometries and squeezers, and so the coarse tensor's pair legs, are as in
+ * the plain form; the coarse tensor's bond (last index of Phi and Psi) has r_bond D
+ * values.  r_bond = 1 (default) is the plain method.  Applies to the single-instance
+ * path (trg_init_* / trg_step); batched lanes use r_bond = 1.
+ * Errors: TRG_ERR_ARG (r_bond outside 1..8). */
+trg_status trg_set_bond_overspan(int r_bond);
+
 /* Run all device work on this cudaStream_t (NULL = the library's own stream). */
 trg_status trg_set_stream(void *cuda_stream);
 

@@ -45,6 +45,7 @@ struct Ctx {
   double *dscal = nullptr;  // [0] logsum [1] c [2] trace [3] trace2; [8..] dot scratch
   int *dflag = nullptr;
   int q_swap = 4, q_rho = 4, precision = TRG_PREC_FP64;
+  int r_bond = 1;              // ILO: re-split and swapped bonds keep r_bond D (Sec. II E)
   bool mixed_now = false;      // this step runs its bulk GEMMs on the tensor cores
   int crit_depth = 0;          // > 0 inside decompositions (QR, re-split, squeezer roots)
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
@@ -760,7 +761,10 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
   Tensor P2 = view(c.phi, {Nf, r}), S2 = view(c.psi, {Nf, r});
   std::unique_ptr<Crit> crit_resplit(new Crit(c));
-  const int64_t k = std::min<int64_t>(D, r);
+  // the bond lines (re-split alpha/beta, swapped gamma) keep Db = r_bond D values; the
+  // ILO form (Sec. II E, Appendix A) has r_bond > 1, the pair legs stay at D
+  const int64_t Db = D * c.r_bond;
+  const int64_t k = std::min<int64_t>(Db, r);
   // only A, D and s outlive the re-split (its orthonormal factors are released)
   Tensor A = c.alloc({Nf, k}), Dm = c.alloc({Nf, k}), svT = c.alloc({r});
   {
@@ -791,9 +795,9 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   //     with P the swap of the two bond legs.  Only the two Grams and the final
   //     X = (C (x) 1) X', Y = (B (x) 1) Y' cost D^7; the power rounds cost D^6.
   const int64_t x = d1, I = d2 * d3 * d4, J = I;
-  const int64_t w = std::min<int64_t>(D + p, k * I);
+  const int64_t w = std::min<int64_t>(Db + p, k * I);
   const int64_t xk = x * k, rows = x * k * k;     // coordinate rows (x, leg, leg)
-  const int64_t Dg = std::min<int64_t>(D, w);
+  const int64_t Dg = std::min<int64_t>(Db, w);
   Tensor X = c.alloc({k, d2, d3, d4, Dg}), Y = c.alloc({k, d2, d3, d4, Dg});
   Tensor sigT = c.alloc({w});
   double *sig = sigT.p;
@@ -1480,6 +1484,13 @@ trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int pr
     c.q_rho = q_rho;
     c.seed = seed;
     c.precision = precision;
+  });
+}
+
+trg_status trg_set_bond_overspan(int r_bond) {
+  return guarded([&] {
+    if (r_bond < 1 || r_bond > 8) throw Error(TRG_ERR_ARG, "need 1 <= r_bond <= 8");
+    ctx().r_bond = r_bond;
   });
 }
 

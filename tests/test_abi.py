@@ -47,6 +47,10 @@ def test_argument_errors_without_gpu(lib):
     assert lib.trg_set_params(4, -1, 1, 0) == -1         # q_rho >= 0
     assert lib.trg_set_params(4, 4, 1, 7) == -1          # precision
     assert lib.trg_set_params(4, 4, 0x5EED, 0) == 0
+    lib.trg_set_bond_overspan.argtypes = [ctypes.c_int]
+    assert lib.trg_set_bond_overspan(0) == -1            # r_bond >= 1
+    assert lib.trg_set_bond_overspan(9) == -1            # r_bond <= 8
+    assert lib.trg_set_bond_overspan(1) == 0
     lib.trg_last_error.restype = ctypes.c_char_p
     assert lib.trg_last_error() == b"ok"
 
