@@ -55,34 +55,40 @@ def args_():
                          "1:1, beta ~ U[0.14, 0.16], h ~ U[0, 0.01], D ~ U{16,24,32,40}) "
                          "on concurrent lanes instead of the single D=48 step")
     ap.add_argument("--lanes", type=int, default=8)
+    ap.add_argument("--r-bond", type=int, default=1,
+                    help="ILO form: bond lines overspanned to r_bond D (1 = plain method)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-check", action="store_true")
     return ap.parse_args()
 
 
 def workload(a):
-    return {"workload": f"triad-ATRG coarse-graining step, 4D Ising, beta={a.beta}, h=0, "
+    w = {"workload": f"triad-ATRG coarse-graining step, 4D Ising, beta={a.beta}, h=0, "
                         f"D={a.D}, p=2D (chi=3D), q_swap=4, q_rho=4, steady state",
             "D": a.D, "sketch_oversample": 2 * a.D, "precision": a.precision,
             "l2_flush": "none: inputs (D^5 FP64 factors) far larger than L2"}
+    if a.r_bond > 1:
+        w["workload"] += f", ILO r_bond={a.r_bond} (bond lines {a.r_bond * a.D})"
+        w["r_bond"] = a.r_bond
+    return w
 
 
 # ----------------------------------------------------------------- oracle sample
-def oracle_sample(D, budget_s=25.0):
+def oracle_sample(D, budget_s=25.0, r_bond=1):
     """Oracle time per step, from its dominant part: the coarse contraction (eqs.
-    makeMG/makeMH) on D-sized triads with the i1 leg cut to t = 1 and 2 of D slices;
-    T(t) = a + b t is extrapolated to t = D.  Other phases are not timed, so the
-    result is an upper bound on the oracle's steps/s."""
+    makeMG/makeMH) on D-sized triads (bond lines r_bond D) with the i1 leg cut to t = 1
+    and 2 of D slices; T(t) = a + b t is extrapolated to t = D.  Other phases are not
+    timed, so the result is an upper bound on the oracle's steps/s."""
     import numpy as np
     from oracle import trg_oracle as O
-    chi = 3 * D
+    chi, Db = 3 * D, r_bond * D
     rng = np.random.default_rng(0)
     times = {}
     for t in (1, 2):
-        E = rng.standard_normal((t, chi, D, D))
-        F = rng.standard_normal((D, chi, D, D))
-        G = rng.standard_normal((D, chi, D, D))
-        H = rng.standard_normal((t, chi, D, D))
+        E = rng.standard_normal((t, chi, D, Db))
+        F = rng.standard_normal((Db, chi, D, Db))
+        G = rng.standard_normal((Db, chi, D, Db))
+        H = rng.standard_normal((t, chi, D, Db))
         U = [rng.standard_normal((D, D, chi)) for _ in range(4)]
         Ms = {mu: rng.standard_normal((D, D, D)) for mu in (2, 3, 4)}
         t0 = time.time()
@@ -104,7 +110,7 @@ def run_reference(a):
     t0 = time.time()
     vals = []
     for _ in range(max(a.steps, 1)):
-        v, times, cores = oracle_sample(a.D)
+        v, times, cores = oracle_sample(a.D, r_bond=a.r_bond)
         vals.append(v)
     v = statistics.median(vals)
     sample = (f"coarse contraction (eqs. makeMG/makeMH) of one D={a.D} step with the i1 leg "
@@ -243,13 +249,14 @@ def learned_gain(trg):
     return float(np.median(r)) if r else None
 
 
-def precision_check(trg, prec, mlp=None):
+def precision_check(trg, prec, mlp=None, r_bond=1):
     """ΔF/F of the mixed form: against the FP64 CPU oracle at D=14 (16 steps; no
     near-degenerate truncation there) and against this library's FP64 form at D=24
     (12 steps; the FP64 form matches the oracle to 1e-10).  With a sketch network the
     oracle runs the same learned sketch."""
     from oracle import trg_oracle as O
-    st = O.run("ising", 4, 0.1497, 0.0, D=14, p=28, nsteps=16, q_swap=4, q_rho=4, mlp=mlp)
+    st = O.run("ising", 4, 0.1497, 0.0, D=14, p=28, nsteps=16, q_swap=4, q_rho=4, mlp=mlp,
+               r_bond=r_bond)
     f_or = O.free_energy(st)[0]
     f14 = run_f(trg, prec, 14, 16)
     f24_64 = run_f(trg, 0, 24, 12)
@@ -268,7 +275,7 @@ def fp64_form_rate(trg, D, nsteps, beta):
         trg.trg_step(n % 4, D, 2 * D)
         n += 1
         dims = trg.trg_state_dims(0)
-        if all(x == D for x in dims) and n >= 4:
+        if all(x == D for x in dims[:4]) and n >= 4:
             break
     torch.cuda.synchronize()
     t = time.time()
@@ -369,14 +376,15 @@ def run_ours(a):
     barrier()
     t_job = time.time()
     trg.trg_set_params(4, 4, 0x5EED, prec)
+    trg.trg_set_bond_overspan(a.r_bond)
     trg.trg_init_ising(4, a.beta, 0.0)
     n = 0
-    while True:  # grow the tensor until every leg and the bond reach D
+    while True:  # grow the tensor until every leg reaches D and the bond r_bond D
         trg.trg_step(n % 4, D, p)
         _ = trg.trg_free_energy()
         n += 1
         dims = trg.trg_state_dims(0)
-        if all(x == D for x in dims[:4]) and dims[4] == D and n >= 4:
+        if all(x == D for x in dims[:4]) and dims[4] == a.r_bond * D and n >= 4:
             break
         if n > 12:
             break
@@ -445,7 +453,7 @@ def run_ours(a):
         line["learned_sketch"] = learned
     if not a.no_precision_check and prec != 0:
         mlp = net_dict(trg.trg_sketch_get_net()) if learned is not None else None
-        line["delta_f_rel"] = precision_check(trg, prec, mlp)
+        line["delta_f_rel"] = precision_check(trg, prec, mlp, a.r_bond)
     if a.precision_steps > 0:
         per = []
         fs = {}
@@ -465,7 +473,7 @@ def run_ours(a):
         line["fp64_form"] = {"value": r, "unit": "RG steps/s", "steps": a.fp64_form_steps,
                              "speedup_of_value": value / r}
     if not a.no_cpu_baseline:
-        v, times, cores = oracle_sample(D)
+        v, times, cores = oracle_sample(D, r_bond=a.r_bond)
         line["cpu_baseline"] = {
             "value": v, "unit": "RG steps/s", "cores": cores, "kind": "oracle",
             "sample": f"coarse contraction (eqs. makeMG/makeMH) of one D={D} step with the i1 "

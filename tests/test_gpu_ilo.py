@@ -41,3 +41,25 @@ def test_ilo_parity(trg, D, r_bond):
     finally:
         trg.trg_set_bond_overspan(1)
 
+
+
+def test_ilo_mixed_form_oz5_within_1e8_of_oracle(trg):
+    """The exact-digit mixed form with r_bond = 2 (tensor cores from the fourth step):
+    f within 1e-8 relative of the oracle's ILO form (D = 7, bond 14, 12 steps; every cut
+    has a relative gap above 3e-3)."""
+    beta, D, r_bond, N = 0.1497, 7, 2, 12
+    trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_OZ5)
+    trg.trg_set_bond_overspan(r_bond)
+    try:
+        trg.trg_kernel_stats(reset=True)
+        trg.trg_init_ising(4, beta, 0.0)
+        for n in range(N):
+            trg.trg_step(n % 4, D, 2 * D)
+        f_gpu, _ = trg.trg_free_energy()
+        assert trg.trg_kernel_stats(reset=True)["tc_launches"] > 0
+    finally:
+        trg.trg_set_bond_overspan(1)
+        trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
+    st = O.run("ising", 4, beta, 0.0, D=D, p=2 * D, nsteps=N, r_bond=r_bond)
+    f_ref, _ = O.free_energy(st)
+    assert abs(f_gpu - f_ref) < 1e-8 * abs(f_ref)
