@@ -34,6 +34,10 @@ Readings where the paper is silent (each is listed in the design doc):
     backward environments), identity when the pair dimension is <= D.
   * Normalisation c_n = ||T||_F; lnZ/V = sum_n ln(c_n)/2^n + 2^-N ln Tr(T_N).
   * Field h and the one-site impurity (magnetisation) with frozen pure projectors.
+  * Two-impurity network (Sec. IV, internal energy): the observable sits on both sites
+    of the first step's unit cell (neighbours along its axis); that step contracts them
+    into one coarse impurity with the pure tensor's projectors, which is then carried
+    like the one-site impurity.  U = -d <s s'> uses the equivalence of the axes.
   * ILO form (r_bond > 1, Sec. II E and Appendix A): the re-split bonds and the swapped
     bond keep r_bond D values; the bond-swap sketch has r_bond D + p columns, so that
     p = D gives the (r_bond + 1) D of the appendix's footnote; the triad isometries,
@@ -186,6 +190,8 @@ class State:
     nsteps: int = 0
     logsum: float = 0.0             # sum_n ln(c_n) / 2^n
     diag: list = field(default_factory=list)
+    imp_pair: bool = False          # the impurity is a nearest-neighbour pair, merged by
+                                    # the next step (two-impurity network, Sec. IV)
 
 
 def _init_from_factor(d: int, beta: float, W: np.ndarray, weight: np.ndarray,
@@ -208,16 +214,29 @@ def _init_from_factor(d: int, beta: float, W: np.ndarray, weight: np.ndarray,
     return st
 
 
-def init_ising(d: int, beta: float, h: float = 0.0) -> State:
-    """d-dim Ising: T = sum_a e^{h s_a} prod W[a, .]  (Sec. III, field h added)."""
+def init_ising(d: int, beta: float, h: float = 0.0, impurity: str = "site") -> State:
+    """d-dim Ising: T = sum_a e^{h s_a} prod W[a, .]  (Sec. III, field h added).
+    impurity "site": one spin s (magnetisation); "pair": s on both sites of the first
+    step's unit cell, i.e. the nearest-neighbour product s_x s_(x+e) along the first
+    step's axis (the two-impurity network of Sec. IV)."""
     W, spins = ising_factor(beta)
-    return _init_from_factor(d, beta, W, np.exp(h * spins), spins)
+    st = _init_from_factor(d, beta, W, np.exp(h * spins), spins)
+    return _set_impurity(st, impurity)
 
 
-def init_clock(d: int, q: int, beta: float, h: float = 0.0) -> State:
-    """Z_q clock model, site weight e^{h cos theta}, observable cos theta."""
+def init_clock(d: int, q: int, beta: float, h: float = 0.0, impurity: str = "site") -> State:
+    """Z_q clock model, site weight e^{h cos theta}, observable cos theta (impurity as in
+    init_ising)."""
     W, cth = clock_factor(q, beta)
-    return _init_from_factor(d, beta, W, np.exp(h * cth), cth)
+    st = _init_from_factor(d, beta, W, np.exp(h * cth), cth)
+    return _set_impurity(st, impurity)
+
+
+def _set_impurity(st: State, impurity: str) -> State:
+    if impurity not in ("site", "pair"):
+        raise ValueError("impurity is 'site' or 'pair'")
+    st.imp_pair = impurity == "pair"
+    return st
 
 
 def frob_norm(phi: np.ndarray, psi: np.ndarray) -> float:
@@ -363,7 +382,7 @@ def squeezer(rho_f: np.ndarray, rho_b: np.ndarray, D: int, chi: int, q_rho: int,
 # (c)-(f): the triad step in four dimensions
 # ----------------------------------------------------------------------------------
 def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, mlp=None,
-                Db=None):
+                Db=None, imp_two=False):
     """One triad-ATRG step on the re-split factors.  Legs (per site):
     A (t=i1(n+1), p2,p3,p4, al)   C = A s  (x=i1(n), q2,q3,q4, be)
     B = Dm s (x=j1(n+1)=i1(n), P2,P3,P4, al)   Dm (w=j1(n), Q2,Q3,Q4, be)
@@ -474,8 +493,13 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, ml
         sp[s > 0] = 1.0 / s[s > 0]
         D_imp = B_imp * sp
         H_imp = np.einsum("wPQRb,PQk->wkRb", D_imp, U["D"])
-        psi_imp = 0.5 * (contract_lower(G_imp, H, K_, L_, Nsq) +
-                         contract_lower(G, H_imp, K_, L_, Nsq))
+        if imp_two:
+            # both sites of the unit cell carry the impurity: one coarse impurity tensor
+            psi_imp = contract_lower(G_imp, H_imp, K_, L_, Nsq)
+        else:
+            # one impurity, at slot n+1 or at slot n with equal weight
+            psi_imp = 0.5 * (contract_lower(G_imp, H, K_, L_, Nsq) +
+                             contract_lower(G, H_imp, K_, L_, Nsq))
     diag = {"gap_swap": gap_swap, "gap_sq": gaps, "sigma": sig, "s": s}
     if sketch_info:
         diag["sketch"] = sketch_info
@@ -578,12 +602,13 @@ def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
             raise ValueError("triad-ATRG is defined for d = 4")
         imp = (st.phi, st.psi_imp) if st.psi_imp is not None else None
         phi, psi, psi_imp, diag = _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, imp,
-                                              mlp, Db)
+                                              mlp, Db, st.imp_pair)
     elif method == "atrg":
         phi, psi, psi_imp, diag = _atrg_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, Db)
     else:
         raise ValueError(method)
     c = frob_norm(phi, psi)
+    st.imp_pair = False
     st.phi = phi
     st.psi = psi / c
     st.psi_imp = None if psi_imp is None else psi_imp / c
@@ -612,11 +637,28 @@ def magnetisation(st: State) -> float:
     return trace_T(st.phi, st.psi_imp) / trace_T(st.phi, st.psi)
 
 
+def nn_correlation(st: State) -> float:
+    """<o_x o_(x+e)> of a run started with impurity "pair": Tr(Phi Psi_imp^T) / Tr(Phi Psi^T)
+    once the first step has merged the two impurities (Sec. IV, two impurity tensors)."""
+    if st.imp_pair or st.nsteps < 1:
+        raise ValueError("the pair impurity is merged by the first step")
+    return trace_T(st.phi, st.psi_imp) / trace_T(st.phi, st.psi)
+
+
+def internal_energy(st: State) -> float:
+    """Ising coupling energy per site, U = -(1/V) d lnZ/d beta = -d <s_x s_(x+e)> on a
+    lattice whose axes are equivalent (the pair lies along the first step's axis and
+    stands for every axis; the field term -h<s> is not included)."""
+    return -st.d * nn_correlation(st)
+
+
 def run(model: str, d: int, beta: float, h: float, D: int, p: int, nsteps: int,
         q_swap: int = 4, q_rho: int = 4, seed: int = 0x5EED, method: str = "triad",
-        axes=None, mlp: dict | None = None, r_bond: int = 1) -> State:
+        axes=None, mlp: dict | None = None, r_bond: int = 1,
+        impurity: str = "site") -> State:
     """Convenience driver: nsteps steps cycling the axes 0,1,..,d-1 (or `axes`)."""
-    st = init_ising(d, beta, h) if model == "ising" else init_clock(d, 3, beta, h)
+    st = (init_ising(d, beta, h, impurity) if model == "ising"
+          else init_clock(d, 3, beta, h, impurity))
     for n in range(nsteps):
         ax = (n % d) if axes is None else axes[n]
         step(st, ax, D, p, q_swap, q_rho, seed, method, mlp, r_bond)
