@@ -96,6 +96,22 @@ trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int pr
  * Errors: TRG_ERR_ARG (r_bond outside 1..8). */
 trg_status trg_set_bond_overspan(int r_bond);
 
+/* Two-impurity network (Sec. IV; the internal energy from two impurity tensors).  Called
+ * after trg_init_* and before the first trg_step: the impurity (s, resp. cos theta) is
+ * placed on both sites of the first step's unit cell, i.e. on nearest neighbours along
+ * that step's axis; the first step contracts them into one coarse impurity tensor with
+ * the pure tensor's projectors, and later steps carry it like the one-site impurity.
+ * trg_magnetisation_impurity then returns <o_x o_(x+e)>.  A new trg_init_* or
+ * trg_set_state returns to the one-site impurity.
+ * Errors: TRG_ERR_NOINIT (no model), TRG_ERR_ARG (a step was already taken). */
+trg_status trg_set_impurity_pair(void);
+
+/* Ising coupling energy per site U = -(1/V) d lnZ/d beta = -4 <s_x s_(x+e)>, from the
+ * merged pair of trg_set_impurity_pair (the pair's axis stands for every axis; the
+ * field term -h <s> is not included).  Errors: TRG_ERR_ARG (u NULL, not the Ising
+ * model), TRG_ERR_NOINIT (no merged pair: trg_set_impurity_pair and one step first). */
+trg_status trg_internal_energy(double *u);
+
 /* Run all device work on this cudaStream_t (NULL = the library's own stream). */
 trg_status trg_set_stream(void *cuda_stream);
 

@@ -17,7 +17,8 @@ EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_sketch_forward", "trg_sketch_grad", "trg_sketch_train", "trg_set_sketch_mode",
             "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats", "trg_batch_create",
             "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free",
-            "trg_gu_wen_ratio", "trg_batch_gu_wen", "trg_set_bond_overspan"]
+            "trg_gu_wen_ratio", "trg_batch_gu_wen", "trg_set_bond_overspan",
+            "trg_set_impurity_pair", "trg_internal_energy"]
 
 TRG_SKETCH_IN, TRG_SKETCH_PARAMS = 5, 67585
 
@@ -43,7 +44,8 @@ def _load():
     sig = {
         "trg_init_ising": [i, d, d], "trg_init_clock": [i, i, d, d], "trg_step": [i, i, i],
         "trg_free_energy": [pd, pd], "trg_magnetisation_impurity": [pd],
-        "trg_set_params": [i, i, ull, i], "trg_set_bond_overspan": [i], "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
+        "trg_set_params": [i, i, ull, i], "trg_set_bond_overspan": [i], "trg_set_impurity_pair": [],
+        "trg_internal_energy": [pd], "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
         "trg_step_timings": [pd, i],
@@ -113,6 +115,18 @@ def trg_set_params(q_swap=4, q_rho=4, seed=0x5EED, precision=TRG_PREC_FP64):
 def trg_set_bond_overspan(r_bond=1):
     """ILO form: bond lines keep r_bond D values from the next step on (1 = plain)."""
     _check(lib.trg_set_bond_overspan(int(r_bond)))
+
+
+def trg_set_impurity_pair():
+    """Two-impurity network: the impurity on both sites of the first step's unit cell."""
+    _check(lib.trg_set_impurity_pair())
+
+
+def trg_internal_energy():
+    """Ising coupling energy per site -4 <s s'> from the merged impurity pair."""
+    u = ctypes.c_double()
+    _check(lib.trg_internal_energy(ctypes.byref(u)))
+    return u.value
 
 
 def trg_set_stream(stream_ptr=None):

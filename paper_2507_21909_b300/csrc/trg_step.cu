@@ -37,6 +37,10 @@ struct Ctx {
   Arena arena;
   bool init = false;
   bool have_imp = false;
+  // two-impurity network (Sec. IV): 1 = the impurity stands on both sites of the next
+  // step's unit cell (merged by that step), 2 = merged nearest-neighbour pair
+  int imp_pair = 0;
+  bool ising = false;          // the model is Ising (internal energy from the pair)
   double beta = 0.0;
   double *phi = nullptr, *psi = nullptr, *psi_imp = nullptr;  // persistent state
   std::vector<int64_t> dims;                                   // d1..d4, r
@@ -1070,9 +1074,15 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     Tensor Dimp = copy(c, Bimp);
     scale_last(c, Dimp, sv, 1, sv, 0.0);
     Tensor Himp = contract(c, "wPQRb,PQk->wkRb", Dimp, UD);
-    PsiImpN = contract_lower(c, Gimp, H, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
-    Tensor Pb = contract_lower(c, G, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
-    axpby(PsiImpN.p, Pb.p, 0.5, 0.5, PsiImpN.size(), s);
+    if (c.imp_pair == 1) {
+      // both sites of the unit cell carry the impurity: one coarse impurity tensor
+      PsiImpN = contract_lower(c, Gimp, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+    } else {
+      // one impurity, at slot n+1 or at slot n with equal weight
+      PsiImpN = contract_lower(c, Gimp, H, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+      Tensor Pb = contract_lower(c, G, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
+      axpby(PsiImpN.p, Pb.p, 0.5, 0.5, PsiImpN.size(), s);
+    }
   }
 
   c.mark(7);
@@ -1092,6 +1102,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   if (c.have_imp) replace_state(c.psi_imp, old_size, PsiImpN, s);
   c.dims = PhiN.dims;
   c.nsteps = n + 1;
+  if (c.imp_pair == 1) c.imp_pair = 2;
   double hc = 1.0;
   int flag = 0;
   TRG_CUDA(cudaMemcpyAsync(&hc, c.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1180,12 +1191,15 @@ static void init_cp(Ctx &c, double beta, const std::vector<double> &W, int nstat
   c.beta = beta;
   c.nsteps = 0;
   c.have_imp = true;
+  c.imp_pair = 0;
+  c.ising = false;
   c.init = true;
 }
 
 static void init_ising_ctx(Ctx &c, double beta, double h) {
   double cb = std::sqrt(std::cosh(beta)), sb = std::sqrt(std::sinh(beta));
   init_cp(c, beta, {cb, sb, cb, -sb}, 2, 2, {std::exp(h), std::exp(-h)}, {1.0, -1.0});
+  c.ising = true;
 }
 
 static void init_clock_ctx(Ctx &c, int q, double beta, double h) {
@@ -1487,6 +1501,26 @@ trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int pr
   });
 }
 
+trg_status trg_set_impurity_pair(void) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!c.init || !c.have_imp) throw Error(TRG_ERR_NOINIT, "no model initialised");
+    if (c.nsteps != 0) throw Error(TRG_ERR_ARG, "the pair is placed before the first step");
+    c.imp_pair = 1;
+  });
+}
+
+trg_status trg_internal_energy(double *u) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!u) throw Error(TRG_ERR_ARG, "u is NULL");
+    if (c.imp_pair != 2)
+      throw Error(TRG_ERR_NOINIT, "no merged impurity pair (trg_set_impurity_pair, then a step)");
+    if (!c.ising) throw Error(TRG_ERR_ARG, "the pair gives the internal energy of the Ising model");
+    *u = -4.0 * magnetisation_ctx(c);
+  });
+}
+
 trg_status trg_set_bond_overspan(int r_bond) {
   return guarded([&] {
     if (r_bond < 1 || r_bond > 8) throw Error(TRG_ERR_ARG, "need 1 <= r_bond <= 8");
@@ -1565,6 +1599,8 @@ trg_status trg_set_state(double beta, const int *dims, const double *phi, const 
     c.beta = beta;
     c.nsteps = nsteps;
     c.have_imp = psi_imp != nullptr;
+    c.imp_pair = 0;
+    c.ising = false;
     c.init = true;
   });
 }
