@@ -104,6 +104,24 @@ trg_status trg_set_bond_overspan(int r_bond);
  * trg_magnetisation_impurity then returns <o_x o_(x+e)>.  A new trg_init_* or
  * trg_set_state returns to the one-site impurity.
  * Errors: TRG_ERR_NOINIT (no model), TRG_ERR_ARG (a step was already taken). */
+/* Plain ATRG (eqs. makeG / makeH), the paper's comparison method, for the Ising model
+ * in d = 2, 3 or 4 dimensions, with its own state (independent of trg_init_* /
+ * trg_step).  Same re-split, Gaussian sketches (trg_set_params: q_swap, q_rho, seed,
+ * precision), squeezer rule and normalisation as the triad step; the bond swap and the
+ * blocks A X sigma, Y D are formed as tensors of D^(2d) values, so d = 4 is limited to
+ * small D (about 12 on one GPU).  For d = 2 the triad form coincides with this method
+ * (Sec. II B), and the free energy compares with Onsager's solution.
+ * trg_atrg_init_ising: T0 of Sec. III in d dimensions with field h.  Errors:
+ * TRG_ERR_ARG (d outside 2..4, beta < 0 or not finite), TRG_ERR_OOM, TRG_ERR_CUDA. */
+trg_status trg_atrg_init_ising(int d, double beta, double h);
+/* One step along physical axis 0 <= axis < d, bond dimension D, sketch oversampling p.
+ * Errors: TRG_ERR_NOINIT, TRG_ERR_ARG, TRG_ERR_OOM, TRG_ERR_CUDA, TRG_ERR_NONFINITE. */
+trg_status trg_atrg_step(int axis, int D, int sketch_oversample);
+/* f and lnZ/V of the ATRG state, as trg_free_energy.  Errors: TRG_ERR_NOINIT. */
+trg_status trg_atrg_free_energy(double *f_per_site, double *lnZ_per_site);
+/* ln c_n of the last ATRG step, the smallest relative gap at its cuts, steps taken. */
+trg_status trg_atrg_diag(double *log_c, double *min_gap, int *nsteps);
+
 trg_status trg_set_impurity_pair(void);
 
 /* Ising coupling energy per site U = -(1/V) d lnZ/d beta = -4 <s_x s_(x+e)>, from the

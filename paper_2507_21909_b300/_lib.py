@@ -18,7 +18,8 @@ EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_sketch_collect", "trg_sketch_fetch", "trg_sketch_stats", "trg_batch_create",
             "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free",
             "trg_gu_wen_ratio", "trg_batch_gu_wen", "trg_set_bond_overspan",
-            "trg_set_impurity_pair", "trg_internal_energy"]
+            "trg_set_impurity_pair", "trg_internal_energy", "trg_atrg_init_ising",
+            "trg_atrg_step", "trg_atrg_free_energy", "trg_atrg_diag"]
 
 TRG_SKETCH_IN, TRG_SKETCH_PARAMS = 5, 67585
 
@@ -45,7 +46,9 @@ def _load():
         "trg_init_ising": [i, d, d], "trg_init_clock": [i, i, d, d], "trg_step": [i, i, i],
         "trg_free_energy": [pd, pd], "trg_magnetisation_impurity": [pd],
         "trg_set_params": [i, i, ull, i], "trg_set_bond_overspan": [i], "trg_set_impurity_pair": [],
-        "trg_internal_energy": [pd], "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
+        "trg_internal_energy": [pd], "trg_atrg_init_ising": [i, d, d],
+        "trg_atrg_step": [i, i, i], "trg_atrg_free_energy": [pd, pd], "trg_atrg_diag": [pd, pd, pi],
+        "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
         "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
         "trg_step_timings": [pd, i],
@@ -127,6 +130,26 @@ def trg_internal_energy():
     u = ctypes.c_double()
     _check(lib.trg_internal_energy(ctypes.byref(u)))
     return u.value
+
+
+def trg_atrg_init_ising(d, beta, h=0.0):
+    _check(lib.trg_atrg_init_ising(int(d), float(beta), float(h)))
+
+
+def trg_atrg_step(axis, D, sketch_oversample):
+    _check(lib.trg_atrg_step(int(axis), int(D), int(sketch_oversample)))
+
+
+def trg_atrg_free_energy():
+    f, lz = ctypes.c_double(), ctypes.c_double()
+    _check(lib.trg_atrg_free_energy(ctypes.byref(f), ctypes.byref(lz)))
+    return f.value, lz.value
+
+
+def trg_atrg_diag():
+    lc, gp, ns = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib.trg_atrg_diag(ctypes.byref(lc), ctypes.byref(gp), ctypes.byref(ns)))
+    return lc.value, gp.value, ns.value
 
 
 def trg_set_stream(stream_ptr=None):
