@@ -73,3 +73,17 @@ def test_set_state_rejects_bad_state_without_gpu(lib):
     assert lib.trg_set_state(float("nan"), dims, buf, buf, None, good_axes, 0, 0.0) == -1
     assert lib.trg_set_state(0.1, dims, buf, buf, None, good_axes, -1, 0.0) == -1
     assert lib.trg_set_state(0.1, dims, None, buf, None, good_axes, 0, 0.0) == -1
+
+
+def test_new_entry_points_reject_without_gpu(lib):
+    """Argument and state checks of the ATRG comparator and the impurity pair come before
+    any device work."""
+    lib.trg_atrg_init_ising.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.trg_atrg_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.trg_internal_energy.argtypes = [ctypes.c_void_p]
+    assert lib.trg_atrg_init_ising(1, 0.2, 0.0) == -1         # d in 2..4
+    assert lib.trg_atrg_init_ising(5, 0.2, 0.0) == -1
+    assert lib.trg_atrg_init_ising(2, -0.1, 0.0) == -1        # beta >= 0
+    assert lib.trg_atrg_step(0, 4, 8) == -6                   # no ATRG model yet
+    assert lib.trg_set_impurity_pair() == -6                  # no model yet
+    assert lib.trg_internal_energy(None) == -1                # NULL output
