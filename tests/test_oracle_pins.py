@@ -111,6 +111,20 @@ def test_brute_force_untruncated(L, axes, beta, h):
     assert abs(O.magnetisation(st) - m_b) < 1e-13
 
 
+@pytest.mark.parametrize("d,L,axes", [(2, (2, 2), [0, 1]), (2, (4, 1), [0, 0]),
+                                      (3, (2, 2, 1), [0, 1]), (3, (2, 1, 2), [2, 0]),
+                                      (4, (2, 2, 1, 1), [1, 0])])
+@pytest.mark.parametrize("beta,h", [(0.3, 0.0), (0.25, 0.2)])
+def test_atrg_brute_force_untruncated(d, L, axes, beta, h):
+    """Plain ATRG (eqs. makeG / makeH) in d = 2, 3, 4, every cut untruncated: exact."""
+    lz_b, _ = brute_force(L, beta, h)
+    st = O.init_ising(d, beta, h)
+    for ax in axes:
+        O.step(st, ax, D=16, p=256, q_swap=2, method="atrg")
+    _, lz = O.free_energy(st)
+    assert abs(lz - lz_b) < 1e-13 * abs(lz_b)
+
+
 # ------------------------------------------------ triad with full chi == ATRG
 @pytest.mark.parametrize("D", [4, 5])
 def test_untruncated_triad_equals_atrg(D):
