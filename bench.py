@@ -55,6 +55,10 @@ def args_():
                          "1:1, beta ~ U[0.14, 0.16], h ~ U[0, 0.01], D ~ U{16,24,32,40}) "
                          "on concurrent lanes instead of the single D=48 step")
     ap.add_argument("--lanes", type=int, default=8)
+    ap.add_argument("--compare-atrg", default="",
+                    help="comma-separated D list: time the triad step against the plain "
+                         "ATRG step (4D Ising, same precision and sketches) at each D "
+                         "instead of the single D=48 step; ATRG holds D^8 tensors, so D <= 12")
     ap.add_argument("--r-bond", type=int, default=1,
                     help="ILO form: bond lines overspanned to r_bond D (1 = plain method)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -334,6 +338,51 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_compare_atrg(a):
+    """Steady-state ms per step of the triad step and of the plain ATRG step (the paper's
+    comparison, Sec. III C) at each D, 4D Ising, one GPU.  Each method grows its tensor
+    for 8 steps (every leg reaches D), then a.warmup untimed and a.steps timed steps."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2507_21909_b300 as trg
+    stream = torch.cuda.Stream()
+    trg.trg_set_stream(stream.cuda_stream)
+    prec = PREC[a.precision]
+    rows = []
+    for D in [int(v) for v in a.compare_atrg.split(",") if v.strip()]:
+        row = {"D": D, "p": 2 * D}
+        for name, init, step in (
+                ("triad", lambda: trg.trg_init_ising(4, a.beta, 0.0), trg.trg_step),
+                ("atrg", lambda: trg.trg_atrg_init_ising(4, a.beta, 0.0), trg.trg_atrg_step)):
+            trg.trg_set_params(4, 4, 0x5EED, prec)
+            init()
+            n = 0
+            for _ in range(8 + a.warmup):
+                step(n % 4, D, 2 * D)
+                n += 1
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(a.steps):
+                step(n % 4, D, 2 * D)
+                n += 1
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            row[f"{name}_ms_per_step"] = ev0.elapsed_time(ev1) / a.steps
+        row["f_triad"] = trg.trg_free_energy()[0]
+        row["f_atrg"] = trg.trg_atrg_free_energy()[0]
+        row["atrg_over_triad"] = row["atrg_ms_per_step"] / row["triad_ms_per_step"]
+        rows.append(row)
+    print(json.dumps({
+        "metric": "ms per RG step, triad-ATRG vs plain ATRG, 4D Ising", "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "dtype": a.precision, "data": "synthetic",
+        "config": {"workload": f"4D Ising beta={a.beta}, h=0, p=2D, q_swap=4, q_rho=4",
+                   "precision": a.precision, "D": [r["D"] for r in rows]},
+        "rows": rows}), flush=True)
+
+
 def reduce_timing(ms, steps, world, dist=None, device="cpu"):
     """Replicas: the slowest rank's timed region counts (max over ranks), and the value is
     the steps all ranks completed in that time."""
@@ -489,5 +538,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.batch > 0:
         run_batch(a)
+    elif a.compare_atrg:
+        run_compare_atrg(a)
     else:
         run_ours(a)

@@ -61,7 +61,7 @@ trg_status trg_init_clock(int d, int q, double beta, double h);
 /* One triad-ATRG coarse-graining step along physical axis `axis` (0..3):
  * re-split T = A s D (eq. ABCD), bond swap by randomized SVD (Appendix A, eqs.
  * bond1/bond2, XY), triad isometries from the canonical-form Grams (eq. HOSVD), triads
- * E..L (eqs. E-L), squeezers from the Gram matrices O, P (Sec. II D), coarse
+ * E..L (eqs. E-L), squeezers from the Gram matrices O, P (Sec. II B), coarse
  * contraction Phi / Psi (eqs. makeMG, makeMH), then T <- T / c_n with
  * c_n = ||T||_F and lnZ bookkeeping sum += ln(c_n) / 2^n.
  * D >= 1: bond dimension kept.  sketch_oversample p >= 0: the overspanned internal
@@ -85,7 +85,7 @@ trg_status trg_magnetisation_impurity(double *m);
  * rounds of the triad / squeezer range finders. */
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision);
 
-/* Internal-line overspanning of the bond swap, the ILO form (Sec. II E; Appendix A with
+/* Internal-line overspanning of the bond swap, the ILO form (Sec. II C; Appendix A with
  * r_bond > 1): from the next trg_step on, the re-split bonds alpha, beta and the swapped
  * bond gamma keep r_bond D singular values instead of D, and the bond-swap sketch has
  * r_bond D + p columns (p = sketch_oversample; p = D gives the appendix's (r_bond + 1) D).
@@ -96,7 +96,7 @@ trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int pr
  * Errors: TRG_ERR_ARG (r_bond outside 1..8). */
 trg_status trg_set_bond_overspan(int r_bond);
 
-/* Two-impurity network (Sec. IV; the internal energy from two impurity tensors).  Called
+/* Two-impurity network (Sec. III D; the internal energy from two impurity tensors).  Called
  * after trg_init_* and before the first trg_step: the impurity (s, resp. cos theta) is
  * placed on both sites of the first step's unit cell, i.e. on nearest neighbours along
  * that step's axis; the first step contracts them into one coarse impurity tensor with
@@ -153,7 +153,7 @@ trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launch
 /* Device scratch of the step engine in bytes: in use now, high-water mark, reserved. */
 trg_status trg_mem_stats(long long *in_use, long long *high_water, long long *reserved);
 
-/* Gu-Wen ratio of the current coarse tensor (Sec. IV, eq. X):
+/* Gu-Wen ratio of the current coarse tensor (Sec. III D, eq. X):
  * X = (Tr A)^2 / Tr(A^2) with A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l], the open leg being the
  * slot of the last physical axis (t) and the other three traced pairwise.  X counts the
  * ground-state degeneracy: -> 1 in the disordered phase, -> 2 in the Z2-ordered phase;

@@ -15,7 +15,7 @@ Method (one coarse-graining step along axis "1", Sec. II and Appendix A):
       Gamma^ATRG = A X sigma Y D                                   (Sec. II B, eq. HOSVD)
   (d) triads E, F, G, H and I, J, K, L                         (Sec. II B, eqs. E-L)
   (e) squeezers M^(mu), N^(mu) from the environments built with the Gram matrices O, P
-                                                       (Sec. II A makeG/makeH text; Sec. II D)
+                                                       (Sec. II A makeG/makeH text; Sec. II B)
   (f) coarse contraction Phi (eq. makeMG) and Psi (eq. makeMH)     (Sec. II B)
 The coarse tensor is kept as T = sum_gamma Phi[i1,k2,k3,k4,gamma] Psi[j1,k2',k3',k4',gamma].
 
@@ -34,11 +34,11 @@ Readings where the paper is silent (each is listed in the design doc):
     backward environments), identity when the pair dimension is <= D.
   * Normalisation c_n = ||T||_F; lnZ/V = sum_n ln(c_n)/2^n + 2^-N ln Tr(T_N).
   * Field h and the one-site impurity (magnetisation) with frozen pure projectors.
-  * Two-impurity network (Sec. IV, internal energy): the observable sits on both sites
+  * Two-impurity network (Sec. III D, internal energy): the observable sits on both sites
     of the first step's unit cell (neighbours along its axis); that step contracts them
     into one coarse impurity with the pure tensor's projectors, which is then carried
     like the one-site impurity.  U = -d <s s'> uses the equivalence of the axes.
-  * ILO form (r_bond > 1, Sec. II E and Appendix A): the re-split bonds and the swapped
+  * ILO form (r_bond > 1, Sec. II C and Appendix A): the re-split bonds and the swapped
     bond keep r_bond D values; the bond-swap sketch has r_bond D + p columns, so that
     p = D gives the (r_bond + 1) D of the appendix's footnote; the triad isometries,
     squeezers and pair legs are as in the plain form.
@@ -191,7 +191,7 @@ class State:
     logsum: float = 0.0             # sum_n ln(c_n) / 2^n
     diag: list = field(default_factory=list)
     imp_pair: bool = False          # the impurity is a nearest-neighbour pair, merged by
-                                    # the next step (two-impurity network, Sec. IV)
+                                    # the next step (two-impurity network, Sec. III D)
 
 
 def _init_from_factor(d: int, beta: float, W: np.ndarray, weight: np.ndarray,
@@ -218,7 +218,7 @@ def init_ising(d: int, beta: float, h: float = 0.0, impurity: str = "site") -> S
     """d-dim Ising: T = sum_a e^{h s_a} prod W[a, .]  (Sec. III, field h added).
     impurity "site": one spin s (magnetisation); "pair": s on both sites of the first
     step's unit cell, i.e. the nearest-neighbour product s_x s_(x+e) along the first
-    step's axis (the two-impurity network of Sec. IV)."""
+    step's axis (the two-impurity network of Sec. III D)."""
     W, spins = ising_factor(beta)
     st = _init_from_factor(d, beta, W, np.exp(h * spins), spins)
     return _set_impurity(st, impurity)
@@ -354,7 +354,7 @@ def gram_root(rho: np.ndarray, chi: int, q_rho: int, key) -> np.ndarray:
 
 def squeezer(rho_f: np.ndarray, rho_b: np.ndarray, D: int, chi: int, q_rho: int,
              key_f, key_b):
-    """Oblique projector M N^T on one pair bond (reading of Sec. II A / Sec. II D).
+    """Oblique projector M N^T on one pair bond (reading of Sec. II A / Sec. II B).
 
     rho_f: Gram of the block whose forward pair is open; rho_b: of the backward pair.
     R1^T R1 ~ rho_f, R2^T R2 ~ rho_b,  R1 R2^T = U S V^T (keep D),
@@ -386,7 +386,7 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, ml
     """One triad-ATRG step on the re-split factors.  Legs (per site):
     A (t=i1(n+1), p2,p3,p4, al)   C = A s  (x=i1(n), q2,q3,q4, be)
     B = Dm s (x=j1(n+1)=i1(n), P2,P3,P4, al)   Dm (w=j1(n), Q2,Q3,Q4, be)
-    Db: width kept on the bond-swap line gamma (r_bond D for the ILO form, Sec. II E and
+    Db: width kept on the bond-swap line gamma (r_bond D for the ILO form, Sec. II C and
     Appendix A; D by default).  The pair legs are still cut to D by the squeezers.
     """
     C = A * s
@@ -589,7 +589,7 @@ def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
     """One coarse-graining step along physical `axis` (in place; returns st).  `mlp`
     (parameters of oracle/sketch_mlp.py) selects the learned sketch of the triad
     isometries.  r_bond > 1 is the internal-line overspanning of the bond swap (ILO,
-    Sec. II E, Appendix A): the re-split bonds alpha, beta and the swapped bond gamma
+    Sec. II C, Appendix A): the re-split bonds alpha, beta and the swapped bond gamma
     keep r_bond D values instead of D; the sketch of the bond swap has r_bond D + p
     columns."""
     if D < 1 or p < 0 or r_bond < 1:
@@ -639,7 +639,7 @@ def magnetisation(st: State) -> float:
 
 def nn_correlation(st: State) -> float:
     """<o_x o_(x+e)> of a run started with impurity "pair": Tr(Phi Psi_imp^T) / Tr(Phi Psi^T)
-    once the first step has merged the two impurities (Sec. IV, two impurity tensors)."""
+    once the first step has merged the two impurities (Sec. III D, two impurity tensors)."""
     if st.imp_pair or st.nsteps < 1:
         raise ValueError("the pair impurity is merged by the first step")
     return trace_T(st.phi, st.psi_imp) / trace_T(st.phi, st.psi)
@@ -667,7 +667,7 @@ def run(model: str, d: int, beta: float, h: float, D: int, p: int, nsteps: int,
 
 
 def gu_wen_ratio(st: State) -> float:
-    """X = (Tr A)^2 / Tr(A^2) with A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l]  (Sec. IV, eq. X;
+    """X = (Tr A)^2 / Tr(A^2) with A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l]  (Sec. III D, eq. X;
     the ratio of Gu and Wen, which counts the ground-state degeneracy: 1 disordered,
     2 in the Z2-ordered phase).  The open leg is the one of the last physical axis; the
     other legs are traced pairwise (forward index = backward index)."""

@@ -37,7 +37,7 @@ struct Ctx {
   Arena arena;
   bool init = false;
   bool have_imp = false;
-  // two-impurity network (Sec. IV): 1 = the impurity stands on both sites of the next
+  // two-impurity network (Sec. III D): 1 = the impurity stands on both sites of the next
   // step's unit cell (merged by that step), 2 = merged nearest-neighbour pair
   int imp_pair = 0;
   bool ising = false;          // the model is Ising (internal energy from the pair)
@@ -49,7 +49,7 @@ struct Ctx {
   double *dscal = nullptr;  // [0] logsum [1] c [2] trace [3] trace2; [8..] dot scratch
   int *dflag = nullptr;
   int q_swap = 4, q_rho = 4, precision = TRG_PREC_FP64;
-  int r_bond = 1;              // ILO: re-split and swapped bonds keep r_bond D (Sec. II E)
+  int r_bond = 1;              // ILO: re-split and swapped bonds keep r_bond D (Sec. II C)
   bool mixed_now = false;      // this step runs its bulk GEMMs on the tensor cores
   int crit_depth = 0;          // > 0 inside decompositions (QR, re-split, squeezer roots)
   bool crit_fp64 = false;      // route GEMMs inside decompositions to FP64
@@ -766,7 +766,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor P2 = view(c.phi, {Nf, r}), S2 = view(c.psi, {Nf, r});
   std::unique_ptr<Crit> crit_resplit(new Crit(c));
   // the bond lines (re-split alpha/beta, swapped gamma) keep Db = r_bond D values; the
-  // ILO form (Sec. II E, Appendix A) has r_bond > 1, the pair legs stay at D
+  // ILO form (Sec. II C, Appendix A) has r_bond > 1, the pair legs stay at D
   const int64_t Db = D * c.r_bond;
   const int64_t k = std::min<int64_t>(Db, r);
   // only A, D and s outlive the re-split (its orthonormal factors are released)
@@ -1262,7 +1262,7 @@ static double magnetisation_ctx(Ctx &c) {
   return h[1] / h[0];
 }
 
-// Gu-Wen ratio X = (Tr A)^2 / Tr(A^2), A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l] (Sec. IV,
+// Gu-Wen ratio X = (Tr A)^2 / Tr(A^2), A_kl = sum T[i1 i2 i3 k, i1 i2 i3 l] (Sec. III D,
 // eq. X): the open leg is the slot of the last physical axis, the others are traced
 // pairwise.  A = Phi' Psi'^T over the three traced legs and the bond (one GEMM).
 static double gu_wen_ctx(Ctx &c) {

@@ -1,4 +1,4 @@
-"""Transition-point search from the Gu-Wen ratio X (Sec. IV, eq. X).
+"""Transition-point search from the Gu-Wen ratio X (Sec. III D, eq. X).
 
 X = (Tr A)^2 / Tr(A^2) of the coarse tensor counts the degenerate ground states: about 2
 in the Z2-ordered phase (large beta), about 1 in the disordered phase.  The search

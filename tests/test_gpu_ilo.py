@@ -1,4 +1,4 @@
-"""ILO form (internal-line overspanning of the bond swap, Sec. II E and Appendix A) on
+"""ILO form (internal-line overspanning of the bond swap, Sec. II C and Appendix A) on
 the GPU against the oracle's ILO form: the re-split and swapped bonds keep r_bond D
 values.  FP64 form, same sketches on both sides.  Tolerances as the plain parity tests:
 ln c_n per step 1e-11, lnZ/V 1e-10 relative, <s> 1e-9.

@@ -1,4 +1,4 @@
-"""Two-impurity network (Sec. IV, internal energy) on the GPU, through the C ABI:
+"""Two-impurity network (Sec. III D, internal energy) on the GPU, through the C ABI:
 exhaustive enumeration on an untruncated lattice, and parity with the oracle's pair
 (FP64 form, same sketches; beta = 0.16, h = 0.05, D = 6, p = 2D, q_swap = 5 has every
 cut, range finders included, separated by a relative gap above 1e-2).  Tolerances: 1e-13 untruncated, 1e-9 absolute against the oracle.

@@ -1,4 +1,4 @@
-"""Transition-point search on the GPU (Gu-Wen ratio X of batched instances, Sec. IV):
+"""Transition-point search on the GPU (Gu-Wen ratio X of batched instances, Sec. III D):
 every evaluated X equals the oracle's X for the same coupling (FP64 form, same
 sketches), and the search keeps the interval where X crosses 1.5."""
 import numpy as np

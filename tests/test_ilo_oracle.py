@@ -1,4 +1,4 @@
-"""Pins of the oracle's ILO form (internal-line overspanning of the bond swap, Sec. II E
+"""Pins of the oracle's ILO form (internal-line overspanning of the bond swap, Sec. II C
 and Appendix A, r_bond > 1): the re-split and the swapped bond keep r_bond D values.
 
 * r_bond = 1 is the plain method, bit for bit.

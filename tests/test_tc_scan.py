@@ -1,4 +1,4 @@
-"""Host logic of the transition-point search (Gu-Wen ratio X, Sec. IV): bracketing and
+"""Host logic of the transition-point search (Gu-Wen ratio X, Sec. III D): bracketing and
 refinement on evaluators with a known crossing, and with the oracle as the evaluator."""
 import math
 

@@ -1,4 +1,4 @@
-"""Pins of the oracle's two-impurity network (Sec. IV: the internal energy from two
+"""Pins of the oracle's two-impurity network (Sec. III D: the internal energy from two
 impurity tensors): the nearest-neighbour product of the observable on the first step's
 unit cell.
 
