@@ -172,8 +172,10 @@ trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
  * dims[0..4] = (d1, d2, d3, d4, r), phi/psi[/psi_imp (may be NULL)] row-major host
  * arrays, axes[0..3] the physical axis of each slot, nsteps taken so far and the
  * log-norm sum so far.  Errors: TRG_ERR_ARG (NULL pointers, a dim < 1, axes not a
- * permutation of 0..3, negative nsteps, beta or logsum not finite; checked before the
- * current state is touched, so a rejected call leaves it as it was), TRG_ERR_OOM. */
+ * permutation of 0..3, negative nsteps, beta or logsum not finite), TRG_ERR_NONFINITE
+ * (a NaN or Inf in phi, psi or psi_imp), TRG_ERR_OOM.  Arguments and buffers are checked
+ * on the host before the current state is touched, so a rejected call leaves it as it
+ * was. */
 trg_status trg_set_state(double beta, const int *dims, const double *phi,
                          const double *psi, const double *psi_imp, const int *axes,
                          int nsteps, double logsum);

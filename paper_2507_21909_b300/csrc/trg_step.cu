@@ -1888,6 +1888,15 @@ trg_status trg_set_state(double beta, const int *dims, const double *phi, const 
     if (seen != 0xF) throw Error(TRG_ERR_ARG, "axes must be a permutation of 0..3");
     if (!std::isfinite(beta) || !(beta >= 0.0) || !std::isfinite(logsum))
       throw Error(TRG_ERR_ARG, "need finite beta >= 0 and finite logsum");
+    int64_t total = 1;
+    for (int i = 0; i < 5; ++i) total *= dims[i];
+    for (const double *buf : {phi, psi, psi_imp}) {
+      if (!buf) continue;
+      for (int64_t i = 0; i < total; ++i)
+        if (!std::isfinite(buf[i]))
+          throw Error(TRG_ERR_NONFINITE, "state buffer holds NaN or Inf at index " +
+                                             std::to_string(i));
+    }
     Ctx &c = ctx();
     ensure_ctx(c);
     TRG_CUDA(cudaStreamSynchronize(c.stream));

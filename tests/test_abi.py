@@ -87,3 +87,20 @@ def test_new_entry_points_reject_without_gpu(lib):
     assert lib.trg_atrg_step(0, 4, 8) == -6                   # no ATRG model yet
     assert lib.trg_set_impurity_pair() == -6                  # no model yet
     assert lib.trg_internal_energy(None) == -1                # NULL output
+
+
+def test_set_state_rejects_nonfinite_buffers_without_gpu(lib):
+    """NaN or Inf in a host state buffer is reported (TRG_ERR_NONFINITE) before upload."""
+    lib.trg_set_state.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double]
+    lib.trg_last_error.restype = ctypes.c_char_p
+    dims = (ctypes.c_int * 5)(2, 2, 2, 2, 2)
+    axes = (ctypes.c_int * 4)(0, 1, 2, 3)
+    good = (ctypes.c_double * 32)(*([1.0] * 32))
+    for bad_value, where in ((float("nan"), 5), (float("inf"), 31), (-float("inf"), 0)):
+        bad = (ctypes.c_double * 32)(*([1.0] * 32))
+        bad[where] = bad_value
+        for args in ((bad, good, None), (good, bad, None), (good, good, bad)):
+            assert lib.trg_set_state(0.2, dims, *args, axes, 0, 0.0) == -4
+            assert f"index {where}".encode() in lib.trg_last_error()
