@@ -176,6 +176,12 @@ trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
  * (a NaN or Inf in phi, psi or psi_imp), TRG_ERR_OOM.  Arguments and buffers are checked
  * on the host before the current state is touched, so a rejected call leaves it as it
  * was. */
+/* beta, the running sum ln Z/V so far without the final trace (sum_n ln c_n / 2^n) and
+ * the step count of the current state: with trg_get_state, everything trg_set_state
+ * needs to resume a run.  Any pointer may be NULL.  Errors: TRG_ERR_NOINIT,
+ * TRG_ERR_CUDA. */
+trg_status trg_get_scalars(double *beta, double *logsum, int *nsteps);
+
 trg_status trg_set_state(double beta, const int *dims, const double *phi,
                          const double *psi, const double *psi_imp, const int *axes,
                          int nsteps, double logsum);

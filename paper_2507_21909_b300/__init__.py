@@ -16,7 +16,8 @@ _NAMES = ("TRG_PREC_BF16X3", "TRG_PREC_BF16X10", "TRG_PREC_OZ4", "TRG_PREC_OZ5",
           "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free",
           "trg_gu_wen_ratio", "trg_batch_gu_wen", "trg_set_bond_overspan",
           "trg_set_impurity_pair", "trg_internal_energy",
-          "trg_atrg_init_ising", "trg_atrg_step", "trg_atrg_free_energy", "trg_atrg_diag")
+          "trg_atrg_init_ising", "trg_atrg_step", "trg_atrg_free_energy", "trg_atrg_diag",
+          "trg_get_scalars", "save_state", "load_state")
 
 
 def __getattr__(name):

@@ -19,7 +19,7 @@ EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_batch_step", "trg_batch_results", "trg_batch_lanes", "trg_batch_free",
             "trg_gu_wen_ratio", "trg_batch_gu_wen", "trg_set_bond_overspan",
             "trg_set_impurity_pair", "trg_internal_energy", "trg_atrg_init_ising",
-            "trg_atrg_step", "trg_atrg_free_energy", "trg_atrg_diag"]
+            "trg_atrg_step", "trg_atrg_free_energy", "trg_atrg_diag", "trg_get_scalars"]
 
 TRG_SKETCH_IN, TRG_SKETCH_PARAMS = 5, 67585
 
@@ -50,7 +50,7 @@ def _load():
         "trg_atrg_step": [i, i, i], "trg_atrg_free_energy": [pd, pd], "trg_atrg_diag": [pd, pd, pi],
         "trg_set_stream": [vp], "trg_diag": [pd, pd, pi],
         "trg_get_state": [i, pi, pi, pd, ctypes.c_longlong],
-        "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_finalize": [],
+        "trg_set_state": [d, pi, pd, pd, pd, pi, i, d], "trg_get_scalars": [pd, pd, pi], "trg_finalize": [],
         "trg_step_timings": [pd, i],
         "trg_mem_stats": [ctypes.POINTER(ctypes.c_longlong)] * 3,
         "trg_gemm_noalloc": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d,
@@ -179,6 +179,38 @@ def trg_state_dims(which=0):
     dims = (ctypes.c_int * 5)()
     _check(lib.trg_get_state(int(which), dims, None, None, 0))
     return tuple(dims)
+
+
+def trg_get_scalars():
+    """(beta, logsum, nsteps) of the current state."""
+    b, ls, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib.trg_get_scalars(ctypes.byref(b), ctypes.byref(ls), ctypes.byref(n)))
+    return b.value, ls.value, n.value
+
+
+def save_state(path):
+    """Write the current coarse-graining state (factors, axis order, beta, ln-norm sum,
+    step count) to an .npz file; load_state resumes from it."""
+    phi, axes = trg_get_state(0)
+    psi, _ = trg_get_state(1)
+    try:
+        psi_imp, _ = trg_get_state(2)
+    except TrgError:
+        psi_imp = None
+    beta, logsum, nsteps = trg_get_scalars()
+    arrays = {"phi": phi, "psi": psi, "axes": np.asarray(axes, dtype=np.int64),
+              "scalars": np.array([beta, logsum, nsteps], dtype=np.float64)}
+    if psi_imp is not None:
+        arrays["psi_imp"] = psi_imp
+    np.savez(path, **arrays)
+
+
+def load_state(path):
+    with np.load(path) as z:
+        beta, logsum, nsteps = z["scalars"]
+        psi_imp = z["psi_imp"] if "psi_imp" in z.files else None
+        trg_set_state(beta, z["phi"], z["psi"], psi_imp, tuple(int(a) for a in z["axes"]),
+                      int(nsteps), logsum)
 
 
 def trg_set_state(beta, phi, psi, psi_imp, axes, nsteps, logsum):

@@ -1875,6 +1875,19 @@ trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
   });
 }
 
+trg_status trg_get_scalars(double *beta, double *logsum, int *nsteps) {
+  return guarded([&] {
+    Ctx &c = ctx();
+    if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
+    double ls = 0.0;
+    TRG_CUDA(cudaMemcpyAsync(&ls, c.dscal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    if (beta) *beta = c.beta;
+    if (logsum) *logsum = ls;
+    if (nsteps) *nsteps = c.nsteps;
+  });
+}
+
 trg_status trg_set_state(double beta, const int *dims, const double *phi, const double *psi,
                          const double *psi_imp, const int *axes, int nsteps, double logsum) {
   return guarded([&] {
