@@ -38,6 +38,9 @@ Readings where the paper is silent (each is listed in the design doc):
     of the first step's unit cell (neighbours along its axis); that step contracts them
     into one coarse impurity with the pure tensor's projectors, which is then carried
     like the one-site impurity.  U = -d <s s'> uses the equivalence of the axes.
+  * Three dimensions (end of Sec. II B gives only the cost, O(r^2 D^6)): the pair (i2, i3)
+    of each of A, X, Y, D is compressed by a triad isometry; two squeezers; the coarse
+    tensor is (E F)(I J M2 M3).  d = 2 uses plain ATRG, which the paper says coincides.
   * ILO form (r_bond > 1, Sec. II C and Appendix A): the re-split bonds and the swapped
     bond keep r_bond D values; the bond-swap sketch has r_bond D + p columns, so that
     p = D gives the (r_bond + 1) D of the appendix's footnote; the triad isometries,
@@ -506,6 +509,72 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, ml
     return phi, psi, psi_imp, diag
 
 
+def _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, Db=None):
+    """The triad step in three dimensions (the d = 3 case the paper discusses at the end
+    of Sec. II B, cost O(r^2 D^6)).  Legs (per site):
+    A (t, p2, p3, al), C = A s (x, q2, q3, be), B = Dm s (x, P2, P3, al), Dm (w, Q2, Q3, be).
+    The pair (i2, i3) of each of A, X, Y, D is compressed by a triad isometry of width
+    chi = D + p (ranges of the canonical-form Grams, as in d = 4); the triads are
+    E (t, kA, al), F (al, kX, g), G (be, kY, g), H (w, kD, be); two squeezers (mu = 2, 3)
+    come from the environments of the upper block E F I J and the lower block G H K L;
+    Phi = (E F)(I J M2 M3), Psi = (H G)(K L N2 N3)."""
+    C = A * s
+    B = Dm * s
+    X, sig, Y, gap_swap = bond_swap(B, C, D if Db is None else Db, p, q_swap, seed, step)
+    d2, d3 = A.shape[1:3]
+    chi_pair = d2 * d3
+    Xs = X * sig
+    Ys = Y * sig
+    W_al = np.einsum("aIJg,bIJg->ab", Xs, Xs)
+    W_be = np.einsum("aIJg,bIJg->ab", Ys, Ys)
+    rho = {"A": np.einsum("tbca,ae,tBCe->bcBC", A, W_al, A, optimize=True),
+           "X": np.einsum("abcg,aBCg->bcBC", Xs, Xs),
+           "Y": np.einsum("abcg,aBCg->bcBC", Ys, Ys),
+           "D": np.einsum("wbca,ae,wBCe->bcBC", Dm, W_be, Dm, optimize=True)}
+    chi = min(D + p, chi_pair)
+    U = {name: rsvd_range_sym(r_.reshape(chi_pair, chi_pair), chi, q_rho,
+                              sketch_key(seed, step, TAG_RHO[name])).reshape(d2, d3, -1)
+         for name, r_ in rho.items()}
+    E = np.einsum("tbca,bck->tka", A, U["A"])
+    F = np.einsum("abcg,bck,g->akg", X, U["X"], sig, optimize=True)
+    G = np.einsum("bPQg,PQk->bkg", Y, U["Y"])
+    H = np.einsum("wPQb,PQk->wkb", Dm, U["D"])
+    I_, J_, K_, L_ = U["A"], U["X"], U["Y"], U["D"]
+    Ig, Jg = np.einsum("bck,bcl->kl", I_, I_), np.einsum("bck,bcl->kl", J_, J_)
+    Kg, Lg = np.einsum("bck,bcl->kl", K_, K_), np.einsum("bck,bcl->kl", L_, L_)
+    # Grams of the two blocks on the bond gamma
+    EEI = np.einsum("tka,tle,kl->ae", E, E, Ig, optimize=True)
+    O = np.einsum("ae,akg,elh,kl->gh", EEI, F, F, Jg, optimize=True)
+    HHL = np.einsum("wkb,wle,kl->be", H, H, Lg, optimize=True)
+    Pm = np.einsum("be,bkg,elh,kl->gh", HHL, G, G, Kg, optimize=True)
+    # pair environments: forward = upper block with P on gamma, backward = lower with O
+    EE2 = np.einsum("tka,tle->kale", E, E)
+    FPF2 = np.einsum("akg,gh,elh->akel", F, Pm, F, optimize=True)
+    GOG2 = np.einsum("bkg,gh,elh->kble", G, O, G, optimize=True)
+    HH2 = np.einsum("wkb,wle->kble", H, H)
+    Msq, Nsq, gaps = {}, {}, {}
+    dims = {2: d2, 3: d3}
+    for mu, sub in ((2, "bck,Bcl->bkBl"), (3, "cbk,cBl->bkBl")):
+        II, JJ = np.einsum(sub, I_, I_), np.einsum(sub, J_, J_)
+        KK, LL = np.einsum(sub, K_, K_), np.einsum(sub, L_, L_)
+        rf = np.einsum("paPe,aqeQ->pqPQ", np.einsum("pkPl,kale->paPe", II, EE2),
+                       np.einsum("qkQl,akel->aqeQ", JJ, FPF2))
+        rb = np.einsum("PbRe,bQeS->PQRS", np.einsum("PkRl,kble->PbRe", KK, GOG2),
+                       np.einsum("QkSl,kble->bQeS", LL, HH2))
+        n = dims[mu] ** 2
+        M, N, gaps[mu] = squeezer(rf.reshape(n, n), rb.reshape(n, n), D, min(D + p, n), q_rho,
+                                  sketch_key(seed, step, TAG_SQ_F[mu]),
+                                  sketch_key(seed, step, TAG_SQ_B[mu]))
+        Msq[mu] = M.reshape(dims[mu], dims[mu], -1)
+        Nsq[mu] = N.reshape(dims[mu], dims[mu], -1)
+    ThU = np.einsum("bck,BCl,bBm,cCn->klmn", I_, J_, Msq[2], Msq[3], optimize=True)
+    ThL = np.einsum("bck,BCl,bBm,cCn->klmn", K_, L_, Nsq[2], Nsq[3], optimize=True)
+    phi = np.einsum("tka,alg,klmn->tmng", E, F, ThU, optimize=True)
+    psi = np.einsum("wlb,bkg,klmn->wmng", H, G, ThL, optimize=True)
+    return (np.ascontiguousarray(phi), np.ascontiguousarray(psi), None,
+            {"gap_swap": gap_swap, "gap_sq": gaps, "sigma": sig, "s": s})
+
+
 def contract_upper(E, F, I_, J_, Msq):
     """Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG)."""
     Theta = np.einsum("bck,BCl,bBm,cCn->klmn", I_, J_, Msq[2], Msq[3], optimize=True)  # (kA kX k2 k3)
@@ -597,9 +666,12 @@ def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
     Db = r_bond * D
     _rotate(st, axis)
     A, Dm, s = resplit(st.phi, st.psi, Db)
-    if method == "triad":
+    if method == "triad" and st.d == 3:
+        phi, psi, psi_imp, diag = _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps,
+                                               Db)
+    elif method == "triad":
         if st.d != 4:
-            raise ValueError("triad-ATRG is defined for d = 4")
+            raise ValueError("triad-ATRG is defined for d = 3 and 4 (d = 2: method 'atrg')")
         imp = (st.phi, st.psi_imp) if st.psi_imp is not None else None
         phi, psi, psi_imp, diag = _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps, imp,
                                               mlp, Db, st.imp_pair)
