@@ -1664,24 +1664,24 @@ static void atrg_step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   // coarse tensors Phi[t, k2..kd, g] = Up . M_2 ... M_d, Psi likewise with N
   auto coarse = [&](const Tensor &blk, std::vector<Tensor> &S) {
     Tensor cur = view(blk.p, ldims);
-    std::string cs_ = full;
+    std::string legs = full;
     for (int mu = 2; mu <= d; ++mu) {
       const char pc = pl[mu - 2], qc = ql[mu - 2], kc = char('K' + (mu - 2));
       std::string out;
-      for (char ch : cs_)
+      for (char ch : legs)
         if (ch != pc && ch != qc) out += ch;
       out += kc;
       const int64_t dm = a.dims[mu - 1];
       Tensor Sv = view(S[mu].p, {dm, dm, S[mu].dims[1]});
-      cur = contract(c, cs_ + "," + std::string{pc, qc, kc} + "->" + out, cur, Sv);
-      cs_ = out;
+      cur = contract(c, legs + "," + std::string{pc, qc, kc} + "->" + out, cur, Sv);
+      legs = out;
     }
-    // cs_ = t g K L M ... -> t K L M ... g
+    // legs = t g K L M ... -> t K L M ... g
     std::string want = "t";
     for (int mu = 2; mu <= d; ++mu) want += char('K' + (mu - 2));
     want += "g";
     std::vector<int> perm;
-    for (char ch : want) perm.push_back((int)cs_.find(ch));
+    for (char ch : want) perm.push_back((int)legs.find(ch));
     return permuted(c, cur, perm);
   };
   Tensor PhiN = coarse(Up, Msq);
