@@ -52,3 +52,22 @@ def test_reference_arm_prints_on_rank0_only():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """Rank 0's reference line: the keys the driver reads, the oracle as cpu_baseline,
+    e2e with zero host-device bytes, and the ILO width in the config when asked for."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    for extra, want_rb in (([], None), (["--r-bond", "2"], 2)):
+        r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                            "--warmup", "0", "--D", "6"] + extra,
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        line = json.loads(r.stdout.strip().splitlines()[-1])
+        for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup",
+                  "ms_per_step", "higher_is_better", "config", "cpu_baseline", "e2e"):
+            assert k in line, k
+        assert line["impl"] == "reference" and line["value"] > 0
+        assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+        assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+        assert line["config"].get("r_bond") == want_rb
