@@ -50,12 +50,14 @@ typedef int trg_status;
  * [sqrt(cosh b), -sqrt(sinh b)]]) with an added site field e^{h s}.
  * d: must be 4 (the triad step is four-dimensional).  beta >= 0.  The impurity
  * factor (one site carrying s) is created as well.  Resets the log-norm sum to
- * ln c_0, c_0 = ||T_0||_F, and the step counter to 0.  Errors: TRG_ERR_ARG. */
+ * ln c_0, c_0 = ||T_0||_F, and the step counter to 0.  Errors: TRG_ERR_ARG (d != 4,
+ * beta < 0 or not finite, h not finite), TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_init_ising(int d, double beta, double h);
 
 /* Z_q clock model (extension, not in the paper): bond weight e^{beta cos(th-th')},
  * th = 2 pi k / q, factorised in the real Fourier basis; site weight e^{h cos th};
- * impurity observable cos th.  d = 4, q in [2, 8], beta >= 0. */
+ * impurity observable cos th.  d = 4, q in [2, 8], beta >= 0.  Errors: TRG_ERR_ARG,
+ * TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_init_clock(int d, int q, double beta, double h);
 
 /* One triad-ATRG coarse-graining step along physical axis `axis` (0..3):
@@ -77,12 +79,18 @@ trg_status trg_free_energy(double *f_per_site, double *lnZ_per_site);
 
 /* One-site impurity expectation <s> (Ising) or <cos th> (clock):
  * Tr(Phi Psi_imp^T) / Tr(Phi Psi^T).  The impurity is coarse-grained with the pure
- * tensor's frozen projectors, averaged over its two slots in each step. */
+ * tensor's frozen projectors, averaged over its two slots in each step (the impurity
+ * tensors of Sec. III D, one site).  After trg_set_impurity_pair and a step it returns
+ * the pair's <o_x o_(x+e)>.  Errors: TRG_ERR_NOINIT (no model or no impurity factor),
+ * TRG_ERR_ARG (m NULL), TRG_ERR_CUDA. */
 trg_status trg_magnetisation_impurity(double *m);
 
 /* Parameters of the randomized SVDs and the precision mode (defaults: 4, 4, 0x5EED,
- * TRG_PREC_FP64).  q_swap >= 1 rounds of the bond-swap loop; q_rho >= 0 extra power
- * rounds of the triad / squeezer range finders. */
+ * TRG_PREC_FP64).  q_swap >= 1 rounds of the bond-swap loop (q of eqs. bond1/bond2,
+ * Appendix A); q_rho >= 0 extra power rounds of the triad / squeezer range finders;
+ * seed of the counter-based Gaussian sketches; precision TRG_PREC_* (an extension: the
+ * paper runs FP64).  Take effect from the next trg_step or trg_atrg_step.
+ * Errors: TRG_ERR_ARG (q_swap < 1, q_rho < 0, precision outside 0..6). */
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision);
 
 /* Internal-line overspanning of the bond swap, the ILO form (Sec. II C; Appendix A with
@@ -104,6 +112,14 @@ trg_status trg_set_bond_overspan(int r_bond);
  * trg_magnetisation_impurity then returns <o_x o_(x+e)>.  A new trg_init_* or
  * trg_set_state returns to the one-site impurity.
  * Errors: TRG_ERR_NOINIT (no model), TRG_ERR_ARG (a step was already taken). */
+trg_status trg_set_impurity_pair(void);
+
+/* Ising coupling energy per site (Sec. III D) U = -(1/V) d lnZ/d beta = -4 <s_x s_(x+e)>, from the
+ * merged pair of trg_set_impurity_pair (the pair's axis stands for every axis; the
+ * field term -h <s> is not included).  Errors: TRG_ERR_ARG (u NULL, not the Ising
+ * model), TRG_ERR_NOINIT (no merged pair: trg_set_impurity_pair and one step first). */
+trg_status trg_internal_energy(double *u);
+
 /* Plain ATRG (eqs. makeG / makeH), the paper's comparison method, for the Ising model
  * in d = 2, 3 or 4 dimensions, with its own state (independent of trg_init_* /
  * trg_step).  Same re-split, Gaussian sketches (trg_set_params: q_swap, q_rho, seed,
@@ -114,43 +130,48 @@ trg_status trg_set_bond_overspan(int r_bond);
  * trg_atrg_init_ising: T0 of Sec. III in d dimensions with field h.  Errors:
  * TRG_ERR_ARG (d outside 2..4, beta < 0 or not finite), TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_atrg_init_ising(int d, double beta, double h);
-/* One step along physical axis 0 <= axis < d, bond dimension D, sketch oversampling p.
+/* One plain-ATRG step (eqs. makeG / makeH) along physical axis 0 <= axis < d, bond
+ * dimension D, sketch oversampling p (bond-swap sketch width D + p, squeezer ranges
+ * min(D + p, pair dimension)).  On an error the ATRG state keeps its factors.
  * Errors: TRG_ERR_NOINIT, TRG_ERR_ARG, TRG_ERR_OOM, TRG_ERR_CUDA, TRG_ERR_NONFINITE. */
 trg_status trg_atrg_step(int axis, int D, int sketch_oversample);
-/* f and lnZ/V of the ATRG state, as trg_free_energy.  Errors: TRG_ERR_NOINIT. */
+/* f and lnZ/V of the ATRG state, as trg_free_energy (Sec. III A).  Either pointer may be
+ * NULL.  Errors: TRG_ERR_NOINIT, TRG_ERR_CUDA. */
 trg_status trg_atrg_free_energy(double *f_per_site, double *lnZ_per_site);
-/* ln c_n of the last ATRG step, the smallest relative gap at its cuts, steps taken. */
+/* Diagnostics of the ATRG state (not in the paper): ln c_n of the last step, the
+ * smallest relative gap at its bond-swap and squeezer cuts, steps taken.  Any pointer
+ * may be NULL.  Reads host-side values only; always TRG_OK. */
 trg_status trg_atrg_diag(double *log_c, double *min_gap, int *nsteps);
 
-trg_status trg_set_impurity_pair(void);
-
-/* Ising coupling energy per site U = -(1/V) d lnZ/d beta = -4 <s_x s_(x+e)>, from the
- * merged pair of trg_set_impurity_pair (the pair's axis stands for every axis; the
- * field term -h <s> is not included).  Errors: TRG_ERR_ARG (u NULL, not the Ising
- * model), TRG_ERR_NOINIT (no merged pair: trg_set_impurity_pair and one step first). */
-trg_status trg_internal_energy(double *u);
-
-/* Run all device work on this cudaStream_t (NULL = the library's own stream). */
+/* Run all device work on this cudaStream_t (NULL = the library's own stream); the
+ * previous stream is synchronised first.  A service of the library (no counterpart in
+ * the paper).  Errors: TRG_ERR_CUDA. */
 trg_status trg_set_stream(void *cuda_stream);
 
-/* Diagnostics of the last step: ln c_n, the smallest relative singular-value gap at
- * the bond-swap and squeezer truncations, and the number of steps taken. */
+
+/* Diagnostics of the last step (not in the paper): ln c_n, the smallest relative
+ * singular-value gap at the bond-swap and squeezer truncations (a gap near 0 marks a
+ * near-degenerate cut, where two implementations may keep different subspaces), and the
+ * number of steps taken.  Any pointer may be NULL; always TRG_OK. */
 trg_status trg_diag(double *log_c, double *min_gap, int *nsteps);
 
 /* Device time (ms, CUDA events on the library stream) of the phases of the last step:
  * [0] leg rotation + re-split, [1] bond swap, [2] triad isometries, [3] triads, Grams O, P
  * and environments, [4] squeezers, [5] coarse contraction Phi, Psi, [6] impurity,
- * [7] normalisation and state update.  Writes min(n, 8) values. */
+ * [7] normalisation and state update.  Writes min(n, 8) values.  Measurement service
+ * (not in the paper).  Errors: TRG_ERR_ARG (ms NULL or n < 0), TRG_ERR_CUDA. */
 trg_status trg_step_timings(double *ms, int n);
 
 /* Counters since the last reset: device time (ms, CUDA events on the launching stream)
  * and tensor-pipe flop of the split-BF16 tcgen05 GEMM kernel launches inside trg_step
  * (each slice product counted as a full BF16 GEMM), their number, and the number of all
- * kernel launches of the library.  reset != 0 zeroes them after reading. */
+ * kernel launches of the library.  reset != 0 zeroes them after reading.  Measurement
+ * service (not in the paper); any pointer may be NULL; always TRG_OK. */
 trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launches,
                             long long *all_launches, int reset);
 
-/* Device scratch of the step engine in bytes: in use now, high-water mark, reserved. */
+/* Device scratch of the step engine in bytes: in use now, high-water mark, reserved.
+ * Any pointer may be NULL; always TRG_OK. */
 trg_status trg_mem_stats(long long *in_use, long long *high_water, long long *reserved);
 
 /* Gu-Wen ratio of the current coarse tensor (Sec. III D, eq. X):
@@ -168,6 +189,12 @@ trg_status trg_gu_wen_ratio(double *X);
 trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
                          long long capacity);
 
+/* beta, the running sum ln Z/V so far without the final trace (sum_n ln c_n / 2^n) and
+ * the step count of the current state: with trg_get_state, everything trg_set_state
+ * needs to resume a run.  Any pointer may be NULL.  Errors: TRG_ERR_NOINIT,
+ * TRG_ERR_CUDA. */
+trg_status trg_get_scalars(double *beta, double *logsum, int *nsteps);
+
 /* Load a state (e.g. an oracle state at step n, for per-step parity):
  * dims[0..4] = (d1, d2, d3, d4, r), phi/psi[/psi_imp (may be NULL)] row-major host
  * arrays, axes[0..3] the physical axis of each slot, nsteps taken so far and the
@@ -176,12 +203,6 @@ trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
  * (a NaN or Inf in phi, psi or psi_imp), TRG_ERR_OOM.  Arguments and buffers are checked
  * on the host before the current state is touched, so a rejected call leaves it as it
  * was. */
-/* beta, the running sum ln Z/V so far without the final trace (sum_n ln c_n / 2^n) and
- * the step count of the current state: with trg_get_state, everything trg_set_state
- * needs to resume a run.  Any pointer may be NULL.  Errors: TRG_ERR_NOINIT,
- * TRG_ERR_CUDA. */
-trg_status trg_get_scalars(double *beta, double *logsum, int *nsteps);
-
 trg_status trg_set_state(double beta, const int *dims, const double *phi,
                          const double *psi, const double *psi_imp, const int *axes,
                          int nsteps, double logsum);
@@ -248,17 +269,21 @@ trg_status trg_batch_create(int n, const int *model, const double *beta, const d
 trg_status trg_batch_step(int nsteps, double *wall_ms);
 
 /* Per instance (host arrays of length n, any may be NULL): f per site, ln Z/V, the
- * one-site impurity observable (Ising: <s>, clock: <cos theta>), steps taken. */
+ * one-site impurity observable (Ising: <s>, clock: <cos theta>), steps taken, as
+ * trg_free_energy / trg_magnetisation_impurity per instance.  Errors: TRG_ERR_NOINIT (no
+ * batch), TRG_ERR_CUDA. */
 trg_status trg_batch_results(double *f, double *lnz, double *m, int *nsteps);
 
 /* lane_of[i] (length n) and the scratch bytes each lane has reserved (length lanes);
- * either may be NULL. */
+ * either may be NULL.  Errors: TRG_ERR_NOINIT (no batch). */
 trg_status trg_batch_lanes(int *lane_of, long long *scratch_bytes);
 
-/* Release every instance and lane. */
+/* Release every instance and lane (no batch: nothing to do).  Always TRG_OK. */
 trg_status trg_batch_free(void);
 
-/* Gu-Wen ratio of every instance (host array of length n); see trg_gu_wen_ratio. */
+/* Gu-Wen ratio of every instance (host array of length n); see trg_gu_wen_ratio
+ * (Sec. III D, eq. X).  Errors: TRG_ERR_NOINIT (no batch), TRG_ERR_ARG (X NULL),
+ * TRG_ERR_CUDA. */
 trg_status trg_batch_gu_wen(double *X);
 
 /* ---------------------------------------------------------------------------------
@@ -284,47 +309,56 @@ trg_status trg_batch_gu_wen(double *X);
  * the Adam moments.  Errors: TRG_ERR_ARG (wrong n or NULL), TRG_ERR_CUDA. */
 trg_status trg_sketch_set_net(const float *params, long long n);
 
-/* Copy the current network to the host (n = TRG_SKETCH_PARAMS).  TRG_ERR_NOINIT if none
- * was loaded. */
+/* Copy the current network to the host (n = TRG_SKETCH_PARAMS).  Errors: TRG_ERR_ARG
+ * (wrong n or NULL), TRG_ERR_NOINIT (none loaded), TRG_ERR_CUDA. */
 trg_status trg_sketch_get_net(float *params, long long n);
 
 /* u[r] for rows x TRG_SKETCH_IN host inputs X (row-major); bf16 != 0: the inference
  * kernel used inside trg_step (BF16 inputs, weights and activations, FP32 sums),
- * bf16 == 0: the FP32 training forward pass.  Host buffers; synchronous. */
+ * bf16 == 0: the FP32 training forward pass.  Host buffers; synchronous.  Errors:
+ * TRG_ERR_ARG (NULL buffers, rows < 1), TRG_ERR_NOINIT (no network), TRG_ERR_CUDA. */
 trg_status trg_sketch_forward(const float *X, long long rows, float *u, int bf16);
 
 /* Loss L = mean (u - t)^2 of the FP32 network over rows (X rows x 5, t rows; host) and
- * its gradient (host, TRG_SKETCH_PARAMS floats, parameter order as above). */
+ * its gradient (host, TRG_SKETCH_PARAMS floats, parameter order as above).  Errors:
+ * TRG_ERR_ARG (NULL buffers, rows < 1), TRG_ERR_NOINIT (no network), TRG_ERR_CUDA. */
 trg_status trg_sketch_grad(const float *X, const float *t, long long rows, double *loss,
                            float *grad);
 
 /* Adam (beta 0.9, 0.999, eps 1e-8, rate lr) over `epochs` passes of shuffled minibatches
  * of `batch` rows (host std::mt19937_64(seed) permutation; a ragged last batch is
- * skipped); *loss = mean loss of the last epoch.  The network must be loaded. */
+ * skipped); *loss = mean loss of the last epoch.  The network must be loaded.
+ * Errors: TRG_ERR_ARG (NULL buffers, rows, epochs or batch < 1), TRG_ERR_NOINIT,
+ * TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_sketch_train(const float *X, const float *t, long long rows, int epochs,
                             int batch, float lr, unsigned long long seed, double *loss);
 
 /* 0: Gaussian sketches (the paper's form, default); 1: learned sketch with the plain
- * range as fallback.  TRG_ERR_NOINIT for 1 without a loaded network. */
+ * range as fallback.  Errors: TRG_ERR_ARG (other modes), TRG_ERR_NOINIT (1 without a
+ * loaded network). */
 trg_status trg_set_sketch_mode(int mode);
 
 /* Collect training rows during trg_step: every triad range finder (with chi < n) appends
  * d_a + d_b rows (inputs, target) computed from its plain range, up to `capacity` rows
  * (later rows are counted as dropped).  capacity 0 stops collecting and frees the
- * buffer; a new call discards earlier rows. */
+ * buffer; a new call discards earlier rows.  Errors: TRG_ERR_ARG (capacity < 0),
+ * TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_sketch_collect(long long capacity);
 
 /* Copy the collected rows to the host: X (capacity x 5 floats), t (capacity floats);
  * either may be NULL (then only *rows / *dropped are written).  TRG_ERR_ARG if
- * capacity < the number of collected rows. */
+ * capacity < the number of collected rows; TRG_ERR_CUDA. */
 trg_status trg_sketch_fetch(float *X, float *t, long long capacity, long long *rows,
                             long long *dropped);
 
 /* Range finders that kept the learned range / fell back to the plain one since the last
- * reset (reset != 0 zeroes the counters after reading). */
+ * reset (reset != 0 zeroes the counters after reading).  Either pointer may be NULL.
+ * Errors: TRG_ERR_CUDA. */
 trg_status trg_sketch_stats(long long *learned, long long *fallback, int reset);
 
-/* Release every device buffer of the context. */
+/* Release every device buffer of the library: the single-instance and ATRG states, the
+ * batch, the sketch network and collection buffers, the scratch arena.  Always TRG_OK
+ * (release errors are ignored). */
 trg_status trg_finalize(void);
 
 /* Message of the last error (static storage, never NULL). */

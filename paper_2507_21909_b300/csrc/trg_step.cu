@@ -2196,6 +2196,7 @@ trg_status trg_sketch_forward(const float *X, long long rows, float *u, int bf16
   return guarded([&] {
     if (!X || !u || rows < 1) throw Error(TRG_ERR_ARG, "sketch forward: bad arguments");
     Ctx &c = ctx();
+    if (!c.net.loaded) throw Error(TRG_ERR_NOINIT, "no sketch network loaded");
     ensure_ctx(c);
     DevF dX(X, rows * kMlpIn, c.stream), du(nullptr, rows, c.stream);
     mlp_forward(c.net, dX.p, rows, du.p, bf16 != 0, c.stream);
@@ -2209,6 +2210,7 @@ trg_status trg_sketch_grad(const float *X, const float *t, long long rows, doubl
   return guarded([&] {
     if (!X || !t || !grad || rows < 1) throw Error(TRG_ERR_ARG, "sketch grad: bad arguments");
     Ctx &c = ctx();
+    if (!c.net.loaded) throw Error(TRG_ERR_NOINIT, "no sketch network loaded");
     ensure_ctx(c);
     DevF dX(X, rows * kMlpIn, c.stream), dt(t, rows, c.stream), dg(nullptr, kMlpParams, c.stream);
     const double L = mlp_grad(c.net, dX.p, dt.p, rows, dg.p, c.stream);
@@ -2225,6 +2227,7 @@ trg_status trg_sketch_train(const float *X, const float *t, long long rows, int 
     if (!X || !t || rows < 1 || epochs < 1 || batch < 1 || !(lr > 0.f))
       throw Error(TRG_ERR_ARG, "sketch train: bad arguments");
     Ctx &c = ctx();
+    if (!c.net.loaded) throw Error(TRG_ERR_NOINIT, "no sketch network loaded");
     ensure_ctx(c);
     DevF dX(X, rows * kMlpIn, c.stream), dt(t, rows, c.stream);
     const double L = mlp_train(c.net, dX.p, dt.p, rows, epochs, batch, lr, seed, c.stream);

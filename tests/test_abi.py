@@ -104,3 +104,22 @@ def test_set_state_rejects_nonfinite_buffers_without_gpu(lib):
         for args in ((bad, good, None), (good, bad, None), (good, good, bad)):
             assert lib.trg_set_state(0.2, dims, *args, axes, 0, 0.0) == -4
             assert f"index {where}".encode() in lib.trg_last_error()
+
+
+def test_sketch_calls_without_network_without_gpu(lib):
+    """The learned-sketch calls report a missing network before any device work."""
+    x = (ctypes.c_float * 5)()
+    u = (ctypes.c_float * 1)()
+    lib.trg_sketch_forward.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                       ctypes.c_int]
+    lib.trg_sketch_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    lib.trg_sketch_train.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_ulonglong, ctypes.c_void_p]
+    assert lib.trg_sketch_forward(x, 1, u, 1) == -6
+    g = (ctypes.c_float * 67585)()
+    assert lib.trg_sketch_grad(x, u, 1, None, g) == -6
+    assert lib.trg_sketch_train(x, u, 1, 1, 1, ctypes.c_float(1e-3), 0, None) == -6
+    assert lib.trg_sketch_forward(None, 1, u, 1) == -1
+    assert lib.trg_set_sketch_mode(1) == -6
