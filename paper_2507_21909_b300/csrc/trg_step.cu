@@ -1,10 +1,13 @@
 // Step orchestration of libtrg and the C ABI (include/trg.h).
 //
 // One triad-ATRG coarse-graining step (arXiv 2507.21909, Sec. II B and Appendix A) as a
-// sequence of device kernels on one stream.  Every tensor contraction is planned as
-// (permute) + batched GEMM; the small dense decompositions run in the kernels of
-// linalg_small.cu.  Shapes are structural (fixed by D, p and the step history), so the
-// host never waits on device data inside a step except for the final status read.
+// sequence of device kernels on one stream, with its ILO width (Sec. II C), the one-site
+// and pair impurities (Sec. III D), the batched lanes of a coupling sweep, and the plain
+// ATRG step of the paper's comparison (eqs. makeG / makeH).  Every tensor contraction is
+// planned as (permute) + batched GEMM; the small dense decompositions run in the kernels
+// of linalg_small.cu.  Shapes are structural (fixed by D, p and the step history), so
+// the host reads back only small diagnostics inside a step (the singular values at the
+// cuts, for the gap report) and the final norm and status.
 #include <algorithm>
 #include <thread>
 #include <chrono>
