@@ -509,7 +509,8 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, ml
     return phi, psi, psi_imp, diag
 
 
-def _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, Db=None):
+def _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, Db=None, psi_imp_pair=None,
+                 imp_two=False):
     """The triad step in three dimensions (the d = 3 case the paper discusses at the end
     of Sec. II B, cost O(r^2 D^6)).  Legs (per site):
     A (t, p2, p3, al), C = A s (x, q2, q3, be), B = Dm s (x, P2, P3, al), Dm (w, Q2, Q3, be).
@@ -570,8 +571,29 @@ def _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, Db=None):
     ThU = np.einsum("bck,BCl,bBm,cCn->klmn", I_, J_, Msq[2], Msq[3], optimize=True)
     ThL = np.einsum("bck,BCl,bBm,cCn->klmn", K_, L_, Nsq[2], Nsq[3], optimize=True)
     phi = np.einsum("tka,alg,klmn->tmng", E, F, ThU, optimize=True)
-    psi = np.einsum("wlb,bkg,klmn->wmng", H, G, ThL, optimize=True)
-    return (np.ascontiguousarray(phi), np.ascontiguousarray(psi), None,
+
+    def lower(G_, H_):
+        return np.ascontiguousarray(np.einsum("wlb,bkg,klmn->wmng", H_, G_, ThL, optimize=True))
+
+    psi = lower(G, H)
+    psi_imp = None
+    if psi_imp_pair is not None:
+        # impurity with the pure tensor's frozen projectors, as in the 4D step
+        phi_old, psi_imp_old = psi_imp_pair
+        r = phi_old.shape[-1]
+        PA = phi_old.reshape(-1, r).T @ A.reshape(-1, A.shape[-1])
+        B_imp = (psi_imp_old.reshape(-1, r) @ PA).reshape(B.shape)
+        CX = np.tensordot(C, X, axes=([1, 2], [1, 2]))                 # (x be al g)
+        Ytil = np.einsum("xPQa,xbag->bPQg", B_imp, CX)
+        sinv = np.zeros_like(sig)
+        sinv[sig > 0] = 1.0 / sig[sig > 0]
+        G_imp = np.einsum("bPQg,PQk->bkg", Ytil * sinv, U["Y"])
+        sp = np.zeros_like(s)
+        sp[s > 0] = 1.0 / s[s > 0]
+        H_imp = np.einsum("wPQb,PQk->wkb", B_imp * sp, U["D"])
+        psi_imp = (lower(G_imp, H_imp) if imp_two
+                   else 0.5 * (lower(G_imp, H) + lower(G, H_imp)))
+    return (np.ascontiguousarray(phi), psi, psi_imp,
             {"gap_swap": gap_swap, "gap_sq": gaps, "sigma": sig, "s": s})
 
 
@@ -667,8 +689,9 @@ def step(st: State, axis: int, D: int, p: int, q_swap: int = 4, q_rho: int = 4,
     _rotate(st, axis)
     A, Dm, s = resplit(st.phi, st.psi, Db)
     if method == "triad" and st.d == 3:
+        imp = (st.phi, st.psi_imp) if st.psi_imp is not None else None
         phi, psi, psi_imp, diag = _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, st.nsteps,
-                                               Db)
+                                               Db, imp, st.imp_pair)
     elif method == "triad":
         if st.d != 4:
             raise ValueError("triad-ATRG is defined for d = 3 and 4 (d = 2: method 'atrg')")
