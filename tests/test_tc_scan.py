@@ -65,3 +65,40 @@ def test_oracle_evaluator_brackets_the_4d_ising_transition():
     assert x_lo < 1.5 <= x_hi
     assert lo <= res["beta_c"] <= hi
     assert abs(res["beta_c"] - 0.1497) < 0.1 * 0.1497, res["beta_c"]
+
+
+def test_tc_scan_drives_the_batch_calls(monkeypatch):
+    """tc_scan creates one instance per coupling, steps them, reads X and always frees
+    the batch (stand-ins for the library calls)."""
+    from paper_2507_21909_b300 import _lib as L
+    from paper_2507_21909_b300.tc_scan import tc_scan
+    calls = []
+
+    def create(model, beta, h, D, lanes=4, precision=0, **kw):
+        calls.append(("create", list(model), list(beta), list(h), list(D), lanes, precision))
+        calls[-1] = calls[-1] + (len(beta),)
+        create.n = len(beta)
+        create.betas = np.asarray(beta)
+        return len(beta)
+
+    monkeypatch.setattr(L, "trg_batch_create", create)
+    monkeypatch.setattr(L, "trg_batch_step", lambda k: calls.append(("step", k)))
+    monkeypatch.setattr(L, "trg_batch_gu_wen",
+                        lambda n: 1.0 + (create.betas > 0.1497).astype(float))
+    monkeypatch.setattr(L, "trg_batch_free", lambda: calls.append(("free",)))
+    res = tc_scan(0.14, 0.16, D=8, nsteps=20, points=5, rounds=2, lanes=3, precision=5)
+    creates = [c for c in calls if c[0] == "create"]
+    assert len(creates) == 2 and all(c[-1] == 5 for c in creates)
+    assert creates[0][1] == [0] * 5 and creates[0][4] == [8] * 5 and creates[0][6] == 5
+    assert [c for c in calls if c[0] == "step"] == [("step", 20)] * 2
+    assert calls.count(("free",)) == 2
+    lo, hi = res["interval"]
+    assert lo <= 0.1497 <= hi and res["T_c"] == pytest.approx(1 / res["beta_c"])
+
+    def failing_step(k):
+        raise L.TrgError(-3, "device error")
+    monkeypatch.setattr(L, "trg_batch_step", failing_step)
+    calls.clear()
+    with pytest.raises(L.TrgError):
+        tc_scan(0.14, 0.16, D=8, nsteps=20, points=3, rounds=1)
+    assert calls.count(("free",)) == 1
