@@ -9,7 +9,7 @@ draw G and rescales its rows by per-leg weights proposed by a small network:
 
 with u_l[i] the network output for index i of leg l of the pair and q(u) = round(16 u)/16
 clamped to [-8, 8] (a quantised code, so that the GPU and this oracle take the same
-integer decision).  w = 1 is the paper's plain sketch.  Readings (listed in the design doc):
+integer decision).  w = 1 is the paper's plain sketch.  Readings:
 
   * Inputs per leg index i (NIN = 5): (i + 0.5)/d_l, log2(m_i d_l)/8 with m_i the share
     of tr(rho) on the diagonal entries of index i (m_i d_l clipped at 2^-40, above the

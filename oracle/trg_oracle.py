@@ -19,7 +19,7 @@ Method (one coarse-graining step along axis "1", Sec. II and Appendix A):
   (f) coarse contraction Phi (eq. makeMG) and Psi (eq. makeMH)     (Sec. II B)
 The coarse tensor is kept as T = sum_gamma Phi[i1,k2,k3,k4,gamma] Psi[j1,k2',k3',k4',gamma].
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
   * r = eta and the overspanned lines have width chi = min(D + p, natural dim)  (Sec. II B
     footnote on r); the triad isometries keep all chi columns of their range finder.
   * Sketches are Gaussian, drawn from a counter-based SplitMix64 / Box-Muller generator
