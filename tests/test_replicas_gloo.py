@@ -55,7 +55,7 @@ def test_reference_arm_prints_on_rank0_only():
 
 
 def test_reference_arm_line_keeps_the_contract():
-    """Rank 0's reference line: the keys the driver reads, the oracle as cpu_baseline,
+    """Rank 0's reference line: the keys of the benchmark line, the oracle as cpu_baseline,
     e2e with zero host-device bytes, and the ILO width in the config when asked for."""
     env = dict(os.environ, RANK="0", WORLD_SIZE="1")
     for extra, want_rb in (([], None), (["--r-bond", "2"], 2)):
