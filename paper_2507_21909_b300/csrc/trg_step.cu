@@ -1567,7 +1567,10 @@ static void atrg_step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   const int64_t x = a.dims[0], r = a.dims[d];
   const int64_t I = prod(a.dims, 1, d), Nf = x * I;
 
-  // (a) re-split T = Phi Psi^T = A s D^T
+  // (a) re-split T = Phi Psi^T = A s D^T.  c.phase labels each part with the triad
+  // step's phase numbers, so the precision policy's phase mask applies alike (no
+  // timing events are recorded for these steps)
+  c.phase = 0;
   const int64_t k = std::min<int64_t>(D, std::min<int64_t>(r, Nf));
   Tensor A = c.alloc({Nf, k}), Dm = c.alloc({Nf, k}), sv = c.alloc({std::max<int64_t>(r, 1)});
   {
@@ -1585,6 +1588,7 @@ static void atrg_step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   kill_dead(sv.p, k, kRankTol, A.p, Nf, Dm.p, Nf, s);
 
   // (b) bond swap on the explicit M[(al I), (J be)] (Appendix A, q_swap rounds)
+  c.phase = 1;
   const int64_t w = std::min<int64_t>(D + p, k * I), Dg = std::min<int64_t>(D, w);
   Tensor C = copy(c, A), B = copy(c, Dm);                    // C = A s, B = D s
   scale_last(c, C, sv.p);
@@ -1630,6 +1634,7 @@ static void atrg_step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor Y = permuted(c, view(Yc.p, {I, k, Dg}), {1, 0, 2});  // [be, J, g]
   scale_last(c, X, sig.p);                                   // X sigma
 
+  c.phase = 3;
   // blocks Up[t, P, Q, g] = sum_al A[t P al] (X sigma)[al Q g],
   //        Lo[w, P, Q, g] = sum_be Y[be P g] D[w Q be]   (P, Q: the d-1 legs of each site)
   Tensor Up = contract(c, "tPa,aQg->tPQg", view(A.p, {x, I, k}), view(X.p, {k, I, Dg}));
@@ -1654,9 +1659,11 @@ static void atrg_step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     for (auto &ch : sa) ch = ch == pc ? 'P' : ch == qc ? 'Q' : ch;
     for (auto &ch : sb) ch = ch == pc ? 'R' : ch == qc ? 'S' : ch;
     const int64_t dm = a.dims[mu - 1], nn = dm * dm;
+    c.phase = 3;
     Tensor rf = contract(c, sa + "," + sb + "->PQRS", view(UpP.p, ldims), view(Up.p, ldims));
     Tensor rb = contract(c, sa + "," + sb + "->PQRS", view(LoO.p, ldims), view(Lo.p, ldims));
     double g = INFINITY;
+    c.phase = 4;
     auto [Mq, Nq] = squeezer(c, view(rf.p, {nn, nn}), view(rb.p, {nn, nn}), D,
                              std::min<int64_t>(D + p, nn), c.q_rho, key(TAG_SQ_F2 + mu - 2),
                              key(TAG_SQ_B2 + mu - 2), &g);
@@ -1687,6 +1694,7 @@ static void atrg_step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     for (char ch : want) perm.push_back((int)legs.find(ch));
     return permuted(c, cur, perm);
   };
+  c.phase = 5;
   Tensor PhiN = coarse(Up, Msq);
   Tensor PsiN = coarse(Lo, Nsq);
 
