@@ -384,6 +384,35 @@ def squeezer(rho_f: np.ndarray, rho_b: np.ndarray, D: int, chi: int, q_rho: int,
 # ----------------------------------------------------------------------------------
 # (c)-(f): the triad step in four dimensions
 # ----------------------------------------------------------------------------------
+def triad_grams(A, Dm, X, sig, Y) -> dict:
+    """The four Grams of eq. HOSVD (Sec. II B) on the leg pair (i2, i3) of each factor of
+    Gamma^ATRG = A X sigma Y D, reduced with the canonical form (d = 3 or 4).
+
+    Legs: A (t, p2, p3, [p4,] al), X (al, q2, q3, [q4,] g), Y (be, P2, P3, [P4,] g),
+    Dm (w, Q2, Q3, [Q4,] be).  A is isometric from (t, p..) to al, X from (al, q..) to g,
+    Y from (be, P..) to g and Dm from (w, Q..) to be (columns orthonormal or zero, zero
+    columns only where sigma or s vanishes), so tracing Gamma Gamma^T over every leg but
+    one pair leaves
+        rho^A = A W_al A^T,  W_al[a, a'] = sum_{q, g} X[a q g] sigma_g^2 X[a' q g],
+        rho^X = sum_{al, q_rest, g} X sigma^2 X^T,   rho^Y likewise with Y,
+        rho^D = Dm W_be Dm^T,  W_be from Y as W_al from X,
+    with the open pair as rows and every other leg of the factor summed.  Returned with
+    shape (d2, d3, d2, d3) each, keys "A", "X", "Y", "D"."""
+    Xs = X * sig
+    Ys = Y * sig
+    inner = list(range(1, X.ndim))                 # (q.., g) of X, (P.., g) of Y
+    W_al = np.tensordot(Xs, Xs, axes=(inner, inner))
+    W_be = np.tensordot(Ys, Ys, axes=(inner, inner))
+    rest = [0] + list(range(3, A.ndim))            # every leg but the pair (1, 2)
+    last = A.ndim - 1
+    AW = np.tensordot(A, W_al, axes=([last], [0]))  # bond leg still last
+    DW = np.tensordot(Dm, W_be, axes=([last], [0]))
+    return {"A": np.tensordot(AW, A, axes=(rest, rest)),
+            "X": np.tensordot(Xs, Xs, axes=(rest, rest)),
+            "Y": np.tensordot(Ys, Ys, axes=(rest, rest)),
+            "D": np.tensordot(DW, Dm, axes=(rest, rest))}
+
+
 def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, mlp=None,
                 Db=None, imp_two=False):
     """One triad-ATRG step on the re-split factors.  Legs (per site):
@@ -398,20 +427,12 @@ def _triad_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, psi_imp_pair=None, ml
     d2, d3, d4 = A.shape[1:4]
     chi_pair = d2 * d3
 
-    # (c) triad isometries from the canonical form (eq. HOSVD): only A, X, sigma are
-    #     needed for U^A (D, Y isometric) and symmetrically for the others.
-    Xs = X * sig
-    Ys = Y * sig
-    W_al = np.einsum("aIJKg,bIJKg->ab", Xs, Xs)
-    W_be = np.einsum("aIJKg,bIJKg->ab", Ys, Ys)
-    rhoA = np.tensordot(np.tensordot(A, W_al, axes=([4], [0])), A, axes=([0, 3, 4], [0, 3, 4]))
-    rhoX = np.tensordot(Xs, Xs, axes=([0, 3, 4], [0, 3, 4]))
-    rhoY = np.tensordot(Ys, Ys, axes=([0, 3, 4], [0, 3, 4]))
-    rhoD = np.tensordot(np.tensordot(Dm, W_be, axes=([4], [0])), Dm, axes=([0, 3, 4], [0, 3, 4]))
+    # (c) triad isometries from the canonical form (eq. HOSVD)
+    rho_all = triad_grams(A, Dm, X, sig, Y)
     chi = min(D + p, chi_pair)
     U = {}
     sketch_info = {}
-    for name, rho in (("A", rhoA), ("X", rhoX), ("Y", rhoY), ("D", rhoD)):
+    for name, rho in rho_all.items():
         key = sketch_key(seed, step, TAG_RHO[name])
         if mlp is None:
             Q = rsvd_range_sym(rho.reshape(chi_pair, chi_pair), chi, q_rho, key)
@@ -524,14 +545,7 @@ def _triad3_step(A, Dm, s, D, p, q_swap, q_rho, seed, step, Db=None, psi_imp_pai
     X, sig, Y, gap_swap = bond_swap(B, C, D if Db is None else Db, p, q_swap, seed, step)
     d2, d3 = A.shape[1:3]
     chi_pair = d2 * d3
-    Xs = X * sig
-    Ys = Y * sig
-    W_al = np.einsum("aIJg,bIJg->ab", Xs, Xs)
-    W_be = np.einsum("aIJg,bIJg->ab", Ys, Ys)
-    rho = {"A": np.einsum("tbca,ae,tBCe->bcBC", A, W_al, A, optimize=True),
-           "X": np.einsum("abcg,aBCg->bcBC", Xs, Xs),
-           "Y": np.einsum("abcg,aBCg->bcBC", Ys, Ys),
-           "D": np.einsum("wbca,ae,wBCe->bcBC", Dm, W_be, Dm, optimize=True)}
+    rho = triad_grams(A, Dm, X, sig, Y)
     chi = min(D + p, chi_pair)
     U = {name: rsvd_range_sym(r_.reshape(chi_pair, chi_pair), chi, q_rho,
                               sketch_key(seed, step, TAG_RHO[name])).reshape(d2, d3, -1)
