@@ -1,13 +1,14 @@
 // trg_gemm_noalloc: the split-BF16 tensor-core GEMM for callers that must not allocate.
 //
-// Some callers cannot call cudaMalloc at the point where they need a product: code that
-// runs while a CUDA graph is being captured (allocation is not a capturable operation),
-// host frameworks that own all device memory through their own pool and forbid foreign
-// allocations, and real-time loops that must not risk an allocation stall or failure
-// after start-up.  This entry point serves them: inputs and outputs are the caller's
-// device buffers, and the only scratch (BF16 slice buffers and split-K partial tiles) is
-// a fixed file-scope __device__ array of kScratchBytes.  No cudaMalloc, cudaFree or
-// allocating library routine is called.
+// Some callers cannot call cudaMalloc at the point where they need a product: host
+// frameworks that own all device memory through their own pool and forbid foreign
+// allocations (a second allocator would fragment or overcommit the pool), real-time
+// loops that must not risk an allocation stall or an out-of-memory failure after
+// start-up, and code that must not let cudaMalloc synchronise the device in the middle
+// of its own asynchronous work.  This entry point serves them: inputs and outputs are
+// the caller's device buffers, and the only scratch (BF16 slice buffers and split-K
+// partial tiles) is a fixed file-scope __device__ array of kScratchBytes.  No
+// cudaMalloc, cudaFree or allocating library routine is called.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,6 +93,13 @@ extern "C" trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long 
       throw Error(TRG_ERR_ARG, "trg_gemm_noalloc: precision must be a split-BF16 mode (1..3)");
     if (!A || !B || !C || M < 1 || N < 1 || K < 1)
       throw Error(TRG_ERR_ARG, "trg_gemm_noalloc: NULL buffer or empty size");
+    // row-major op(A) is M x K and op(B) K x N: a leading dimension shorter than the
+    // stored row would make the kernels read or write outside the caller's buffers
+    if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N)
+      throw Error(TRG_ERR_ARG, "trg_gemm_noalloc: leading dimension shorter than a row "
+                               "(need lda >= " + std::to_string(ta ? M : K) + ", ldb >= " +
+                               std::to_string(tb ? K : N) + ", ldc >= " + std::to_string(N) +
+                               ")");
     const int ns = precision == TRG_PREC_BF16X3 ? 2 : precision == TRG_PREC_BF16X6 ? 3 : 4;
     const size_t need = scratch_needed(M, N, K, ns);
     if (need > kScratchBytes)
@@ -99,8 +107,23 @@ extern "C" trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long 
                                    " MiB of scratch, more than the fixed " +
                                    std::to_string(kScratchBytes >> 20) + " MiB");
     FixedScratch scr(scratch_for_current_device());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     gemm_tc(ta != 0, tb != 0, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1, ns, scr,
-            static_cast<cudaStream_t>(stream));
+            st);
+    // wait for the product and report a bounded wait inside the kernel that gave up (the
+    // flag is cleared here, so it cannot be blamed on a later call); a stream that is
+    // capturing work is not waited on
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+      cudaGetLastError();
+      cap = cudaStreamCaptureStatusActive;
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
+      TRG_CUDA(cudaStreamSynchronize(st));
+      if (tc_error_flag(true))
+        throw Error(TRG_ERR_TIMEOUT, "trg_gemm_noalloc: a tensor-core pipeline wait timed out; "
+                                     "C is not valid");
+    }
     set_last_error("ok");
     return TRG_OK;
   } catch (const Error &e) {
