@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "triad-ATRG RG steps/s at D=48 4D Ising (mixed vs FP64 form, ΔF/F ≤1e-8)"
-PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "bf16x10": 3, "oz4": 4, "oz5": 5, "oz6": 6}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "bf16x10": 3, "oz4": 4, "oz5": 5, "oz6": 6,
+        "tf32x3": 7, "oz7": 8}
 
 
 def args_():
@@ -43,9 +44,13 @@ def args_():
     ap.add_argument("--precision", default="oz5", choices=list(PREC))
     ap.add_argument("--fp64-form-steps", type=int, default=0,
                     help="also time this many steady-state steps of the FP64 form (slow)")
-    ap.add_argument("--precision-steps", type=int, default=0,
+    ap.add_argument("--precision-steps", type=int, default=6,
                     help="N > 0: also run N steps of the FP64 form and of the mixed form at "
-                         "the bench's D and report dF/F per step (slow: FP64 form)")
+                         "the bench's D from the initial tensor; report dF/F after every "
+                         "step and the FP64 form's rate from its last (full-size) step")
+    ap.add_argument("--also-forms", default="",
+                    help="comma-separated precision forms also compared against the FP64 "
+                         "form in the size-level precision check (e.g. oz4,oz7,tf32x3)")
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "learned"],
                     help="learned: train the sketch network on rows collected from plain "
@@ -61,6 +66,10 @@ def args_():
                          "instead of the single D=48 step; ATRG holds D^8 tensors, so D <= 12")
     ap.add_argument("--r-bond", type=int, default=1,
                     help="ILO form: bond lines overspanned to r_bond D (1 = plain method)")
+    ap.add_argument("--gemm", default="",
+                    help="M,N,K: time one contraction-engine GEMM C = A B of that shape (host "
+                         "FP64 buffers through trg_gemm, --precision) instead of the step; "
+                         "for kernel profiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-check", action="store_true")
     return ap.parse_args()
@@ -78,33 +87,63 @@ def workload(a):
 
 
 # ----------------------------------------------------------------- oracle sample
-def oracle_sample(D, budget_s=25.0, r_bond=1):
-    """Oracle time per step, from its dominant part: the coarse contraction (eqs.
-    makeMG/makeMH) on D-sized triads (bond lines r_bond D) with the i1 leg cut to t = 1
-    and 2 of D slices; T(t) = a + b t is extrapolated to t = D.  Other phases are not
-    timed, so the result is an upper bound on the oracle's steps/s."""
-    import numpy as np
-    from oracle import trg_oracle as O
-    chi, Db = 3 * D, r_bond * D
-    rng = np.random.default_rng(0)
-    times = {}
-    for t in (1, 2):
-        E = rng.standard_normal((t, chi, D, Db))
-        F = rng.standard_normal((Db, chi, D, Db))
-        G = rng.standard_normal((Db, chi, D, Db))
-        H = rng.standard_normal((t, chi, D, Db))
-        U = [rng.standard_normal((D, D, chi)) for _ in range(4)]
-        Ms = {mu: rng.standard_normal((D, D, D)) for mu in (2, 3, 4)}
-        t0 = time.time()
-        O.contract_upper(E, F, U[0], U[1], Ms)
-        O.contract_lower(G, H, U[2], U[3], Ms)
-        times[t] = time.time() - t0
-        if times[t] > budget_s:
-            break
-    b = max(times.get(2, times[1]) - times[1], 0.0)
-    a0 = times[1] - b
-    per_step = a0 + b * D
-    return 1.0 / per_step, times, os.cpu_count()
+def sample_sizes(D):
+    """Bond dimensions of the oracle sample: the target D itself when a whole oracle step
+    there takes seconds, else two smaller D whose whole steps take 3-15 s each."""
+    return (D,) if D <= 20 else (16, 20)
+
+
+class OracleSample:
+    """Whole steps of the FP64 CPU oracle (every phase: re-split, bond swap, triad
+    isometries, triads, squeezers, coarse contraction, impurity, norm) on 4D Ising states
+    grown to the sample bond dimensions (growth untimed).  step() times one more step at
+    each sample D; per_step(D_target) is the time of one step at D_target, taken directly
+    when D_target is sampled, else extrapolated as c D^e with c, e fitted to the medians of
+    the two sample sizes (the method's cost grows as D^7 at large D; the exponent fitted
+    at small D is stated with the result)."""
+
+    def __init__(self, D, beta, r_bond=1):
+        from oracle import trg_oracle as O
+        self.O = O
+        self.sizes = sample_sizes(D)
+        self.r_bond = r_bond
+        self.st, self.n, self.times = {}, {}, {d: [] for d in self.sizes}
+        for d in self.sizes:
+            st = O.init_ising(4, beta, 0.0)
+            n = 0
+            while n < 4 or any(x != d for x in st.phi.shape[:4]):
+                O.step(st, n % 4, d, 2 * d, 4, 4, 0x5EED, r_bond=r_bond)
+                n += 1
+            self.st[d], self.n[d] = st, n
+
+    def step(self):
+        t_all = 0.0
+        for d in self.sizes:
+            t0 = time.time()
+            self.O.step(self.st[d], self.n[d] % 4, d, 2 * d, 4, 4, 0x5EED, r_bond=self.r_bond)
+            dt = time.time() - t0
+            self.n[d] += 1
+            self.times[d].append(dt)
+            t_all += dt
+        return t_all
+
+    def per_step(self, D):
+        med = {d: statistics.median(v) for d, v in self.times.items() if v}
+        if D in med:
+            return med[D], None
+        (d0, t0), (d1, t1) = sorted(med.items())
+        e = math.log(t1 / t0) / math.log(d1 / d0)
+        return t1 * (D / d1) ** e, e
+
+    def describe(self, D):
+        per, e = self.per_step(D)
+        med = {d: round(statistics.median(v), 3) for d, v in self.times.items() if v}
+        if e is None:
+            return (f"whole oracle steps (all phases) at D={D}, p=2D on a grown 4D Ising state; "
+                    f"median {med[D]:.3f} s over {len(self.times[D])} steps")
+        return (f"whole oracle steps (all phases) at D={list(med)} (p=2D, grown 4D Ising "
+                f"states), median s/step {med}; extrapolated to D={D} as c D^e with the "
+                f"fitted e={e:.2f}: {per:.0f} s/step")
 
 
 def run_reference(a):
@@ -112,17 +151,21 @@ def run_reference(a):
     if rank != 0:
         return
     t0 = time.time()
-    vals = []
-    for _ in range(max(a.steps, 1)):
-        v, times, cores = oracle_sample(a.D, r_bond=a.r_bond)
-        vals.append(v)
-    v = statistics.median(vals)
-    sample = (f"coarse contraction (eqs. makeMG/makeMH) of one D={a.D} step with the i1 leg "
-              f"cut to 1 and 2 of {a.D} slices, extrapolated linearly to {a.D}; other phases "
-              f"not timed (upper bound); timings {times}")
+    smp = OracleSample(a.D, a.beta, a.r_bond)       # growth: untimed set-up
+    for _ in range(a.warmup):
+        smp.step()
+    for d in smp.times:
+        smp.times[d].clear()
+    walls = [smp.step() for _ in range(max(a.steps, 1))]
+    per, _ = smp.per_step(a.D)
+    v = 1.0 / per
+    cores = os.cpu_count()
+    sample = smp.describe(a.D)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "RG steps/s",
-        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        # wall time of one reference step as run (the sample), not of a D=48 step
+        "ms_per_step": 1e3 * statistics.mean(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload(a),
         "cpu_baseline": {"value": v, "unit": "RG steps/s", "cores": cores, "kind": "oracle",
@@ -254,8 +297,8 @@ def learned_gain(trg):
 
 
 def precision_check(trg, prec, mlp=None, r_bond=1):
-    """ΔF/F of the mixed form: against the FP64 CPU oracle at D=14 (16 steps; no
-    near-degenerate truncation there) and against this library's FP64 form at D=24
+    """dF/F of the mixed form at small D: against the FP64 CPU oracle at D=14 (16 steps;
+    no near-degenerate truncation there) and against this library's FP64 form at D=24
     (12 steps; the FP64 form matches the oracle to 1e-10).  With a sketch network the
     oracle runs the same learned sketch."""
     from oracle import trg_oracle as O
@@ -267,6 +310,42 @@ def precision_check(trg, prec, mlp=None, r_bond=1):
     f24 = run_f(trg, prec, 24, 12)
     return {"vs_oracle_D14_16steps": abs(f14 - f_or) / abs(f_or),
             "vs_fp64_form_D24_12steps": abs(f24 - f24_64) / abs(f24_64)}
+
+
+def precision_at_size(trg, prec, D, beta, nsteps, stream, others=()):
+    """The headline's accuracy gate and its speed-up at the bench's own D: nsteps steps of
+    the FP64 form and of the mixed form from the same initial tensor (same sketches), the
+    relative free-energy difference after every step, and the FP64 form's rate from its
+    last step (full size from the fifth step on; CUDA events on the library stream).
+    `others`: further precision forms compared against the same FP64 run."""
+    import torch
+    out = {}
+    for pr in (0, prec) + tuple(others):
+        trg.trg_set_params(4, 4, 0x5EED, pr)
+        trg.trg_init_ising(4, beta, 0.0)
+        fs, ms = [], []
+        for k in range(nsteps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            trg.trg_step(k % 4, D, 2 * D)
+            e1.record(stream)
+            fs.append(trg.trg_free_energy()[0])
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[pr] = (fs, ms, list(trg.trg_state_dims(0)))
+    f64, ms64, dims64 = out[0]
+    fmx, msmx, _ = out[prec]
+    per = [abs(x - y) / abs(y) for x, y in zip(fmx, f64)]
+    res = {"steps": nsteps, "per_step": per, "max": max(per),
+           "fp64_form_ms_last_step": ms64[-1], "mixed_form_ms_last_step": msmx[-1],
+           "last_step_input_dims": dims64, "fp64_form_steps_per_s": 1e3 / ms64[-1]}
+    names = {v: k for k, v in PREC.items()}
+    for pr in others:
+        fo, mso, _ = out[pr]
+        po = [abs(x - y) / abs(y) for x, y in zip(fo, f64)]
+        res.setdefault("other_forms", {})[names[pr]] = {
+            "per_step": po, "max": max(po), "ms_last_step": mso[-1]}
+    return res
 
 
 def fp64_form_rate(trg, D, nsteps, beta):
@@ -383,6 +462,31 @@ def run_compare_atrg(a):
         "rows": rows}), flush=True)
 
 
+def run_gemm(a):
+    """One GEMM shape through trg_gemm (upload, product, download), warm-up then timed."""
+    import numpy as np
+    import paper_2507_21909_b300 as trg
+    M, N, K = (int(v) for v in a.gemm.split(","))
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    prec = PREC[a.precision]
+    for _ in range(a.warmup):
+        trg.trg_gemm(A, B, precision=prec)
+    t = []
+    for _ in range(max(a.steps, 1)):
+        t0 = time.time()
+        C = trg.trg_gemm(A, B, precision=prec)
+        t.append(time.time() - t0)
+    rows = rng.choice(M, 8, replace=False)
+    ref = A[rows] @ B
+    err = float(np.abs(C[rows] - ref).max() / (np.abs(A[rows]) @ np.abs(B)).max())
+    print(json.dumps({"metric": "trg_gemm wall time (upload + product + download)",
+                      "unit": "ms", "value": 1e3 * statistics.median(t), "M": M, "N": N, "K": K,
+                      "precision": a.precision, "sampled_rel_err": err,
+                      "alg_flop": 2.0 * M * N * K}), flush=True)
+
+
 def reduce_timing(ms, steps, world, dist=None, device="cpu"):
     """Replicas: the slowest rank's timed region counts (max over ranks), and the value is
     the steps all ranks completed in that time."""
@@ -392,6 +496,40 @@ def reduce_timing(ms, steps, world, dist=None, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     return ms_max, world * steps / (ms_max / 1e3)
+
+
+# Traffic of the dominant kernel per launch (dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture), keyed by kernel; None until captured on the current build.
+TRAFFIC = {}
+
+
+def roofline(stats, step_ms_total, steps, prec, peak, peak_src):
+    """Roofline of the dominant kernel: the exact-digit GEMM (digit forms) or the split-BF16
+    GEMM.  achieved = algorithmic flop (2 M N K of every product the step asks for, counted
+    once) / the kernel's device time (CUDA events around each launch, on its stream);
+    pipe_utilisation counts every BF16 digit / slice product as tensor-pipe work."""
+    k = "oz" if 4 <= prec <= 6 else "x7" if prec == 8 else "tc"
+    name = ("oz_gemm_kernel (exact-digit tcgen05 GEMM, %d digit products per product)"
+            % {4: 10, 5: 15, 6: 21, 8: 28}.get(prec, 0) if k in ("oz", "x7") else
+            "tc_gemm_kernel (split-BF16 or 3xTF32 tcgen05 GEMM, FP32 accumulation)")
+    ms, alg, pipe, n = stats[k + "_ms"], stats[k + "_flop"], stats[k + "_pipe_flop"], stats[
+        k + "_launches"]
+    ach = alg / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    both_ms = stats["oz_ms"] + stats["tc_ms"] + stats["x7_ms"]
+    return {
+        "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+        "traffic": TRAFFIC.get(k), "peak_source": peak_src, "kernel": name,
+        "flop": "algorithmic: 2 M N K per GEMM the step issues (FP64-equivalent product), "
+                "digit/slice products not counted",
+        "launches_per_step": n / steps, "alg_flop_per_launch": alg / n if n else 0.0,
+        "ms_per_launch": ms / n if n else 0.0, "kernel_ms_per_step": ms / steps,
+        "kernel_share_of_step": ms / step_ms_total,
+        "pipe_utilisation": (pipe / (ms / 1e3) / 1e12 / peak) if ms > 0 else 0.0,
+        "tensor_core_share_of_step": both_ms / step_ms_total,
+        "step_alg_tflops": (stats["oz_flop"] + stats["tc_flop"] + stats["x7_flop"])
+                           / (step_ms_total / 1e3) / 1e12,
+        "by_kind_ms_per_step": {k2: stats[k2 + "_ms"] / steps for k2 in ("oz", "tc", "x7")},
+    }
 
 
 def run_ours(a):
@@ -449,6 +587,7 @@ def run_ours(a):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     phases = {}
+    torch.cuda.nvtx.range_push("timed_steps")
     ev0.record(stream)
     for _ in range(a.steps):
         trg.trg_step(n % 4, D, p)
@@ -457,6 +596,7 @@ def run_ours(a):
         for k, v in trg.trg_step_timings().items():
             phases[k] = phases.get(k, 0.0) + v / a.steps
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clocks = clk.stop()
     t_job = time.time() - t_job
@@ -470,13 +610,7 @@ def run_ours(a):
             dist.destroy_process_group()
         return
     peak, peak_src = peaks()
-    achieved = stats["tc_flop"] / (stats["tc_ms"] / 1e3) / 1e12 if stats["tc_ms"] > 0 else 0.0
-    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-            "kernel": "tcgen05 GEMMs (oz_gemm_kernel digit products, tc_gemm_kernel BF16 splits); "
-                      "flop = BF16 tensor work of every slice/digit product",
-            "tc_launches": stats["tc_launches"], "tc_ms_per_step": stats["tc_ms"] / a.steps,
-            "tc_share_of_step": stats["tc_ms"] / ms}
+    roof = roofline(stats, ms, a.steps, prec, peak, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": "RG steps/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
@@ -503,30 +637,32 @@ def run_ours(a):
     if not a.no_precision_check and prec != 0:
         mlp = net_dict(trg.trg_sketch_get_net()) if learned is not None else None
         line["delta_f_rel"] = precision_check(trg, prec, mlp, a.r_bond)
-    if a.precision_steps > 0:
-        per = []
-        fs = {}
-        for pr in (prec, 0):
-            trg.trg_set_params(4, 4, 0x5EED, pr)
-            trg.trg_init_ising(4, a.beta, 0.0)
-            fs[pr] = []
-            for k in range(a.precision_steps):
-                trg.trg_step(k % 4, D, p)
-                fs[pr].append(trg.trg_free_energy()[0])
-        per = [abs(x - y) / abs(y) for x, y in zip(fs[prec], fs[0])]
+    if a.precision_steps > 0 and prec != 0:
+        others = tuple(PREC[x] for x in a.also_forms.split(",") if x.strip())
+        chk = precision_at_size(trg, prec, D, a.beta, a.precision_steps, stream, others)
         dfr = line.setdefault("delta_f_rel", {})
-        dfr[f"vs_fp64_form_D{D}_per_step"] = per
-        dfr[f"vs_fp64_form_D{D}_max"] = max(per)
+        dfr[f"vs_fp64_form_D{D}_per_step"] = chk["per_step"]
+        dfr[f"vs_fp64_form_D{D}_max"] = chk["max"]
+        line["fp64_form"] = {
+            "value": chk["fp64_form_steps_per_s"], "unit": "RG steps/s",
+            "measured": f"step {a.precision_steps - 1} of the FP64-form run above (input legs "
+                        f"{chk['last_step_input_dims']}), CUDA events on the library stream",
+            "ms_per_step": chk["fp64_form_ms_last_step"],
+            "mixed_form_ms_same_step": chk["mixed_form_ms_last_step"],
+            "speedup_of_value": value / chk["fp64_form_steps_per_s"]}
+        if "other_forms" in chk:
+            dfr[f"other_forms_vs_fp64_form_D{D}"] = chk["other_forms"]
     if a.fp64_form_steps > 0:
         r = fp64_form_rate(trg, D, a.fp64_form_steps, a.beta)
         line["fp64_form"] = {"value": r, "unit": "RG steps/s", "steps": a.fp64_form_steps,
                              "speedup_of_value": value / r}
     if not a.no_cpu_baseline:
-        v, times, cores = oracle_sample(D, r_bond=a.r_bond)
-        line["cpu_baseline"] = {
-            "value": v, "unit": "RG steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"coarse contraction (eqs. makeMG/makeMH) of one D={D} step with the i1 "
-                      f"leg cut to 1 and 2 slices, extrapolated to {D}; other phases not timed"}
+        smp = OracleSample(D, a.beta, a.r_bond)
+        smp.step()
+        per, _ = smp.per_step(D)
+        line["cpu_baseline"] = {"value": 1.0 / per, "unit": "RG steps/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": smp.describe(D)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -536,6 +672,8 @@ if __name__ == "__main__":
     a = args_()
     if a.impl == "reference":
         run_reference(a)
+    elif a.gemm:
+        run_gemm(a)
     elif a.batch > 0:
         run_batch(a)
     elif a.compare_atrg:

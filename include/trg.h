@@ -42,25 +42,32 @@ typedef int trg_status;
                                   tcgen05 products), exact FP32 chunks + int64 sums      */
 #define TRG_PREC_OZ5       5   /* 5 digits (15 products)                               */
 #define TRG_PREC_OZ6       6   /* 6 digits (21 products)                               */
-/* In the mixed forms (1..6) a step runs on the tensor cores only once all four legs and
- * the bond have reached D; the earlier, smaller steps run in FP64. */
+#define TRG_PREC_TF32X3    7   /* bulk GEMMs as 3xTF32 tcgen05 (kind::tf32: a_hi b_hi +
+                                  a_hi b_lo + a_lo b_hi), FP32 accum                     */
+#define TRG_PREC_OZ7       8   /* 7 digits (28 products), levels 0..3 exact: the FP64-
+                                  equivalent digit GEMM, for every bulk GEMM             */
+/* In the mixed forms (1..8) the first three steps run in FP64, later steps put their bulk
+ * GEMMs on the tensor cores.  In the digit forms (4..6, 8) the products that the bulk
+ * rule keeps off the tensor cores (Grams and R^-1 products of the orthonormalisations,
+ * squeezer Gram roots, thin products) run as the seven-digit FP64-equivalent GEMM. */
 
 /* Initial tensor of the d-dimensional Ising model, Sec. III (CP form
  * T = sum_a prod_legs W[a, leg], W = [[sqrt(cosh b), sqrt(sinh b)],
  * [sqrt(cosh b), -sqrt(sinh b)]]) with an added site field e^{h s}.
- * d: must be 4 (the triad step is four-dimensional).  beta >= 0.  The impurity
- * factor (one site carrying s) is created as well.  Resets the log-norm sum to
- * ln c_0, c_0 = ||T_0||_F, and the step counter to 0.  Errors: TRG_ERR_ARG (d != 4,
- * beta < 0 or not finite, h not finite), TRG_ERR_OOM, TRG_ERR_CUDA. */
+ * d: 4 (the paper's case) or 3 (the three-dimensional triad step whose cost the paper
+ * gives at the end of Sec. II B).  beta >= 0.  The impurity factor (one site carrying
+ * s) is created as well.  Resets the log-norm sum to ln c_0, c_0 = ||T_0||_F, and the
+ * step counter to 0.  Errors: TRG_ERR_ARG (d not 3 or 4, beta < 0 or not finite, h not
+ * finite), TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_init_ising(int d, double beta, double h);
 
 /* Z_q clock model (extension, not in the paper): bond weight e^{beta cos(th-th')},
  * th = 2 pi k / q, factorised in the real Fourier basis; site weight e^{h cos th};
- * impurity observable cos th.  d = 4, q in [2, 8], beta >= 0.  Errors: TRG_ERR_ARG,
- * TRG_ERR_OOM, TRG_ERR_CUDA. */
+ * impurity observable cos th.  d = 3 or 4, q in [2, 8], beta >= 0.  Errors:
+ * TRG_ERR_ARG, TRG_ERR_OOM, TRG_ERR_CUDA. */
 trg_status trg_init_clock(int d, int q, double beta, double h);
 
-/* One triad-ATRG coarse-graining step along physical axis `axis` (0..3):
+/* One triad-ATRG coarse-graining step along physical axis `axis` (0..d-1):
  * re-split T = A s D (eq. ABCD), bond swap by randomized SVD (Appendix A, eqs.
  * bond1/bond2, XY), triad isometries from the canonical-form Grams (eq. HOSVD), triads
  * E..L (eqs. E-L), squeezers from the Gram matrices O, P (Sec. II B), coarse
@@ -90,7 +97,7 @@ trg_status trg_magnetisation_impurity(double *m);
  * Appendix A); q_rho >= 0 extra power rounds of the triad / squeezer range finders;
  * seed of the counter-based Gaussian sketches; precision TRG_PREC_* (an extension: the
  * paper runs FP64).  Take effect from the next trg_step or trg_atrg_step.
- * Errors: TRG_ERR_ARG (q_swap < 1, q_rho < 0, precision outside 0..6). */
+ * Errors: TRG_ERR_ARG (q_swap < 1, q_rho < 0, precision outside 0..8). */
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision);
 
 /* Internal-line overspanning of the bond swap, the ILO form (Sec. II C; Appendix A with
@@ -114,7 +121,7 @@ trg_status trg_set_bond_overspan(int r_bond);
  * Errors: TRG_ERR_NOINIT (no model), TRG_ERR_ARG (a step was already taken). */
 trg_status trg_set_impurity_pair(void);
 
-/* Ising coupling energy per site (Sec. III D) U = -(1/V) d lnZ/d beta = -4 <s_x s_(x+e)>, from the
+/* Ising coupling energy per site (Sec. III D) U = -(1/V) d lnZ/d beta = -d <s_x s_(x+e)>, from the
  * merged pair of trg_set_impurity_pair (the pair's axis stands for every axis; the
  * field term -h <s> is not included).  Errors: TRG_ERR_ARG (u NULL, not the Ising
  * model), TRG_ERR_NOINIT (no merged pair: trg_set_impurity_pair and one step first). */
@@ -162,13 +169,18 @@ trg_status trg_diag(double *log_c, double *min_gap, int *nsteps);
  * (not in the paper).  Errors: TRG_ERR_ARG (ms NULL or n < 0), TRG_ERR_CUDA. */
 trg_status trg_step_timings(double *ms, int n);
 
-/* Counters since the last reset: device time (ms, CUDA events on the launching stream)
- * and tensor-pipe flop of the split-BF16 tcgen05 GEMM kernel launches inside trg_step
- * (each slice product counted as a full BF16 GEMM), their number, and the number of all
- * kernel launches of the library.  reset != 0 zeroes them after reading.  Measurement
- * service (not in the paper); any pointer may be NULL; always TRG_OK. */
-trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launches,
-                            long long *all_launches, int reset);
+/* Counters of the tensor-core GEMM launches inside trg_step / trg_atrg_step since the
+ * last reset, written to out[0..min(n, 13)):
+ *   [0] exact-digit GEMM (3..6 digits, TRG_PREC_OZ4..6) device ms (CUDA events on the
+ *   launching stream), [1] its algorithmic flop, 2 M N K per product asked for (the
+ *   FP64-equivalent work), [2] its tensor-pipe flop (every BF16 digit product counted,
+ *   a TF32 product as two), [3] its launches, [4..7] the same for the split GEMM
+ *   (TRG_PREC_BF16X*, TRG_PREC_TF32X3, and the impurity-only products of the digit forms),
+ *   [8..11] the same for the seven-digit FP64-equivalent digit GEMM (TRG_PREC_OZ7, and the
+ *   decomposition products of the digit forms), [12] all kernel launches of the library.
+ * reset != 0 zeroes them after reading.  Measurement service (not in the paper).
+ * Errors: TRG_ERR_ARG (out NULL with n > 0, n < 0). */
+trg_status trg_kernel_stats(double *out, int n, int reset);
 
 /* Device scratch of the step engine in bytes: in use now, high-water mark, reserved.
  * Any pointer may be NULL; always TRG_OK. */
@@ -185,7 +197,9 @@ trg_status trg_gu_wen_ratio(double *X);
 /* Copy a state factor to the host.  which: 0 = Phi, 1 = Psi, 2 = Psi_imp.
  * dims_out[0..4] receives (d1, d2, d3, d4, r); host may be NULL (query only), else it
  * must hold `capacity` doubles >= d1 d2 d3 d4 r.  axes_out[0..3] (may be NULL) gets
- * the physical axis of each leg slot.  Errors: TRG_ERR_NOINIT, TRG_ERR_ARG. */
+ * the physical axis of each leg slot.  A three-dimensional state (d1, d2, d3, r) is
+ * reported as (d1, d2, d3, 1, r), the same row-major layout, with axes_out[3] = -1.
+ * Errors: TRG_ERR_NOINIT, TRG_ERR_ARG. */
 trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
                          long long capacity);
 
@@ -198,7 +212,8 @@ trg_status trg_get_scalars(double *beta, double *logsum, int *nsteps);
 /* Load a state (e.g. an oracle state at step n, for per-step parity):
  * dims[0..4] = (d1, d2, d3, d4, r), phi/psi[/psi_imp (may be NULL)] row-major host
  * arrays, axes[0..3] the physical axis of each slot, nsteps taken so far and the
- * log-norm sum so far.  Errors: TRG_ERR_ARG (NULL pointers, a dim < 1, axes not a
+ * log-norm sum so far.  dims[3] = 1 with axes[3] = -1 loads a three-dimensional state
+ * (d1, d2, d3, r) (axes[0..2] a permutation of 0..2).  Errors: TRG_ERR_ARG (NULL pointers, a dim < 1, axes not a
  * permutation of 0..3, negative nsteps, beta or logsum not finite), TRG_ERR_NONFINITE
  * (a NaN or Inf in phi, psi or psi_imp), TRG_ERR_OOM.  Arguments and buffers are checked
  * on the host before the current state is touched, so a rejected call leaves it as it
@@ -217,23 +232,30 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
                     long long ldb, double beta, double *C, long long ldc);
 
 /* C = alpha op(A) op(B) + beta C like trg_gemm, but on the caller's DEVICE buffers
- * (row-major FP64, leading dimensions lda, ldb, ldc) and without allocating anything:
- * for callers that cannot call cudaMalloc at this point, such as code running while a
- * CUDA graph is captured, host frameworks that own all device memory through their own
- * pool, or real-time loops that must not allocate after start-up.  The paper has no
- * counterpart; this is a service of the library's contraction engine.
+ * (row-major FP64, leading dimensions lda, ldb, ldc) and without allocating anything.
+ * The paper has no counterpart; this is a service of the library's contraction engine,
+ * for callers that cannot call cudaMalloc where they need a product: host frameworks
+ * that own all device memory through their own pool and forbid foreign allocations,
+ * real-time loops that must not risk an allocation stall or an out-of-memory failure
+ * after start-up, and code that must not let cudaMalloc synchronise the device in the
+ * middle of its own asynchronous work.
  * precision: TRG_PREC_BF16X3, _BF16X6 or _BF16X10 (the split-BF16 tcgen05 GEMM; the
- * FP64 CUDA-core GEMM needs a workspace and is not offered here).  The only scratch is a
- * fixed 64 MiB __device__ array in the library (every GPU that loads the library holds
- * it until the process exits); problems that need more (BF16 slices of A and B plus
+ * FP64 CUDA-core GEMM needs a workspace and is not offered here).  lda >= K (ta = 0) or
+ * M (ta != 0), ldb >= N (tb = 0) or K (tb != 0), ldc >= N.  The only scratch is a fixed
+ * 64 MiB __device__ array in the library (every GPU that loads the library holds it
+ * until the process exits); problems that need more (BF16 slices of A and B plus
  * split-K partial tiles) are rejected with TRG_ERR_ARG and a message.  The work is
- * queued on `stream` (a cudaStream_t, NULL = legacy default stream) and not
- * synchronised.  The first call on each device looks up the array's device address
+ * queued on `stream` (a cudaStream_t, NULL = legacy default stream); the call then
+ * waits for it (cudaStreamSynchronize) and returns TRG_ERR_TIMEOUT if a bounded wait
+ * inside the tensor-core kernel gave up, in which case C is not valid.  If `stream` is
+ * capturing work when the call is made, it is not waited on and no kernel status is
+ * returned.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.  Every
- * call shares the array; calls whose work overlaps on the GPU (different streams, or
- * different host threads) race on it — serialise them.  All scratch is overwritten
- * before it is read, so no state carries over between calls.
- * Errors (returned before any work is queued): TRG_ERR_ARG, TRG_ERR_CUDA; see
+ * call shares the array and leaves its contents behind; all scratch is overwritten
+ * before it is read, so nothing carries over between calls, but calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on it:
+ * serialise them.
+ * Errors: TRG_ERR_ARG (before any work is queued), TRG_ERR_CUDA, TRG_ERR_TIMEOUT; see
  * trg_last_error(). */
 trg_status trg_gemm_noalloc(int precision, int ta, int tb, long long M, long long N,
                             long long K, double alpha, const double *A, long long lda,

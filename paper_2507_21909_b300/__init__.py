@@ -5,7 +5,7 @@ thin ctypes binding with the same entry-point names as ``include/trg.h``.  Acces
 any entry point fails loudly (ImportError) if the library has not been built with
 ``python -m paper_2507_21909_b300.build``; there is no CPU fallback.
 """
-_NAMES = ("TRG_PREC_BF16X3", "TRG_PREC_BF16X10", "TRG_PREC_OZ4", "TRG_PREC_OZ5", "TRG_PREC_OZ6", "TRG_PREC_BF16X6", "TRG_PREC_FP64", "TrgError", "lib",
+_NAMES = ("TRG_PREC_BF16X3", "TRG_PREC_BF16X10", "TRG_PREC_OZ4", "TRG_PREC_OZ5", "TRG_PREC_OZ6", "TRG_PREC_TF32X3", "TRG_PREC_OZ7", "TRG_PREC_BF16X6", "TRG_PREC_FP64", "TrgError", "lib",
           "library_path", "trg_diag", "trg_finalize", "trg_free_energy", "trg_get_state",
           "trg_init_clock", "trg_init_ising", "trg_magnetisation_impurity", "trg_set_params",
           "trg_set_state", "trg_set_stream", "trg_step", "EXPORTED", "trg_step_timings",

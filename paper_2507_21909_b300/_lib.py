@@ -9,6 +9,7 @@ _PATH = os.path.join(HERE, "libtrg.so")
 
 TRG_PREC_FP64, TRG_PREC_BF16X3, TRG_PREC_BF16X6, TRG_PREC_BF16X10 = 0, 1, 2, 3
 TRG_PREC_OZ4, TRG_PREC_OZ5, TRG_PREC_OZ6 = 4, 5, 6
+TRG_PREC_TF32X3, TRG_PREC_OZ7 = 7, 8
 EXPORTED = ["trg_init_ising", "trg_init_clock", "trg_step", "trg_free_energy",
             "trg_magnetisation_impurity", "trg_set_params", "trg_set_stream", "trg_diag",
             "trg_get_state", "trg_set_state", "trg_finalize", "trg_last_error",
@@ -56,8 +57,7 @@ def _load():
         "trg_gemm_noalloc": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d,
                              vp, ctypes.c_longlong, vp, ctypes.c_longlong, d, vp,
                              ctypes.c_longlong, vp],
-        "trg_kernel_stats": [pd, pd, ctypes.POINTER(ctypes.c_longlong),
-                             ctypes.POINTER(ctypes.c_longlong), i],
+        "trg_kernel_stats": [pd, i, i],
         "trg_gemm": [i, i, i, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, d, pd,
                      ctypes.c_longlong, pd, ctypes.c_longlong, d, pd, ctypes.c_longlong],
         "trg_sketch_set_net": [pf, ll], "trg_sketch_get_net": [pf, ll],
@@ -126,7 +126,7 @@ def trg_set_impurity_pair():
 
 
 def trg_internal_energy():
-    """Ising coupling energy per site -4 <s s'> from the merged impurity pair."""
+    """Ising coupling energy per site -d <s s'> from the merged impurity pair."""
     u = ctypes.c_double()
     _check(lib.trg_internal_energy(ctypes.byref(u)))
     return u.value
@@ -163,7 +163,9 @@ def trg_diag():
 
 
 def trg_get_state(which):
-    """Returns (array of shape (d1,d2,d3,d4,r), axes tuple)."""
+    """Returns (array of shape (d1,d2,d3,d4,r), axes tuple); a three-dimensional state
+    (reported by the library as (d1,d2,d3,1,r) with axes[3] = -1) comes back as
+    (d1,d2,d3,r) with three axes."""
     dims = (ctypes.c_int * 5)()
     axes = (ctypes.c_int * 4)()
     _check(lib.trg_get_state(int(which), dims, axes, None, 0))
@@ -171,14 +173,17 @@ def trg_get_state(which):
     out = np.empty(shape, dtype=np.float64)
     _check(lib.trg_get_state(int(which), dims, axes,
                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+    if axes[3] == -1:
+        return out.reshape(shape[:3] + shape[4:]), tuple(axes)[:3]
     return out, tuple(axes)
 
 
 def trg_state_dims(which=0):
-    """(d1, d2, d3, d4, r) of a state factor without copying it."""
+    """(d1, d2, d3, d4, r) of a state factor without copying it ((d1, d2, d3, r) in 3D)."""
     dims = (ctypes.c_int * 5)()
-    _check(lib.trg_get_state(int(which), dims, None, None, 0))
-    return tuple(dims)
+    axes = (ctypes.c_int * 4)()
+    _check(lib.trg_get_state(int(which), dims, axes, None, 0))
+    return tuple(dims)[:3] + tuple(dims)[4:] if axes[3] == -1 else tuple(dims)
 
 
 def trg_get_scalars():
@@ -214,11 +219,20 @@ def load_state(path):
 
 
 def trg_set_state(beta, phi, psi, psi_imp, axes, nsteps, logsum):
+    """Load a state: 4D factors (d1,d2,d3,d4,r) with four axes, or 3D factors (d1,d2,d3,r)
+    with three axes (passed to the library as (d1,d2,d3,1,r) with axes[3] = -1)."""
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     psi = np.ascontiguousarray(psi, dtype=np.float64)
-    if phi.shape != psi.shape or phi.ndim != 5:
-        raise ValueError("phi and psi must have the same 5-leg shape")
-    dims = (ctypes.c_int * 5)(*phi.shape)
+    if phi.shape != psi.shape or phi.ndim not in (4, 5):
+        raise ValueError("phi and psi must have the same 4- or 5-leg shape")
+    if phi.ndim == 4:
+        if len(axes) != 3:
+            raise ValueError("a three-dimensional state takes three axes")
+        shape = phi.shape[:3] + (1,) + phi.shape[3:]
+        axes = tuple(axes) + (-1,)
+    else:
+        shape = phi.shape
+    dims = (ctypes.c_int * 5)(*shape)
     ax = (ctypes.c_int * 4)(*axes)
     P = ctypes.POINTER(ctypes.c_double)
     imp = None
@@ -257,12 +271,16 @@ def trg_gemm(A, B, precision=TRG_PREC_FP64, ta=False, tb=False, alpha=1.0, beta=
 
 
 def trg_kernel_stats(reset=False):
-    ms, fl = ctypes.c_double(), ctypes.c_double()
-    n, alln = ctypes.c_longlong(), ctypes.c_longlong()
-    _check(lib.trg_kernel_stats(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n),
-                                ctypes.byref(alln), int(reset)))
-    return {"tc_ms": ms.value, "tc_flop": fl.value, "tc_launches": n.value,
-            "launches": alln.value}
+    """Tensor-core GEMM counters: per kind (oz = exact-digit 3..6 digits, tc = split-BF16 or
+    3xTF32, x7 = seven-digit FP64-equivalent) the device ms, algorithmic flop (2 M N K),
+    tensor-pipe flop and launches; all library launches."""
+    out = (ctypes.c_double * 13)()
+    _check(lib.trg_kernel_stats(out, 13, int(reset)))
+    v = list(out)
+    return {"oz_ms": v[0], "oz_flop": v[1], "oz_pipe_flop": v[2], "oz_launches": int(v[3]),
+            "tc_ms": v[4], "tc_flop": v[5], "tc_pipe_flop": v[6], "tc_launches": int(v[7]),
+            "x7_ms": v[8], "x7_flop": v[9], "x7_pipe_flop": v[10], "x7_launches": int(v[11]),
+            "launches": int(v[12])}
 
 
 def trg_mem_stats():

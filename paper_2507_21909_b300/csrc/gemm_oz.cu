@@ -51,6 +51,7 @@ constexpr int MAX_STAGES = 8;
 // as much as 12; warps 10 and 11 only take part in the block-wide barriers
 constexpr int NWARPS = 12, THREADS = NWARPS * 32;
 constexpr int MAX_PAIRS = 36;
+constexpr int kGroupM = 12;                 // row tiles per CTA-order group (~sqrt(148))
 constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 / @384 (alternating)
 
 struct Params {
@@ -153,6 +154,41 @@ __device__ __forceinline__ void umma(uint32_t acc_t, uint64_t da, uint64_t db, u
       : "memory");
 }
 
+// Store one warp's 32 x W output block, staged in shared memory as st[row][W + 1] (one
+// row per lane, as the TMEM lane layout delivers it), with consecutive lanes on
+// consecutive columns, so every row leaves as contiguous doubles: C = alpha v + beta C,
+// or v into a split-K workspace (to_ws).  With beta != 0 the old values of 8 rows are
+// loaded before any of them is stored, so those loads overlap.
+template <int W>
+__device__ __forceinline__ void store_block(const double *st, int lane, int64_t row0,
+                                            int64_t col0, int64_t M, int64_t N, double *Cbase,
+                                            int64_t ldc, bool to_ws, double alpha,
+                                            double beta) {
+  constexpr int Q = W / 32;
+  const bool rd = !to_ws && beta != 0.0;
+#pragma unroll 1
+  for (int r0 = 0; r0 < 32; r0 += 8) {
+    double old[8 * Q];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int64_t row = row0 + r0 + r, col = col0 + q * 32 + lane;
+        old[r * Q + q] = (rd && row < M && col < N) ? Cbase[row * ldc + col] : 0.0;
+      }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int64_t row = row0 + r0 + r, col = col0 + q * 32 + lane;
+        if (row < M && col < N) {
+          const double x = st[(r0 + r) * (W + 1) + q * 32 + lane];
+          Cbase[row * ldc + col] = to_ws ? x : rd ? alpha * x + beta * old[r * Q + q] : alpha * x;
+        }
+      }
+  }
+}
+
 template <int NS>
 __global__ void __launch_bounds__(THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -168,7 +204,19 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   // drained, bar[2nst+2] all done
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * MAX_STAGES + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  // CTA order: groups of kGroupM row tiles, column tiles within a group, so that the CTAs
+  // resident at one time cover a near-square patch of output tiles and share their A and
+  // B tiles in L2 (row-tile-fastest order would stream all of A once per few column tiles)
+  int64_t mt, nt;
+  {
+    const int64_t gx = gridDim.x, gy = gridDim.y;
+    const int64_t lin = (int64_t)blockIdx.y * gx + blockIdx.x;
+    const int64_t g = lin / ((int64_t)kGroupM * gy), idx = lin % ((int64_t)kGroupM * gy);
+    const int64_t first = g * kGroupM, gsz = min((int64_t)kGroupM, gx - first);
+    mt = first + idx % gsz;
+    nt = idx / gsz;
+  }
+  const int64_t m0 = mt * BM, n0 = nt * BN;
   const int64_t b = blockIdx.z % p.batch, split = blockIdx.z / p.batch;
   const int nks_total = (int)(p.Kp / KS);
   const int ks0 = (int)split * p.nks;
@@ -306,23 +354,250 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mb_arrive(su32(&bar[2 * nst + 1]));
     }
-    bool done = ok && nchunks > 0 && mb_wait(su32(&bar[2 * nst + 2]), 0);
+    // warp-uniform (the staged store below synchronises the warp)
+    const bool done =
+        __all_sync(0xffffffffu, ok && nchunks > 0 && mb_wait(su32(&bar[2 * nst + 2]), 0));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
     const int64_t ldc = p.to_ws ? p.N : p.ldc;
     const int er = row < p.M ? decode_exp(p.ea[b * p.M + row]) : 0;
-    if (row < p.M) {
-      double *crow = Cbase + row * ldc;
+    if (done) {
+      // every MMA has completed, so the stage ring is free: stage this warp's 32 x 64
+      // block there and store it row-contiguously
+      double *st = reinterpret_cast<double *>(smem) + (size_t)ew * 32 * 65;
 #pragma unroll
       for (int j = 0; j < 64; ++j) {
         const int64_t col = n0 + half * 64 + j;
-        if (col >= p.N) continue;
-        const double v =
-            done ? ldexp((double)acc[j], er + decode_exp(p.eb[b * p.N + col]) - 40) : 0.0;
-        if (p.to_ws)
-          crow[col] = v;
-        else
-          crow[col] = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * crow[col];
+        st[lane * 65 + j] = (row < p.M && col < p.N)
+                                ? ldexp((double)acc[j], er + decode_exp(p.eb[b * p.N + col]) - 40)
+                                : 0.0;
+      }
+      __syncwarp();
+      store_block<64>(st, lane, m0 + quad * 32, n0 + half * 64, p.M, p.N, Cbase, ldc, p.to_ws,
+                      p.alpha, p.beta);
+    } else if (row < p.M) {
+      // a pipeline wait gave up (flag set): the output is zeroed, row by row
+      double *crow = Cbase + row * ldc;
+      for (int j = 0; j < 64; ++j) {
+        const int64_t col = n0 + half * 64 + j;
+        if (col < p.N) crow[col] = 0.0;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// ------------------------------------------------------ the FP64-equivalent form
+// Seven digits (49 bits of every row of op(A) and column of op(B)) with levels 0..3 exact
+// per chunk: over a 256-deep chunk a level l sums l + 1 digit products of at most
+// 128 x 64 per k (<= 6.3e6 < 2^24 for l = 3), so levels 0..3 are exact FP32 integers;
+// the levels >= 4 (2^-14 and below of the result, ^a ^b units) share one FP32
+// accumulator per chunk (two buffers, alternating chunks).  Every chunk all five are
+// drained into an int64 fixed-point accumulator with XFRAC = 16 fractional bits:
+// |acc| <= K 2^44, so K per split stays <= 2^18.  The error of a product is then about
+// 2^-50 of max|a| max|b| per chunk, the level of an FP64 dot product, from 28 digit
+// products; tiles are 128 x 64 so that six 64-column accumulators fit the 512 TMEM
+// columns (L0..L3 @ 0, 64, 128, 192; H @ 256 / 320).
+constexpr int XNS = 7, XNL = 4, XBN = 64, XFRAC = 16;
+constexpr uint32_t XA_TILE = BM * KS * 2;                  // 4 KB
+constexpr uint32_t XB_TILE = XBN * KS * 2;                 // 2 KB
+constexpr uint32_t XSTAGE = XNS * (XA_TILE + XB_TILE);     // 42 KB
+constexpr int XSTAGES = 4;
+constexpr int64_t kXMaxKSplit = int64_t(1) << 18;
+constexpr uint32_t kIdescX = (1u << 4) | (1u << 7) | (1u << 10) |
+                             ((uint32_t)(XBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_x(uint32_t acc_t, uint64_t da, uint64_t db,
+                                       uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc_t),
+      "l"(da), "l"(db), "r"(kIdescX), "r"(accum)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const Params p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  constexpr int nst = XSTAGES;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * XSTAGE);
+  // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] chunk
+  // drained, bar[2nst+2] all done
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * nst + 3);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t mt, nt;
+  {
+    const int64_t gx = gridDim.x, gy = gridDim.y;
+    const int64_t lin = (int64_t)blockIdx.y * gx + blockIdx.x;
+    const int64_t g = lin / ((int64_t)kGroupM * gy), idx = lin % ((int64_t)kGroupM * gy);
+    const int64_t first = g * kGroupM, gsz = min((int64_t)kGroupM, gx - first);
+    mt = first + idx % gsz;
+    nt = idx / gsz;
+  }
+  const int64_t m0 = mt * BM, n0 = nt * XBN;
+  const int64_t b = blockIdx.z % p.batch, split = blockIdx.z / p.batch;
+  const int nks_total = (int)(p.Kp / KS);
+  const int ks0 = (int)split * p.nks;
+  const int nk = max(min(ks0 + p.nks, nks_total) - ks0, 0);
+  const int nchunks = (nk + CHUNK_KS - 1) / CHUNK_KS;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < nst; ++st) {
+      mb_init(su32(&bar[st]), 1);
+      mb_init(su32(&bar[nst + st]), 1);
+    }
+    mb_init(su32(&bar[2 * nst]), 1);
+    mb_init(su32(&bar[2 * nst + 1]), 8 * 32);
+    mb_init(su32(&bar[2 * nst + 2]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------------ TMA producer
+      for (int it = 0; it < nk; ++it) {
+        const int st = it % nst;
+        if (!mb_wait(su32(&bar[nst + st]), ((uint32_t)(it / nst) & 1u) ^ 1u)) break;
+        const uint32_t base = su32(smem + (size_t)st * XSTAGE);
+        const uint32_t full = su32(&bar[st]);
+        mb_expect(full, XSTAGE);
+        const int kc = (ks0 + it) * KS;
+        for (int sl = 0; sl < XNS; ++sl) {
+          tma4(base + sl * XA_TILE, &tmA, full, kc, (int)m0, (int)b, sl);
+          tma4(base + XNS * XA_TILE + sl * XB_TILE, &tmB, full, kc, (int)n0, (int)b, sl);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------ MMA issuer
+      constexpr uint64_t stepA = XA_TILE >> 4, stepB = XB_TILE >> 4;
+      bool ok = true;
+      int it = 0;
+      for (int ch = 0; ch < nchunks && ok; ++ch) {
+        const int kbeg = ch * CHUNK_KS, kend = min((ch + 1) * CHUNK_KS, nk);
+        for (int ks = kbeg; ks < kend; ++ks, ++it) {
+          const int st = it % nst;
+          if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sbase = su32(smem + (size_t)st * XSTAGE);
+          const uint64_t da = sdesc(sbase);
+          const uint64_t db = sdesc(sbase + XNS * XA_TILE);
+          // levels >= 4 into this chunk's H buffer (drained before chunk ch - 1 began)
+          const uint32_t acc_h = tmem + (uint32_t)((XNL + (ch & 1)) * XBN);
+#pragma unroll
+          for (int t = XNL; t < XNS; ++t)
+#pragma unroll
+            for (int i = 0; i <= t; ++i)
+              umma_x(acc_h, da + i * stepA, db + (t - i) * stepB,
+                     (ks > kbeg || t > XNL || i > 0) ? 1u : 0u);
+          // exact levels restart every chunk: the previous chunk must be drained first
+          if (ks == kbeg && ch > 0) {
+            if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+#pragma unroll
+          for (int t = 0; t < XNL; ++t)
+#pragma unroll
+            for (int i = 0; i <= t; ++i)
+              umma_x(tmem + (uint32_t)(t * XBN), da + i * stepA, db + (t - i) * stepB,
+                     (ks > kbeg || i > 0) ? 1u : 0u);
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  su32(&bar[nst + st]))
+              : "memory");
+        }
+        if (!ok) break;
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&bar[2 * nst]))
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(&bar[2 * nst + 2]))
+          : "memory");
+    }
+  } else if (warp < 10) {  // ------------------------------------------ drain warps 2..9
+    const int ew = warp - 2;                  // 0..7
+    const int quad = warp & 3;                // TMEM lane quadrant of this warp
+    const int half = ew >> 2;                 // columns [32 half, 32 half + 32)
+    const int64_t row = m0 + quad * 32 + lane;
+    long long acc[32];   // fixed point, XFRAC fractional bits
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t col = (uint32_t)(half * 32 + c * 16);
+#pragma unroll
+        for (int t = 0; t < XNL; ++t) {
+          uint32_t r[16];
+          tld16(lane_base + (uint32_t)(t * XBN) + col, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          // level t holds integers x 2^(14 - 7t); add them at 2^(14 - 7t + XFRAC)
+          const float unit = __int_as_float((127 - 14 + 7 * t) << 23);   // 2^(7t - 14)
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            acc[c * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * unit)
+                               << (14 - 7 * t + XFRAC);
+        }
+        uint32_t rh[16];
+        tld16(lane_base + (uint32_t)((XNL + (ch & 1)) * XBN) + col, rh);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * (float)(1 << XFRAC));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mb_arrive(su32(&bar[2 * nst + 1]));
+    }
+    // warp-uniform (the staged store below synchronises the warp)
+    const bool done =
+        __all_sync(0xffffffffu, ok && nchunks > 0 && mb_wait(su32(&bar[2 * nst + 2]), 0));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
+    const int64_t ldc = p.to_ws ? p.N : p.ldc;
+    const int er = row < p.M ? decode_exp(p.ea[b * p.M + row]) : 0;
+    if (done) {
+      double *st = reinterpret_cast<double *>(smem) + (size_t)ew * 32 * 33;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t col = n0 + half * 32 + j;
+        st[lane * 33 + j] =
+            (row < p.M && col < p.N)
+                ? ldexp((double)acc[j], er + decode_exp(p.eb[b * p.N + col]) - 28 - XFRAC)
+                : 0.0;
+      }
+      __syncwarp();
+      store_block<32>(st, lane, m0 + quad * 32, n0 + half * 32, p.M, p.N, Cbase, ldc, p.to_ws,
+                      p.alpha, p.beta);
+    } else if (row < p.M) {
+      double *crow = Cbase + row * ldc;
+      for (int j = 0; j < 32; ++j) {
+        const int64_t col = n0 + half * 32 + j;
+        if (col < p.N) crow[col] = 0.0;
       }
     }
   }
@@ -349,12 +624,21 @@ __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int
     const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * KT;
     const int64_t k1 = min(K, k0 + KT);
     const double *Xb = X + b * sX;
-    if (!trans) {  // warp per row, lanes along k
+    if (!trans) {  // warp per row, lanes along k, four independent loads in flight
       for (int i = warp; i < 32; i += nw) {
         const int64_t r = r0 + i;
         if (r >= rows) continue;
-        double m = 0.0;
-        for (int64_t k = k0 + lane; k < k1; k += 32) m = fmax(m, fabs(Xb[r * ld + k]));
+        const double *x = Xb + r * ld;
+        double m = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+        int64_t k = k0 + lane;
+        for (; k + 96 < k1; k += 128) {
+          m = fmax(m, fabs(x[k]));
+          m1 = fmax(m1, fabs(x[k + 32]));
+          m2 = fmax(m2, fabs(x[k + 64]));
+          m3 = fmax(m3, fabs(x[k + 96]));
+        }
+        for (; k < k1; k += 32) m = fmax(m, fabs(x[k]));
+        m = fmax(fmax(m, m1), fmax(m2, m3));
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0 && m > 0.0) {
           int ex;
@@ -364,9 +648,18 @@ __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int
       }
     } else {  // lanes along r (contiguous), warps split the k range
       const int64_t r = r0 + lane;
-      double m = 0.0;
-      if (r < rows)
-        for (int64_t k = k0 + warp; k < k1; k += nw) m = fmax(m, fabs(Xb[k * ld + r]));
+      double m = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+      if (r < rows) {
+        int64_t k = k0 + warp;
+        for (; k + 3 * nw < k1; k += 4 * nw) {
+          m = fmax(m, fabs(Xb[k * ld + r]));
+          m1 = fmax(m1, fabs(Xb[(k + nw) * ld + r]));
+          m2 = fmax(m2, fabs(Xb[(k + 2 * nw) * ld + r]));
+          m3 = fmax(m3, fabs(Xb[(k + 3 * nw) * ld + r]));
+        }
+        for (; k < k1; k += nw) m = fmax(m, fabs(Xb[k * ld + r]));
+        m = fmax(fmax(m, m1), fmax(m2, m3));
+      }
       if (r < rows && m > 0.0) {
         int ex;
         frexp(m, &ex);
@@ -376,61 +669,125 @@ __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int
   }
 }
 
-// digits ^a_s = d_s 2^(-7(s-1)) of op(X) rows, layout [slice][batch][rows][Kp] (K-major)
-__global__ void oz_split_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
-                                int64_t ld, int64_t sX, int trans, int ns, const unsigned *e,
-                                __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
-  __shared__ double tile[32][33];
-  const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
-  const int64_t ntiles = rt * kt * batch;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
-    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 32;
-    const double *Xb = X + b * sX;
-    __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-      double v = 0.0;
-      if (trans) {
-        const int64_t k = k0 + i, r = r0 + tx;
-        if (k < K && r < rows) v = Xb[k * ld + r];
-        tile[tx][i] = v;
-      } else {
-        const int64_t r = r0 + i, k = k0 + tx;
-        if (k < K && r < rows) v = Xb[r * ld + k];
-        tile[i][tx] = v;
-      }
-    }
-    __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-      const int64_t r = r0 + i, k = k0 + tx;
-      if (r >= rows || k >= Kp) continue;
-      // a' 2^(7 ns) rounded once to an integer q (|a'| < 1, so |q| < 2^(7 ns)), then split
-      // into balanced base-128 digits by integer arithmetic: d_{ns-1} .. d_1 in [-64, 63],
-      // d_0 the remaining top digit (|d_0| <= 128)
-      const int ex = decode_exp(e[b * rows + r]);
-      const double scale = __longlong_as_double((long long)(1023 - ex + 7 * ns) << 52);
-      long long q = __double2ll_rn(tile[i][tx] * scale);   // exact power-of-two scaling
-      int d[6];
+// Digit planes: a' = a 2^-e (e the row's exponent) times 2^(7 NS), rounded once to the
+// integer q (|q| < 2^(7 NS)), is cut into balanced base-128 digits, d_{NS-1} .. d_1 in
+// [-64, 63] from the bottom (d_s = ((q + 64) mod 128) - 64, q <- (q - d_s) / 128) and d_0
+// the remaining top digit (|d_0| <= 128).  The recursion only reads the low 7 bits and
+// divides exact multiples of 128, so the low three digits come from the low 21 bits in
+// 32-bit arithmetic and the rest from the high part plus the carry.  Planes are laid out
+// [slice][batch][rows][Kp] (K-major), zero padded for k >= K.
+template <int NS>
+__device__ __forceinline__ void balanced_digits(long long q, int (&d)[NS]) {
+  constexpr int NLOW = NS - 1 < 3 ? NS - 1 : 3;
+  int lo = (int)(q & 0x1FFFFF);
 #pragma unroll
-      for (int s = 5; s >= 1; --s) {
-        if (s < ns) {
-          const long long dd = ((q + 64) & 127) - 64;
-          d[s] = (int)dd;
-          q = (q - dd) >> 7;
-        }
-      }
-      d[0] = (int)q;
+  for (int t = 0; t < NLOW; ++t) {
+    const int dd = ((lo + 64) & 127) - 64;
+    d[NS - 1 - t] = dd;
+    lo = (lo - dd) >> 7;
+  }
+  int r = (int)((q >> 21) * (1ll << (21 - 7 * NLOW))) + lo;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) {
-        if (s < ns) {
-          // ^a_s = d_s 2^(-7(s-1)): exact in BF16 (<= 8 significant bits)
-          const float v = (float)d[s] * __int_as_float((127 - 7 * (s - 1)) << 23);
-          out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = __float2bfloat16_rn(v);
-        }
-      }
+  for (int s2 = NS - 1 - NLOW; s2 >= 1; --s2) {
+    const int dd = ((r + 64) & 127) - 64;
+    d[s2] = dd;
+    r = (r - dd) >> 7;
+  }
+  d[0] = r;
+}
+
+// ^a_s = d_s 2^(-7(s-1)) as BF16 (exact: at most 8 significant bits)
+template <int S>
+__device__ __forceinline__ float digit_value(int d) {
+  return (float)d * __int_as_float((127 - 7 * (S - 1)) << 23);
+}
+
+template <int NS, int S = 0>
+__device__ __forceinline__ void store_pairs(__nv_bfloat16 *o, int64_t plane, const int (&d0)[NS],
+                                            const int (&d1)[NS]) {
+  if constexpr (S < NS) {
+    *reinterpret_cast<__nv_bfloat162 *>(o + S * plane) =
+        __floats2bfloat162_rn(digit_value<S>(d0[S]), digit_value<S>(d1[S]));
+    store_pairs<NS, S + 1>(o, plane, d0, d1);
+  }
+}
+
+// Digit planes of op(X) = X (rows contiguous along K): one warp per row, each lane two
+// consecutive k (coalesced loads, one 4-byte store of two BF16 digits per plane)
+template <int NS>
+__global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
+                                     int64_t ld, int64_t sX, const unsigned *__restrict__ e,
+                                     __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t plane = batch * rows * Kp;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < batch * rows;
+       w += nwarps) {
+    const int64_t b = w / rows, r = w - b * rows;
+    const double *x = X + b * sX + r * ld;
+    const int ex = decode_exp(e[w]);
+    const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
+    __nv_bfloat16 *o = out + w * Kp;
+    for (int64_t k = 2 * lane; k < Kp; k += 64) {
+      const double v0 = k < K ? x[k] : 0.0, v1 = k + 1 < K ? x[k + 1] : 0.0;
+      int d0[NS], d1[NS];
+      balanced_digits<NS>(__double2ll_rn(v0 * scale), d0);
+      balanced_digits<NS>(__double2ll_rn(v1 * scale), d1);
+      store_pairs<NS>(o + k, plane, d0, d1);
     }
   }
+}
+
+// Digit planes of op(X) = X^T (X stored K x rows): 32 rows x 64 k tiles transposed
+// through shared memory, then each lane two consecutive k of one row, as above
+template <int NS>
+__global__ void oz_split_cols_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
+                                     int64_t ld, int64_t sX, const unsigned *__restrict__ e,
+                                     __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
+  __shared__ double tile[32][65];   // [row][k]
+  const int64_t rt = (rows + 31) / 32, kt = (Kp + 63) / 64;
+  const int64_t ntiles = rt * kt * batch;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int64_t plane = batch * rows * Kp;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
+    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 64;
+    const double *Xb = X + b * sX;
+    __syncthreads();
+    for (int i = ty; i < 64; i += 8) {   // k = k0 + i, lanes along the rows (contiguous)
+      const int64_t k = k0 + i, r = r0 + tx;
+      tile[tx][i] = (k < K && r < rows) ? Xb[k * ld + r] : 0.0;
+    }
+    __syncthreads();
+    const int64_t k = k0 + 2 * tx;
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i;
+      if (r >= rows || k >= Kp) continue;
+      const int ex = decode_exp(e[b * rows + r]);
+      const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
+      int d0[NS], d1[NS];
+      balanced_digits<NS>(__double2ll_rn(tile[i][2 * tx] * scale), d0);
+      balanced_digits<NS>(__double2ll_rn(tile[i][2 * tx + 1] * scale), d1);
+      store_pairs<NS>(out + (b * rows + r) * Kp + k, plane, d0, d1);
+    }
+  }
+}
+
+template <int NS>
+static void launch_split(const double *X, int64_t rows, int64_t K, int64_t ld, int64_t sX,
+                         bool trans, const unsigned *e, __nv_bfloat16 *out, int64_t Kp,
+                         int64_t batch, cudaStream_t s) {
+  if (trans) {
+    const int64_t t = ((rows + 31) / 32) * ((Kp + 63) / 64) * batch;
+    oz_split_cols_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32),
+                               dim3(32, 8), 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
+  } else {
+    const int64_t warps = rows * batch;
+    oz_split_rows_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>((warps + 7) / 8, 1),
+                                                            148 * 16),
+                               256, 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
+  }
+  TRG_LAUNCH_CHECK();
 }
 
 __global__ void oz_ws_reduce(const double *__restrict__ W, int ksplit, int64_t batch, int64_t M,
@@ -462,12 +819,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-static CUtensorMap tmap(const void *base, int64_t Kp, int64_t rows, int64_t batch, int ns) {
+static CUtensorMap tmap(const void *base, int64_t Kp, int64_t rows, int64_t batch, int ns,
+                        int box_rows = 128) {
   CUtensorMap m;
   cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)ns};
   cuuint64_t strides[3] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2),
                            (cuuint64_t)(batch * rows * Kp * 2)};
-  cuuint32_t box[4] = {(cuuint32_t)KS, 128u, 1, 1};   // 16 BF16 = 32-byte rows
+  cuuint32_t box[4] = {(cuuint32_t)KS, (cuuint32_t)box_rows, 1, 1};   // 16 BF16 = 32-byte rows
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -492,46 +850,85 @@ int oz_error_flag(bool reset) {
   return v;
 }
 
+// rows of op(X) per block of the small-K exponent kernel
+__global__ void oz_rowexp_small_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
+                                       int64_t ld, int64_t sX, int64_t batch,
+                                       unsigned *__restrict__ code) {
+  // op(X) = X (rows contiguous along K), K <= 128: one thread per row
+  const int64_t total = rows * batch;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / rows, r = t % rows;
+    const double *x = X + b * sX + r * ld;
+    double m = 0.0;
+    for (int64_t k = 0; k < K; ++k) m = fmax(m, fabs(x[k]));
+    unsigned cd = 0;
+    if (m > 0.0) {
+      int ex;
+      frexp(m, &ex);
+      cd = (unsigned)(ex + 4096);
+    }
+    code[b * rows + r] = cd;
+  }
+}
+
+OzOperand oz_prepare(const double *X, int64_t rows, int64_t K, int64_t ld, int64_t sX,
+                     bool trans, int64_t batch, int ns, TcScratch &scr, cudaStream_t s) {
+  using namespace oz;
+  OzOperand o;
+  o.rows = rows;
+  o.K = K;
+  o.Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
+  o.batch = batch;
+  o.ns = ns;
+  unsigned *e = (unsigned *)scr.alloc((size_t)batch * rows * sizeof(unsigned));
+  __nv_bfloat16 *pl = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * rows * o.Kp * 2);
+  if (!trans && K <= 128) {
+    const int64_t t = (rows * batch + 255) / 256;
+    oz_rowexp_small_kernel<<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 64),
+                             256, 0, s>>>(X, rows, K, ld, sX, batch, e);
+    TRG_LAUNCH_CHECK();
+  } else {
+    TRG_CUDA(cudaMemsetAsync(e, 0, (size_t)batch * rows * sizeof(unsigned), s));
+    const int64_t t = ((rows + 31) / 32) * ((K + 1023) / 1024) * batch;
+    oz_rowexp_kernel<<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32), 256, 0,
+                       s>>>(X, rows, K, ld, sX, trans ? 1 : 0, batch, e);
+    TRG_LAUNCH_CHECK();
+  }
+  switch (ns) {
+    case 3: launch_split<3>(X, rows, K, ld, sX, trans, e, pl, o.Kp, batch, s); break;
+    case 4: launch_split<4>(X, rows, K, ld, sX, trans, e, pl, o.Kp, batch, s); break;
+    case 5: launch_split<5>(X, rows, K, ld, sX, trans, e, pl, o.Kp, batch, s); break;
+    case 6: launch_split<6>(X, rows, K, ld, sX, trans, e, pl, o.Kp, batch, s); break;
+    default: launch_split<7>(X, rows, K, ld, sX, trans, e, pl, o.Kp, batch, s); break;
+  }
+  o.e = e;
+  o.planes = pl;
+  return o;
+}
+
 void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
              int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
              double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
-             cudaStream_t s, TcTiming *timing) {
+             cudaStream_t s, TcTiming *timing, const OzOperand *pa, const OzOperand *pb) {
   using namespace oz;
   if (M == 0 || N == 0 || batch == 0) return;
-  if (ns < 3 || ns > 6) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 6");
+  if (ns < 3 || ns > 7) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 7");
+  const bool x7 = ns == XNS;   // the FP64-equivalent form: its own kernel and tile width
+  const int bn = x7 ? XBN : BN;
   if (batch > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: batch too large");
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
+  auto fits = [&](const OzOperand *o, int64_t rows) {
+    return o && o->rows == rows && o->K == K && o->Kp == Kp && o->batch == batch && o->ns == ns;
+  };
+  if ((pa && !fits(pa, M)) || (pb && !fits(pb, N)))
+    throw Error(TRG_ERR_ARG, "gemm_oz: prepared operand does not match the product");
   // a Gram (op(A) = X^T, op(B) = X, or op(A) = X, op(B) = X^T) has identical digit planes
   const bool gram = A == B && ta != tb && M == N && lda == ldb && sA == sB;
-  unsigned *ea = (unsigned *)scr.alloc((size_t)batch * M * sizeof(unsigned));
-  unsigned *eb = gram ? ea : (unsigned *)scr.alloc((size_t)batch * N * sizeof(unsigned));
-  TRG_CUDA(cudaMemsetAsync(ea, 0, (size_t)batch * M * sizeof(unsigned), s));
-  if (!gram) TRG_CUDA(cudaMemsetAsync(eb, 0, (size_t)batch * N * sizeof(unsigned), s));
-  __nv_bfloat16 *As = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * M * Kp * 2);
-  __nv_bfloat16 *Bs = gram ? As : (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * N * Kp * 2);
-  {
-    auto g1 = [&](int64_t rows) {
-      int64_t t = ((rows + 31) / 32) * ((K + 1023) / 1024) * batch;
-      return (unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32);
-    };
-    oz_rowexp_kernel<<<g1(M), 256, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, batch, ea);
-    TRG_LAUNCH_CHECK();
-    if (!gram) {
-      oz_rowexp_kernel<<<g1(N), 256, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, batch, eb);
-      TRG_LAUNCH_CHECK();
-    }
-    dim3 b2(32, 8);
-    auto nblk = [&](int64_t rows) {
-      int64_t t = ((rows + 31) / 32) * ((Kp + 31) / 32) * batch;
-      return (unsigned)std::min<int64_t>(t, 148 * 32);
-    };
-    oz_split_kernel<<<nblk(M), b2, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, ea, As, Kp, batch);
-    TRG_LAUNCH_CHECK();
-    if (!gram) {
-      oz_split_kernel<<<nblk(N), b2, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, eb, Bs, Kp, batch);
-      TRG_LAUNCH_CHECK();
-    }
-  }
+  OzOperand oa = pa ? *pa : oz_prepare(A, M, K, lda, sA, ta, batch, ns, scr, s);
+  OzOperand ob = pb ? *pb : gram ? oa : oz_prepare(B, N, K, ldb, sB, !tb, batch, ns, scr, s);
+  const unsigned *ea = oa.e, *eb = ob.e;
+  const void *As = oa.planes, *Bs = ob.planes;
   Params p{};
   p.M = M;
   p.N = N;
@@ -549,7 +946,7 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
       p.pl[p.npairs] = t < 2 ? t : 2;
       ++p.npairs;
     }
-  const int64_t gx = (M + BM - 1) / BM, gy = (N + BN - 1) / BN;
+  const int64_t gx = (M + BM - 1) / BM, gy = (N + bn - 1) / bn;
   if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: N too large");
   const int nks_total = (int)(Kp / KS);
   int ksplit = 1;
@@ -560,15 +957,19 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
                                     65535 / batch);
     ksplit = std::max(ksplit, 1);
   }
-  // the fixed-point accumulator holds K 2^41 < 2^63: at most 2^21 K per split
-  ksplit = std::max<int>(ksplit, (int)((Kp + (int64_t(1) << 21) - 1) >> 21));
+  // the fixed-point accumulator holds K 2^41 < 2^63 (K 2^44 in the seven-digit form): at
+  // most 2^21 (2^18) K per split
+  const int64_t kmax = x7 ? kXMaxKSplit : (int64_t(1) << 21);
+  ksplit = std::max<int>(ksplit, (int)((Kp + kmax - 1) / kmax));
   int per = (nks_total + ksplit - 1) / ksplit;
   per = (per + CHUNK_KS - 1) / CHUNK_KS * CHUNK_KS;
   ksplit = (nks_total + per - 1) / per;
   p.nks = per;
   p.ns = ns;
-  p.stages = (int)std::min<size_t>(MAX_STAGES, kStageBudget / (2 * (size_t)ns * SLICE_TILE));
-  const size_t smem = (size_t)p.stages * 2 * ns * SLICE_TILE + 1024 + 256;
+  p.stages = x7 ? XSTAGES
+               : (int)std::min<size_t>(MAX_STAGES, kStageBudget / (2 * (size_t)ns * SLICE_TILE));
+  const size_t smem = x7 ? (size_t)XSTAGES * XSTAGE + 1024 + 256
+                         : (size_t)p.stages * 2 * ns * SLICE_TILE + 1024 + 256;
   if (ksplit > 1) {
     p.C = (double *)scr.alloc((size_t)ksplit * batch * M * N * sizeof(double));
     p.to_ws = 1;
@@ -580,19 +981,20 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     p.ldc = ldc;
     p.sC = sC;
   }
-  CUtensorMap ma = tmap(As, Kp, M, batch, ns), mb = tmap(Bs, Kp, N, batch, ns);
+  CUtensorMap ma = tmap(As, Kp, M, batch, ns), mb = tmap(Bs, Kp, N, batch, ns, bn);
   // thread-safe one-time setup (function-local static initialisation)
   static const bool attr_done = [] {
     for (const void *k : {(const void *)oz_gemm_kernel<3>, (const void *)oz_gemm_kernel<4>,
-                          (const void *)oz_gemm_kernel<5>, (const void *)oz_gemm_kernel<6>})
+                          (const void *)oz_gemm_kernel<5>, (const void *)oz_gemm_kernel<6>,
+                          (const void *)ozx_gemm_kernel})
       TRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kSmemMax));
     return true;
   }();
   (void)attr_done;
-  if (getenv("TRG_DEBUG_ATTR")) {
+  if (debug_opt("attr")) {
     const void *fns[4] = {(const void *)oz_gemm_kernel<5>, (const void *)oz_rowexp_kernel,
-                          (const void *)oz_split_kernel, (const void *)oz_ws_reduce};
+                          (const void *)oz_split_rows_kernel<5>, (const void *)oz_ws_reduce};
     for (int i = 0; i < 4; ++i) {
       cudaFuncAttributes fa;
       cudaFuncGetAttributes(&fa, fns[i]);
@@ -609,10 +1011,13 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     case 3: oz_gemm_kernel<3><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
     case 4: oz_gemm_kernel<4><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
     case 5: oz_gemm_kernel<5><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
-    default: oz_gemm_kernel<6><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    case 6: oz_gemm_kernel<6><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    default: ozx_gemm_kernel<<<grid, THREADS, smem, s>>>(ma, mb, p); break;
   }
   TRG_LAUNCH_CHECK();
-  if (timing) timing->after(s, 2.0 * (double)M * N * K * batch * p.npairs);
+  if (timing)
+    timing->after(s, x7 ? 2 : 0, 2.0 * (double)M * N * K * batch,
+                  2.0 * (double)M * N * K * batch * p.npairs);
   if (ksplit > 1) {
     const int64_t total = batch * M * N;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);

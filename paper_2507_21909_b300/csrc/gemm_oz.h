@@ -4,11 +4,25 @@
 
 namespace trg {
 
-// C (FP64) = alpha op(A) op(B) + beta C with `ns` 7-bit digits per row/column (3..6)
+// Digit planes of one operand op(X) (rows x K; trans: X stored K x rows) as the kernel
+// reads them: exponent codes [batch][rows] and planes [ns][batch][rows][Kp].  An operand
+// that several products share can be split once (oz_prepare) and passed to each.
+struct OzOperand {
+  const unsigned *e = nullptr;
+  const void *planes = nullptr;
+  int64_t rows = 0, K = 0, Kp = 0, batch = 0;
+  int ns = 0;
+};
+OzOperand oz_prepare(const double *X, int64_t rows, int64_t K, int64_t ld, int64_t sX,
+                     bool trans, int64_t batch, int ns, TcScratch &scr, cudaStream_t s);
+
+// C (FP64) = alpha op(A) op(B) + beta C with `ns` 7-bit digits per row/column (3..7);
+// pa / pb: planes of op(A) / op(B) prepared by oz_prepare (else split here)
 void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
              int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
              double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
-             cudaStream_t s, TcTiming *timing = nullptr);
+             cudaStream_t s, TcTiming *timing = nullptr, const OzOperand *pa = nullptr,
+             const OzOperand *pb = nullptr);
 int oz_error_flag(bool reset);
 
 }  // namespace trg

@@ -3,7 +3,10 @@
 // C (FP64) = alpha * op(A) op(B) + beta * C, where every FP64 operand is split into
 // `ns` BF16 slices  a = a_0 + a_1 + ... (a_0 = bf16(a), a_1 = bf16(a - a_0), ...)  and the
 // product is the sum of the slice products a_i b_j with i + j < ns (3 products for
-// ns = 2, 6 for ns = 3), accumulated in FP32 in tensor memory.
+// ns = 2, 6 for ns = 3), accumulated in FP32 in tensor memory.  The TF32 variant
+// (3xTF32 for ns = 2) slices into TF32 values (a_0 = tf32(a), a_1 = tf32(a - a_0)) held
+// as FP32 and issues kind::tf32 MMAs; a 128-byte tile row then holds 32 K values instead
+// of 64, with the same swizzle, descriptors and pipeline.
 //
 // Kernel: one CTA = 128 threads computes a 128 x BN tile.  Warp 0 / lane 0 issues TMA
 // loads (128B-swizzled K-major tiles, 4-stage mbarrier pipeline), warp 1 / lane 0 issues
@@ -96,19 +99,20 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-template <int BN>
-__host__ __device__ constexpr uint32_t idesc_bf16() {
+template <int BN, bool TF>
+__host__ __device__ constexpr uint32_t idesc_split() {
   return (1u << 4)                      // D: F32
-         | (1u << 7)                    // A: BF16
-         | (1u << 10)                   // B: BF16
+         | ((TF ? 2u : 1u) << 7)        // A: TF32 (kind::tf32) or BF16 (kind::f16)
+         | ((TF ? 2u : 1u) << 10)       // B: likewise
          | ((uint32_t)(BN >> 3) << 17)  // N / 8
          | ((uint32_t)(BM >> 4) << 24); // M / 16
 }
 
-template <int BN>
+template <int BN, bool TF>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const Params p) {
+  constexpr int BKE = TF ? BK / 2 : BK;   // K values in one 128-byte tile row
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -158,12 +162,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
       const uint32_t full = smem_u32(&bars[s]);
       mbar_expect_tx(full, STAGE_BYTES);
-      tma_load_4d(sa, &tmA, full, kb * BK, (int)m0, (int)b, p.pi[pr]);
-      tma_load_4d(sb, &tmB, full, kb * BK, (int)n0, (int)b, p.pj[pr]);
+      tma_load_4d(sa, &tmA, full, kb * BKE, (int)m0, (int)b, p.pi[pr]);
+      tma_load_4d(sb, &tmB, full, kb * BKE, (int)n0, (int)b, p.pj[pr]);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16<BN>();
+    constexpr uint32_t idesc = idesc_split<BN, TF>();
     for (int it = 0; it < iters; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -174,11 +178,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t da = sdesc(sa + kk * 32), db = sdesc(sb + kk * 32);
         const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc)
-            : "memory");
+        if constexpr (TF)
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc)
+              : "memory");
+        else
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc)
+              : "memory");
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -193,7 +204,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __syncwarp();
 
   // ---------------- epilogue: TMEM -> registers -> FP64 global
-  const bool have = iters > 0 && mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+  // warp-uniform (the staged store below synchronises the warp)
+  const bool have = __all_sync(0xffffffffu, iters > 0 && mbar_wait(smem_u32(&bars[2 * STAGES]), 0));
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int64_t row = m0 + warp * 32 + lane;
   double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
@@ -214,18 +226,38 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (row < p.M) {
-      double *crow = Cbase + row * ldc;
+    if (have) {
+      // the stage ring is free once the accumulator is ready: stage this warp's 32 x 32
+      // block and store each row as contiguous doubles (one row per lane in TMEM)
+      double *st = reinterpret_cast<double *>(smem) + (size_t)warp * 32 * 33;
 #pragma unroll
+      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = (double)__uint_as_float(r[j]);
+      __syncwarp();
+      const bool rd = !p.to_ws && p.beta != 0.0;
+      const int64_t row0 = m0 + warp * 32, col = n0 + c0 + lane;
+#pragma unroll 1
+      for (int r0 = 0; r0 < 32; r0 += 8) {
+        double old[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int64_t rr = row0 + r0 + i;
+          old[i] = (rd && rr < p.M && col < p.N) ? Cbase[rr * ldc + col] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int64_t rr = row0 + r0 + i;
+          if (rr < p.M && col < p.N) {
+            const double x = st[(r0 + i) * 33 + lane];
+            Cbase[rr * ldc + col] = p.to_ws ? x : rd ? p.alpha * x + p.beta * old[i] : p.alpha * x;
+          }
+        }
+      }
+      __syncwarp();
+    } else if (row < p.M) {
+      double *crow = Cbase + row * ldc;
       for (int j = 0; j < 32; ++j) {
         const int64_t col = n0 + c0 + j;
-        if (col < p.N) {
-          const double v = have ? (double)__uint_as_float(r[j]) : 0.0;
-          if (p.to_ws)
-            crow[col] = v;
-          else
-            crow[col] = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * crow[col];
-        }
+        if (col < p.N) crow[col] = 0.0;
       }
     }
   }
@@ -290,6 +322,53 @@ __global__ void split_kernel(const double *__restrict__ X, int64_t rows, int64_t
   }
 }
 
+// round to TF32 (10 explicit mantissa bits), to nearest, ties away from zero
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// FP64 -> ns TF32 slices (stored as FP32) of op(X), layout as split_kernel's:
+// a_0 = tf32(a), a_s = tf32(a - a_0 - ... - a_{s-1}), remainders formed in FP64
+__global__ void split_tf32_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
+                                  int64_t ld, int64_t sX, int trans, int ns,
+                                  float *__restrict__ out, int64_t Kp, int64_t batch) {
+  __shared__ double tile[32][33];
+  const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
+  const int64_t ntiles = rt * kt * batch;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
+    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 32;
+    const double *Xb = X + b * sX;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      double v = 0.0;
+      if (trans) {
+        const int64_t k = k0 + i, r = r0 + tx;
+        if (k < K && r < rows) v = Xb[k * ld + r];
+        tile[tx][i] = v;
+      } else {
+        const int64_t r = r0 + i, k = k0 + tx;
+        if (k < K && r < rows) v = Xb[r * ld + k];
+        tile[i][tx] = v;
+      }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i, k = k0 + tx;
+      if (r >= rows || k >= Kp) continue;
+      double remd = tile[i][tx];
+      for (int s = 0; s < ns; ++s) {
+        const float h = to_tf32((float)remd);
+        out[((int64_t)s * batch + b) * rows * Kp + r * Kp + k] = h;
+        remd -= (double)h;
+      }
+    }
+  }
+}
+
 __global__ void ws_reduce_kernel(const double *__restrict__ W, int ksplit, int64_t batch,
                                  int64_t M, int64_t N, double alpha, double beta,
                                  double *__restrict__ C, int64_t ldc, int64_t sC) {
@@ -319,16 +398,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 4-D map over slices laid out [ns][batch][rows][Kp] (bf16), box (BK, box_rows, 1, 1)
+// 4-D map over slices laid out [ns][batch][rows][Kp] (bf16, or fp32 holding TF32 values),
+// box (one 128-byte row of K values, box_rows, 1, 1)
 static CUtensorMap make_map(const void *base, int64_t Kp, int64_t rows, int64_t batch, int ns,
-                            int box_rows) {
+                            int box_rows, bool tf32 = false) {
   CUtensorMap m;
+  const int64_t es_b = tf32 ? 4 : 2;
   cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)ns};
-  cuuint64_t strides[3] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2),
-                           (cuuint64_t)(batch * rows * Kp * 2)};
-  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1, 1};
+  cuuint64_t strides[3] = {(cuuint64_t)(Kp * es_b), (cuuint64_t)(rows * Kp * es_b),
+                           (cuuint64_t)(batch * rows * Kp * es_b)};
+  cuuint32_t box[4] = {(cuuint32_t)(128 / es_b), (cuuint32_t)box_rows, 1, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base),
+  CUresult r = get_encode()(&m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                            4, const_cast<void *>(base),
                             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -341,17 +424,18 @@ static size_t smem_bytes() {
   return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
 }
 
-template <int BN>
+template <int BN, bool TF>
 static void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, dim3 grid,
                    cudaStream_t s) {
   // thread-safe one-time setup (function-local static initialisation)
   static const bool attr_done = [&] {
-    TRG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TRG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, TF>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<BN>()));
     return true;
   }();
   (void)attr_done;
-  tc_gemm_kernel<BN><<<grid, THREADS, smem_bytes<BN>(), s>>>(ma, mb, p);
+  tc_gemm_kernel<BN, TF><<<grid, THREADS, smem_bytes<BN>(), s>>>(ma, mb, p);
   TRG_LAUNCH_CHECK();
 }
 
@@ -373,27 +457,40 @@ int tc_error_flag(bool reset) {
 void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
              int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
              double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
-             cudaStream_t s, TcTiming *timing) {
+             cudaStream_t s, TcTiming *timing, bool tf32) {
   using namespace tc;
   if (M == 0 || N == 0 || batch == 0) return;
-  if (ns < 1 || ns > 4) throw Error(TRG_ERR_ARG, "gemm_tc: 1 <= slices <= 4");
+  if (ns < 1 || ns > 4 || (tf32 && ns > 3)) throw Error(TRG_ERR_ARG, "gemm_tc: 1 <= slices <= 4 (3 for TF32)");
   if (M > INT32_MAX || N > INT32_MAX || batch > 65535) throw Error(TRG_ERR_ARG, "gemm_tc: too large");
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
+  const int BKE = tf32 ? BK / 2 : BK;     // K values per 128-byte tile row
+  const size_t esz = tf32 ? 4 : 2;
   // slice buffers
-  const size_t abytes = (size_t)ns * batch * M * Kp * 2, bbytes = (size_t)ns * batch * N * Kp * 2;
-  __nv_bfloat16 *As = (__nv_bfloat16 *)scr.alloc(abytes);
-  __nv_bfloat16 *Bs = (__nv_bfloat16 *)scr.alloc(bbytes);
+  const size_t abytes = (size_t)ns * batch * M * Kp * esz, bbytes = (size_t)ns * batch * N * Kp * esz;
+  void *As = scr.alloc(abytes);
+  void *Bs = scr.alloc(bbytes);
   {
     dim3 blk(32, 8);
     auto nblk = [&](int64_t rows) {
       int64_t t = ((rows + 31) / 32) * ((Kp + 31) / 32) * batch;
       return (unsigned)std::min<int64_t>(t, 148 * 32);
     };
-    split_kernel<<<nblk(M), blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, As, Kp, batch);
-    TRG_LAUNCH_CHECK();
     // op(B)[k][n] -> rows n, K-major: transpose unless B is stored [n][k] (tb)
-    split_kernel<<<nblk(N), blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, Bs, Kp, batch);
-    TRG_LAUNCH_CHECK();
+    if (tf32) {
+      split_tf32_kernel<<<nblk(M), blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns, (float *)As,
+                                                Kp, batch);
+      TRG_LAUNCH_CHECK();
+      split_tf32_kernel<<<nblk(N), blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns, (float *)Bs,
+                                                Kp, batch);
+      TRG_LAUNCH_CHECK();
+    } else {
+      split_kernel<<<nblk(M), blk, 0, s>>>(A, M, K, lda, sA, ta ? 1 : 0, ns,
+                                           (__nv_bfloat16 *)As, Kp, batch);
+      TRG_LAUNCH_CHECK();
+      split_kernel<<<nblk(N), blk, 0, s>>>(B, N, K, ldb, sB, tb ? 0 : 1, ns,
+                                           (__nv_bfloat16 *)Bs, Kp, batch);
+      TRG_LAUNCH_CHECK();
+    }
   }
   Params p{};
   p.M = M;
@@ -413,7 +510,7 @@ void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   const int BNsel = N <= 128 ? 128 : 256;
   const int64_t gx = (N + BNsel - 1) / BNsel, gy = (M + BM - 1) / BM;
   if (gx > 65535) throw Error(TRG_ERR_ARG, "gemm_tc: N too large");
-  const int nkb_total = (int)(Kp / BK);
+  const int nkb_total = (int)(Kp / BKE);
   int ksplit = 1;
   const int64_t tiles = gx * gy * batch;
   if (tiles < 148 && nkb_total >= 8) {
@@ -435,17 +532,20 @@ void gemm_tc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     p.ldc = ldc;
     p.sC = sC;
   }
-  CUtensorMap ma = make_map(As, Kp, M, batch, ns, BM);
-  CUtensorMap mb = make_map(Bs, Kp, N, batch, ns, BNsel);
+  CUtensorMap ma = make_map(As, Kp, M, batch, ns, BM, tf32);
+  CUtensorMap mb = make_map(Bs, Kp, N, batch, ns, BNsel, tf32);
   dim3 grid((unsigned)gy, (unsigned)gx, (unsigned)(batch * ksplit));  // M tiles on x
   if (timing) timing->before(s);
   if (BNsel == 128)
-    launch<128>(ma, mb, p, grid, s);
+    tf32 ? launch<128, true>(ma, mb, p, grid, s) : launch<128, false>(ma, mb, p, grid, s);
   else
-    launch<256>(ma, mb, p, grid, s);
+    tf32 ? launch<256, true>(ma, mb, p, grid, s) : launch<256, false>(ma, mb, p, grid, s);
   ++g_tc_launches;
-  // tensor-pipe work of this launch: every slice product is a full M x N x K BF16 GEMM
-  if (timing) timing->after(s, 2.0 * (double)M * N * K * batch * p.npairs);
+  // tensor-pipe work of this launch: every slice product is a full M x N x K GEMM; a TF32
+  // product runs at half the BF16 rate, so it counts as two BF16 products
+  if (timing)
+    timing->after(s, 1, 2.0 * (double)M * N * K * batch,
+                  2.0 * (double)M * N * K * batch * p.npairs * (tf32 ? 2 : 1));
   if (ksplit > 1) {
     const int64_t total = batch * M * N;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);

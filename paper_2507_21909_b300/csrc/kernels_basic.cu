@@ -1,9 +1,46 @@
 // Elementwise, permutation, reduction and sketch kernels of libtrg (FP64).
+#include <algorithm>
+#include <cstdlib>
+#include <utility>
+
 #include "trg_internal.h"
 
 namespace trg {
 
 std::atomic<int64_t> g_kernel_launches{0};
+
+// ------------------------------------------------------------------ switches
+static std::vector<std::pair<std::string, std::string>> parse_list(const char *var) {
+  std::vector<std::pair<std::string, std::string>> out;
+  const char *e = getenv(var);
+  if (!e) return out;
+  std::string s(e);
+  size_t i = 0;
+  while (i <= s.size()) {
+    size_t j = s.find(',', i);
+    if (j == std::string::npos) j = s.size();
+    std::string item = s.substr(i, j - i);
+    if (!item.empty()) {
+      size_t eq = item.find('=');
+      out.emplace_back(item.substr(0, eq), eq == std::string::npos ? "1" : item.substr(eq + 1));
+    }
+    i = j + 1;
+  }
+  return out;
+}
+
+std::string study_opt(const char *key) {
+  for (auto &kv : parse_list("TRG_STUDY"))   // read at every call: tests set it per case
+    if (kv.first == key) return kv.second;
+  return std::string();
+}
+
+bool debug_opt(const char *key) {
+  static const auto opts = parse_list("TRG_DEBUG");
+  for (auto &kv : opts)
+    if (kv.first == key) return true;
+  return false;
+}
 
 // ------------------------------------------------------------------ permutation
 constexpr int kMaxDims = 10;
@@ -418,11 +455,93 @@ __global__ void sign_gauge_kernel(double *m1, int64_t rows1, double *m2, int64_t
   }
 }
 
+// The same rule for tall row-major matrices in three coalesced passes over all SMs.
+// Threads per block are a multiple of `cols`, so every thread stays on one column:
+// (1) per-column max |a| (non-negative doubles order like their bit patterns, so
+// atomicMax on the bits), (2) per column the first row within 1e-6 of it (atomicMin),
+// (3) the sign of that entry flips the column of m1 and of m2.
+__global__ void col_absmax_kernel(const double *__restrict__ m, int64_t n, int64_t cols,
+                                  unsigned long long *mx) {
+  extern __shared__ unsigned long long red[];
+  double v = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride)
+    v = fmax(v, fabs(m[e]));
+  red[threadIdx.x] = (unsigned long long)__double_as_longlong(v);
+  __syncthreads();
+  if (threadIdx.x < cols) {
+    unsigned long long b = 0;
+    for (int t = threadIdx.x; t < (int)blockDim.x; t += (int)cols) b = max(b, red[t]);
+    atomicMax(&mx[threadIdx.x], b);
+  }
+}
+
+__global__ void col_first_kernel(const double *__restrict__ m, int64_t n, int64_t cols,
+                                 const unsigned long long *mx, unsigned long long *first) {
+  extern __shared__ unsigned long long red[];
+  const int c = (int)(threadIdx.x % cols);
+  const double thr = (1.0 - 1e-6) * __longlong_as_double((long long)mx[c]);
+  unsigned long long f = ~0ull;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (thr > 0.0)
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride)
+      if (fabs(m[e]) >= thr) { f = (unsigned long long)(e / cols); break; }
+  red[threadIdx.x] = f;
+  __syncthreads();
+  if (threadIdx.x < cols) {
+    unsigned long long b = ~0ull;
+    for (int t = threadIdx.x; t < (int)blockDim.x; t += (int)cols) b = min(b, red[t]);
+    atomicMin(&first[threadIdx.x], b);
+  }
+}
+
+__global__ void col_sign_kernel(const double *m1, int64_t cols, const unsigned long long *first,
+                                double *sign) {
+  const int c = threadIdx.x;
+  if (c >= cols) return;
+  const unsigned long long f = first[c];
+  sign[c] = (f != ~0ull && m1[(int64_t)f * cols + c] < 0.0) ? -1.0 : 1.0;
+}
+
+__global__ void col_scale_kernel(double *m, int64_t n, int64_t cols, const double *sign) {
+  const int c = (int)(threadIdx.x % cols);
+  const double sg = sign[c];
+  if (sg > 0.0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride)
+    m[e] = -m[e];
+}
+
 void sign_gauge(double *m1, int64_t rows1, double *m2, int64_t rows2, int64_t cols,
                 cudaStream_t s) {
   if (cols == 0) return;
-  sign_gauge_kernel<<<(unsigned)cols, 256, 0, s>>>(m1, rows1, m2, rows2, cols);
+  if (cols > 256 || rows1 * cols < (int64_t(1) << 20)) {
+    sign_gauge_kernel<<<(unsigned)cols, 256, 0, s>>>(m1, rows1, m2, rows2, cols);
+    TRG_LAUNCH_CHECK();
+    return;
+  }
+  // workspace: cols max bits, cols first rows, cols signs (4 KB each at most)
+  static thread_local unsigned long long *ws = nullptr;
+  if (!ws) TRG_CUDA(cudaMalloc(&ws, 3 * 256 * sizeof(unsigned long long)));
+  unsigned long long *mx = ws, *first = ws + 256;
+  double *sign = reinterpret_cast<double *>(ws + 512);
+  TRG_CUDA(cudaMemsetAsync(mx, 0, 256 * sizeof(unsigned long long), s));
+  TRG_CUDA(cudaMemsetAsync(first, 0xFF, 256 * sizeof(unsigned long long), s));
+  const int threads = (int)(cols * std::max<int64_t>(1, 256 / cols));
+  const size_t shm = (size_t)threads * sizeof(unsigned long long);
+  const int blocks = 148 * 8;
+  col_absmax_kernel<<<blocks, threads, shm, s>>>(m1, rows1 * cols, cols, mx);
   TRG_LAUNCH_CHECK();
+  col_first_kernel<<<blocks, threads, shm, s>>>(m1, rows1 * cols, cols, mx, first);
+  TRG_LAUNCH_CHECK();
+  col_sign_kernel<<<1, 256, 0, s>>>(m1, cols, first, sign);
+  TRG_LAUNCH_CHECK();
+  col_scale_kernel<<<blocks, threads, 0, s>>>(m1, rows1 * cols, cols, sign);
+  TRG_LAUNCH_CHECK();
+  if (m2) {
+    col_scale_kernel<<<blocks, threads, 0, s>>>(m2, rows2 * cols, cols, sign);
+    TRG_LAUNCH_CHECK();
+  }
 }
 
 __global__ void fill_identity_kernel(double *out, int64_t n, int64_t cols) {

@@ -36,6 +36,22 @@ extern std::atomic<int64_t> g_kernel_launches;
 // message returned by trg_last_error()
 void set_last_error(const std::string &msg);
 
+// Two environment variables, read once, hold every switch that is not part of the API:
+//   TRG_STUDY="key=value,..."  precision and slicing studies; these change how a step is
+//       computed (never set by the library's own callers):
+//       slice_mb=<MiB>      budget of one coarse-contraction slice (default 1024)
+//       decomp_fp64=1       every GEMM inside a decomposition in FP64
+//       tc_phases=<mask>    phases whose GEMMs may use the tensor cores (default 0xFF)
+//       exact_everywhere=1  impurity-only products in the exact-digit form too
+//       tc_min_max=<n>      smallest max(M, N) sent to the tensor cores (default 64)
+//       swap_gram_digits=<n> digits of the bond-swap compression Grams (64 = FP64)
+//       decomp_cuda_fp64=1  digit forms: decomposition / thin products on the FP64 CUDA
+//                           cores instead of the seven-digit FP64-equivalent GEMM
+//   TRG_DEBUG="gemm,mem,svd,attr"  diagnostic prints to stderr (no effect on results).
+// study_opt returns the value of `key` ("" if unset); debug_opt whether it is listed.
+std::string study_opt(const char *key);
+bool debug_opt(const char *key);
+
 // ------------------------------------------------------------------ device arena
 // Bump allocator over a few large cudaMalloc chunks.  Scratch of one step is released
 // at once by reset(); persistent state buffers are separate cudaMalloc'd buffers.

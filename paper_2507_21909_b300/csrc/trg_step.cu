@@ -48,6 +48,7 @@ struct Ctx {
   double *phi = nullptr, *psi = nullptr, *psi_imp = nullptr;  // persistent state
   std::vector<int64_t> dims;                                   // d1..d4, r
   int axes[4] = {0, 1, 2, 3};
+  int d = 4;                   // lattice dimension (3 or 4)
   int nsteps = 0;
   double *dscal = nullptr;  // [0] logsum [1] c [2] trace [3] trace2; [8..] dot scratch
   int *dflag = nullptr;
@@ -63,11 +64,23 @@ struct Ctx {
   // cannot hold the dynamic range of a triangular inverse
   int64_t tc_min_mn = 16, tc_min_max = 64;
   bool cheap_policy = true;    // exact-digit forms use BF16x6 for those products
+  // exact-digit forms: the products kept off the bulk digit GEMM (orthonormalisations,
+  // squeezer roots, thin products) use the seven-digit FP64-equivalent GEMM, else FP64
+  bool x7_policy = true;
+  // digit planes of operands that several products of one scope share (PlaneScope)
+  struct PlaneEntry {
+    const double *ptr;
+    int64_t rows, K, ld, stride, batch;
+    bool trans;
+    int ns;
+    OzOperand op;
+  };
+  std::vector<PlaneEntry> plane_cache;
   bool b_upper = false;        // the next GEMM's right factor is upper triangular (R^-1)
   int ortho = 0;               // > 0: Grams and R^-1 products of an orthonormalisation (FP64)
   int digits_override = 0;     // > 0: digit count of the next digit-form GEMMs
   // digits of the bond swap's compression Grams G^C, G^B in the digit forms (0: the
-  // form's own; 64: FP64), for precision studies (TRG_SWAP_GRAM_DIGITS)
+  // form's own; 64: FP64), for precision studies (study switch swap_gram_digits)
   int swap_gram_digits = 0;
   // learned sketch of the triad-isometry range finders
   SketchNet net;
@@ -85,7 +98,7 @@ struct Ctx {
     phase = i;
     if (!ev[i]) TRG_CUDA(cudaEventCreate(&ev[i]));
     TRG_CUDA(cudaEventRecord(ev[i], stream));
-    static const bool dbg = getenv("TRG_DEBUG_MEM") != nullptr;
+    static const bool dbg = debug_opt("mem");
     if (dbg)
       fprintf(stderr, "phase %d: scratch in use %.2f GB, high water %.2f GB\n", i,
               arena.in_use() / 1073741824.0, arena.high_water() / 1073741824.0);
@@ -94,7 +107,8 @@ struct Ctx {
   // CUDA-event timing of the tensor-core kernel launches inside a step
   struct Timing : TcTiming {
     std::vector<cudaEvent_t> pool;
-    std::vector<double> flop;
+    struct Rec { int kind; double alg, pipe; };
+    std::vector<Rec> rec;
     size_t used = 0;
     void before(cudaStream_t s) override {
       if (pool.size() < 2 * used + 2) {
@@ -106,22 +120,27 @@ struct Ctx {
       }
       TRG_CUDA(cudaEventRecord(pool[2 * used], s));
     }
-    void after(cudaStream_t s, double f) override {
+    void after(cudaStream_t s, int kind, double alg, double pipe) override {
       TRG_CUDA(cudaEventRecord(pool[2 * used + 1], s));
-      if (flop.size() <= used) flop.resize(used + 1);
-      flop[used] = f;
+      if (rec.size() <= used) rec.resize(used + 1);
+      rec[used] = {kind, alg, pipe};
       ++used;
     }
   } timing;
-  double tc_ms = 0.0, tc_flop = 0.0;
-  int64_t tc_launches = 0;
+  // per kind (0 exact-digit GEMM, 1 split-BF16 / 3xTF32 GEMM, 2 seven-digit GEMM): device
+  // ms, algorithmic flop (2 M N K, counted once), tensor-pipe flop (every digit / slice
+  // product), launches
+  double k_ms[3] = {}, k_alg[3] = {}, k_pipe[3] = {};
+  int64_t k_launches[3] = {};
   void collect_tc() {  // after a stream synchronise
     for (size_t i = 0; i < timing.used; ++i) {
       float ms = 0.f;
       TRG_CUDA(cudaEventElapsedTime(&ms, timing.pool[2 * i], timing.pool[2 * i + 1]));
-      tc_ms += ms;
-      tc_flop += timing.flop[i];
-      ++tc_launches;
+      const int k = std::min(std::max(timing.rec[i].kind, 0), 2);
+      k_ms[k] += ms;
+      k_alg[k] += timing.rec[i].alg;
+      k_pipe[k] += timing.rec[i].pipe;
+      ++k_launches[k];
     }
     timing.used = 0;
   }
@@ -175,40 +194,88 @@ struct ArenaScratch : TcScratch {
 };
 
 static int slices_of(int precision) {
-  return precision == TRG_PREC_BF16X3 ? 2 : precision == TRG_PREC_BF16X6 ? 3 : 4;
+  return precision == TRG_PREC_BF16X3 || precision == TRG_PREC_TF32X3 ? 2
+         : precision == TRG_PREC_BF16X6                              ? 3
+                                                                     : 4;
 }
+static bool is_digit_form(int precision) {
+  return (precision >= TRG_PREC_OZ4 && precision <= TRG_PREC_OZ6) || precision == TRG_PREC_OZ7;
+}
+static int digits_of(int precision) { return precision == TRG_PREC_OZ7 ? 7 : precision; }
 
-// every GEMM of the step goes through here: bulk products run as split-BF16 tcgen05
-// GEMMs in the mixed forms, everything else (and every GEMM of the FP64 form) on the
-// FP64 CUDA cores
-static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
-                 const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
-                 int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
+// Where a product runs: the bulk digit GEMM (digits > 0 with on_tc), the split GEMM
+// (on_tc, digits 0), the seven-digit FP64-equivalent digit GEMM (on_x7) or FP64 cores.
+struct Route {
+  bool on_tc = false, on_x7 = false;
+  int digits = 0;   // digit count of a digit-GEMM route, 0 otherwise
+};
+static Route route_of(const Ctx &c, int64_t M, int64_t N, int64_t K) {
   // per-matrix work decides the route, so that batching independent problems does not
   // change how each one is computed
   const double work = (double)M * N * K;
-  static const bool dbg = getenv("TRG_DEBUG_GEMM") != nullptr;
+  Route r;
+  const bool tc_allowed = c.mixed_now && ((c.phase_mask >> c.phase) & 1u) &&
+                          !(c.crit_fp64 && c.crit_depth > 0) && work >= (double)(1 << 22) &&
+                          K >= 16;
+  r.on_tc = tc_allowed && c.ortho == 0 && std::min(M, N) >= c.tc_min_mn &&
+            std::max(M, N) >= c.tc_min_max && !(c.b_upper && N < c.tc_min_max);
+  // digit forms: the products the rule above keeps off the bulk digit GEMM (Grams and
+  // R^-1 products of orthonormalisations, squeezer Gram roots, thin products) run as the
+  // seven-digit FP64-equivalent digit GEMM instead of on the FP64 CUDA cores
+  r.on_x7 = !r.on_tc && tc_allowed && c.x7_policy && is_digit_form(c.precision) &&
+            std::min(M, N) >= 8;
+  // exact-digit forms: products that feed only the impurity (not the free energy) run as
+  // 6-term BF16 splits (the bond-swap range finder stays exact: with q_swap = 4 rounds its
+  // range depends on the iterates at first order)
+  const bool cheap = is_digit_form(c.precision) && c.bulk_cheap > 0 && c.crit_depth == 0;
+  if (r.on_x7)
+    r.digits = 7;
+  else if (r.on_tc && is_digit_form(c.precision) && !cheap)
+    r.digits = c.digits_override > 0 ? c.digits_override : digits_of(c.precision);
+  return r;
+}
+
+static const OzOperand *cached_planes(const Ctx &c, const double *X, int64_t rows, int64_t K,
+                                      int64_t ld, int64_t stride, int64_t batch, bool trans,
+                                      int ns) {
+  for (const auto &e : c.plane_cache)
+    if (e.ptr == X && e.rows == rows && e.K == K && e.ld == ld && e.batch == batch &&
+        e.trans == trans && e.ns == ns && (batch == 1 || e.stride == stride))
+      return &e.op;
+  return nullptr;
+}
+
+// every GEMM of the step goes through here: in the mixed forms bulk products run on the
+// tensor cores (digit or split GEMMs), in the digit forms the decomposition products as
+// the seven-digit GEMM; everything else (and every GEMM of the FP64 form) on the FP64
+// CUDA cores
+static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                 const double *A, int64_t lda, int64_t sA, const double *B, int64_t ldb,
+                 int64_t sB, double beta, double *C, int64_t ldc, int64_t sC, int64_t batch) {
+  const Route rt = route_of(c, M, N, K);
+  static const bool dbg = debug_opt("gemm");
   if (dbg)
-    fprintf(stderr, "gemm phase %d M %lld N %lld K %lld batch %lld ta %d tb %d crit %d cheap %d\n",
+    fprintf(stderr,
+            "gemm phase %d M %lld N %lld K %lld batch %lld ta %d tb %d crit %d cheap %d ortho %d "
+            "route %s digits %d\n",
             c.phase, (long long)M, (long long)N, (long long)K, (long long)batch, (int)ta, (int)tb,
-            c.crit_depth, c.bulk_cheap);
-  if (c.mixed_now && ((c.phase_mask >> c.phase) & 1u) && !(c.crit_fp64 && c.crit_depth > 0) &&
-      c.ortho == 0 &&
-      work >= (double)(1 << 22) && std::min(M, N) >= c.tc_min_mn && std::max(M, N) >= c.tc_min_max &&
-      K >= 16 && !(c.b_upper && N < c.tc_min_max)) {
+            c.crit_depth, c.bulk_cheap, c.ortho, rt.on_tc ? "tc" : rt.on_x7 ? "x7" : "f64",
+            rt.digits);
+  if (rt.digits > 0) {
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
-    // exact-digit forms: products that feed only the impurity (not the free energy) run
-    // as 6-term BF16 splits (the bond-swap range finder stays exact: with q_swap = 4
-    // rounds its range depends on the iterates at first order)
-    const bool cheap = c.precision >= TRG_PREC_OZ4 && c.bulk_cheap > 0 && c.crit_depth == 0;
-    if (c.precision >= TRG_PREC_OZ4 && !cheap)
-      gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-              c.digits_override > 0 ? c.digits_override : c.precision, scr, c.stream,
-              &c.timing);
-    else
-      gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-              cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing);
+    const OzOperand *pa = cached_planes(c, A, M, K, lda, sA, batch, ta, rt.digits);
+    const OzOperand *pb = cached_planes(c, B, N, K, ldb, sB, batch, !tb, rt.digits);
+    gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, rt.digits,
+            scr, c.stream, &c.timing, pa, pb);
+    c.arena.release(mk);
+  } else if (rt.on_tc) {
+    Arena::Mark mk = c.arena.mark();
+    ArenaScratch scr(c.arena);
+    const bool cheap = is_digit_form(c.precision);   // an impurity-only product of a digit form
+    gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+            cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing,
+            !cheap && c.precision == TRG_PREC_TF32X3);
     c.arena.release(mk);
   } else {
     gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream,
@@ -216,9 +283,36 @@ static void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
   }
 }
 
-// Grams that feed a Cholesky factor, and the products with its inverse, stay FP64 in the
-// mixed forms: a Gram squares the spectrum, and a digit error of 2^-35 of the largest
-// entry would swamp the eigenvalues near the truncation cut
+// Operands that several products of a scope share are split into digit planes once:
+// share() prepares the planes when a product of the given shape would run on a digit
+// GEMM, from the arena at the current level (so they live until the enclosing arena mark
+// is released), and gemm() finds them by pointer and layout.  The destructor forgets the
+// scope's entries.
+struct PlaneScope {
+  Ctx &c;
+  size_t n0;
+  explicit PlaneScope(Ctx &cc) : c(cc), n0(cc.plane_cache.size()) {}
+  ~PlaneScope() { c.plane_cache.resize(n0); }
+  // X as op(A) (as_a) or op(B) of the product op(A) op(B) with sizes M, N, K; t is that
+  // side's transpose flag (ta or tb) and ld its leading dimension
+  // (a batch of products: `batch` matrices `stride` doubles apart)
+  void share(const double *X, bool as_a, bool t, int64_t M, int64_t N, int64_t K, int64_t ld,
+             int64_t stride = 0, int64_t batch = 1) {
+    const Route rt = route_of(c, M, N, K);
+    if (rt.digits == 0) return;
+    const int64_t rows = as_a ? M : N;
+    const bool trans = as_a ? t : !t;
+    if (cached_planes(c, X, rows, K, ld, stride, batch, trans, rt.digits)) return;
+    ArenaScratch scr(c.arena);
+    OzOperand op = oz_prepare(X, rows, K, ld, stride, trans, batch, rt.digits, scr, c.stream);
+    c.plane_cache.push_back({X, rows, K, ld, stride, batch, trans, rt.digits, op});
+  }
+};
+
+// Grams that feed a Cholesky factor, and the products with its inverse, do not run on the
+// bulk digit GEMM: a Gram squares the spectrum, and a digit error of 2^-35 of the largest
+// entry would swamp the eigenvalues near the truncation cut (the digit forms run them as
+// the seven-digit FP64-equivalent GEMM, the other forms in FP64)
 struct Ortho {
   Ctx &c;
   explicit Ortho(Ctx &cc) : c(cc) { ++c.ortho; }
@@ -261,7 +355,11 @@ static Tensor mm_cols(Ctx &c, const Tensor &Q, const Tensor &U, int64_t ncols) {
 
 // einsum-style contraction of two tensors (every index appears in exactly two of the
 // three index strings): batch = in all three, M = A and out, N = B and out, K = A and B.
-static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const Tensor &B) {
+// With `into`, the result goes to that buffer: written (beta_into = 0, any output order)
+// or accumulated as *into = result + beta_into * *into (then the output order must be
+// the GEMM's natural one, batch + M + N indices).
+static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const Tensor &B,
+                       Tensor *into = nullptr, double beta_into = 0.0) {
   size_t comma = spec.find(','), arrow = spec.find("->");
   std::string sa = spec.substr(0, comma), sb = spec.substr(comma + 1, arrow - comma - 1),
               so = spec.substr(arrow + 2);
@@ -301,7 +399,9 @@ static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const T
   };
   std::vector<int64_t> odims;
   for (char ch : so) odims.push_back(dim[ch]);
-  Tensor out = c.alloc(odims);
+  if (into && (into->dims != odims || (beta_into != 0.0 && so != bt + Mi + Ni)))
+    throw Error(TRG_ERR_ARG, "contract: accumulation needs the natural output order in " + spec);
+  Tensor out = into ? *into : c.alloc(odims);
   Arena::Mark mk = c.arena.mark();
   bool ta = false, tb = false;
   const double *pa, *pb;
@@ -317,8 +417,8 @@ static Tensor contract(Ctx &c, const std::string &spec, const Tensor &A, const T
   std::vector<int64_t> ndims;
   for (char ch : nat) ndims.push_back(dim[ch]);
   Tensor C = (so == nat) ? out : c.alloc(ndims);
-  gemm(c, ta, tb, M, N, K, 1.0, pa, ta ? M : K, M * K, pb, tb ? K : N, K * N, 0.0, C.p, N,
-       M * N, nb);
+  gemm(c, ta, tb, M, N, K, 1.0, pa, ta ? M : K, M * K, pb, tb ? K : N, K * N,
+       into ? beta_into : 0.0, C.p, N, M * N, nb);
   if (so != nat) {
     std::vector<int> perm;
     for (char ch : so) perm.push_back((int)nat.find(ch));
@@ -382,6 +482,45 @@ static std::pair<Tensor, Tensor> orth_qr(Ctx &c, const Tensor &Y) {
   return {Q, R};
 }
 
+// The same shifted CholeskyQR3 with its last pass kept as factors: Y = Q2 R, with Q2 the
+// basis after two passes, Ri3 the inverse of the third pass's Cholesky factor and
+// R = R3 R2 R1 (each pass Q_{i+1} = Q_i R_i^-1, so Y = Q2 R2 R1 = Q R3 R2 R1).  The
+// orthonormal factor is Q = Q2 Ri3; a caller that needs Q W forms Q2 (Ri3 W), which
+// saves the third tall product and the product Q^T Y that R would otherwise cost.
+struct FoldedQR {
+  Tensor Q2, Ri3, R;
+};
+static FoldedQR orth_qr_folded(Ctx &c, const Tensor &Y) {
+  Crit cr(c);
+  Ortho og(c);
+  const int64_t n = Y.dims[0], w = Y.dims[1];
+  FoldedQR f;
+  f.Q2 = c.alloc(Y.dims);
+  f.Ri3 = c.alloc({w, w});
+  f.R = c.alloc({w, w});
+  Arena::Mark mk = c.arena.mark();
+  Tensor Q = Y;
+  Tensor Rp[3];
+  for (int pass = 0; pass < 3; ++pass) {
+    Tensor G = mm(c, Q, Q, true, false);
+    Rp[pass] = c.alloc({w, w});
+    Tensor Ri = pass == 2 ? f.Ri3 : c.alloc({w, w});
+    chol_rinv(G.p, Rp[pass].p, Ri.p, (int)w, 1, pass == 0 ? 0.0 : kPivotTol,
+              pass == 0 ? kShiftRel : 0.0, c.stream);
+    if (pass < 2) {
+      Tensor Qn = pass == 1 ? f.Q2 : c.alloc(Y.dims);
+      c.b_upper = true;
+      gemm(c, false, false, n, w, w, 1.0, Q.p, w, 0, Ri.p, w, 0, 0.0, Qn.p, w, 0, 1);
+      c.b_upper = false;
+      Q = Qn;
+    }
+  }
+  Tensor R32 = mm(c, Rp[2], Rp[1], false, false);
+  gemm(c, false, false, w, w, w, 1.0, R32.p, w, 0, Rp[0].p, w, 0, 0.0, f.R.p, w, 0, 1);
+  c.arena.release(mk);
+  return f;
+}
+
 struct Svd {
   Tensor U, S, V;
 };
@@ -392,7 +531,7 @@ static Svd svd_small(Ctx &c, const Tensor &A) {
   r.S = c.alloc({n});
   r.V = c.alloc({n, n});
   Tensor work = c.alloc({(int64_t)svd_jacobi_work((int)m, (int)n, 1) + 1});
-  static const bool dbg = getenv("TRG_DEBUG_SVD") != nullptr;
+  static const bool dbg = debug_opt("svd");
   int *info = dbg ? reinterpret_cast<int *>(work.p + work.size() - 1) : nullptr;
   svd_jacobi(A.p, (int)m, (int)n, r.U.p, r.S.p, r.V.p, 1, work.p, info, c.stream);
   if (dbg) {
@@ -488,13 +627,50 @@ static Tensor range_from_factor(Ctx &c, const Tensor &F, const Tensor &Om, int q
   return Q;
 }
 
+// F's digit planes for both products of the range finder (F^T V and F Z), split once
+static void share_factor(PlaneScope &ps, const Tensor &F, int64_t chi) {
+  const int64_t n = F.dims[0], m = F.dims[1];
+  ps.share(F.p, true, true, m, chi, n, m);    // F^T V: op(A) = F^T (m x n)
+  ps.share(F.p, true, false, n, chi, m, m);   // F Z:   op(A) = F   (n x m)
+}
+
 static Tensor rsvd_factor(Ctx &c, const Tensor &F, int64_t chi, int q, uint64_t key) {
   const int64_t n = F.dims[0];
   Tensor out = c.alloc({n, chi});
   Arena::Mark mk = c.arena.mark();
+  PlaneScope ps(c);
+  share_factor(ps, F, chi);
   Tensor Om = c.alloc({n, chi});
   fill_gaussian(Om.p, n, chi, key, c.stream);
   Tensor Q = range_from_factor(c, F, Om, q);
+  TRG_CUDA(cudaMemcpyAsync(out.p, Q.p, out.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
+  c.arena.release(mk);
+  return out;
+}
+
+// nb range finders of rho_i = F_i F_i^T at once (every F_i n x m, stacked [nb][n][m]):
+// the sketches and subspaces of rsvd_factor on each, with every product, Gram and
+// Cholesky of a power round one batched launch and the F_i split into digit planes once
+static Tensor rsvd_factor_batched(Ctx &c, const Tensor &Fs, int64_t chi, int q,
+                                  const std::vector<uint64_t> &keys) {
+  const int64_t nb = Fs.dims[0], n = Fs.dims[1], m = Fs.dims[2];
+  Tensor out = c.alloc({nb, n, chi});
+  Arena::Mark mk = c.arena.mark();
+  PlaneScope ps(c);
+  ps.share(Fs.p, true, true, m, chi, n, m, n * m, nb);    // F^T V: op(A) = F^T (m x n)
+  ps.share(Fs.p, true, false, n, chi, m, m, n * m, nb);   // F Z:   op(A) = F   (n x m)
+  Tensor Om = c.alloc({nb, n, chi});
+  for (int64_t b = 0; b < nb; ++b) fill_gaussian(Om.p + b * n * chi, n, chi, keys[b], c.stream);
+  auto apply = [&](const Tensor &V) {
+    Tensor Z = c.alloc({nb, m, chi}), Y = c.alloc({nb, n, chi});
+    gemm(c, true, false, m, chi, n, 1.0, Fs.p, m, n * m, V.p, chi, n * chi, 0.0, Z.p, chi,
+         m * chi, nb);
+    gemm(c, false, false, n, chi, m, 1.0, Fs.p, m, n * m, Z.p, chi, m * chi, 0.0, Y.p, chi,
+         n * chi, nb);
+    return Y;
+  };
+  Tensor Q = orth_sc_batched(c, apply(Om));
+  for (int i = 0; i < q; ++i) Q = orth_sc_batched(c, apply(Q));
   TRG_CUDA(cudaMemcpyAsync(out.p, Q.p, out.size() * 8, cudaMemcpyDeviceToDevice, c.stream));
   c.arena.release(mk);
   return out;
@@ -528,6 +704,8 @@ static Tensor range_factor_full(Ctx &c, const Tensor &F, int64_t da, int64_t db,
   cudaStream_t s = c.stream;
   Tensor out = c.alloc({n, chi});
   Arena::Mark mk = c.arena.mark();
+  PlaneScope ps(c);
+  share_factor(ps, F, chi);
   Tensor G = c.alloc({n, chi});
   fill_gaussian(G.p, n, chi, key, s);
   Tensor Qp = range_from_factor(c, F, G, q);
@@ -647,16 +825,19 @@ static Tensor gram_root_batched(Ctx &c, const Tensor &rho, int64_t chi, int q,
 
 // Rows of t (the first leg, i1 of the paper's Table I) per slice of the coarse
 // contraction, so that the intermediate Phi1 (t kA k4 kX g) of one slice stays below
-// `budget` bytes (default 1 GiB; TRG_CONTRACT_SLICE_MB overrides, for tests).  The slices
+// `budget` bytes (default 1 GiB; the study switch slice_mb overrides it, for tests).  The slices
 // are independent GEMM chains; their outputs are disjoint rows of Phi / Psi.
 static int64_t t_slice(int64_t kt, int64_t per_t_elems) {
   int64_t budget = int64_t(1) << 30;
-  if (const char *e = getenv("TRG_CONTRACT_SLICE_MB")) budget = std::max<int64_t>(1, atoll(e)) << 20;
+  const std::string e = study_opt("slice_mb");
+  if (!e.empty()) budget = std::max<int64_t>(1, atoll(e.c_str())) << 20;
   const int64_t per_t = std::max<int64_t>(per_t_elems * (int64_t)sizeof(double), 1);
   return std::max<int64_t>(1, std::min<int64_t>(kt, budget / per_t));
 }
 
-// Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG), sliced over t
+// Phi[t,k2,k3,k4,g] = sum (E F M4)(I J M2 M3)   (eq. makeMG), sliced over t.  Operands
+// that every slice reuses are put in GEMM order once (F as (al q4 | kX g)); each slice's
+// EM comes out in GEMM order, and its result is permuted straight into Phi's rows.
 static Tensor contract_upper(Ctx &c, const Tensor &E, const Tensor &F, const Tensor &I_,
                              const Tensor &J_, const Tensor &M2, const Tensor &M3,
                              const Tensor &M4) {
@@ -669,20 +850,37 @@ static Tensor contract_upper(Ctx &c, const Tensor &E, const Tensor &F, const Ten
   Tensor IM2 = contract(c, "bck,bBm->ckBm", I_, M2);              // (c kA B k2)
   Tensor JM3 = contract(c, "BCl,cCn->Blcn", J_, M3);              // (B kX c k3)
   Tensor Theta = contract(c, "ckBm,Blcn->klmn", IM2, JM3);        // (kA kX k2 k3)
+  Tensor Fg = permuted(c, F, {0, 2, 1, 3});                       // (al q4 kX g)
   const int64_t ts = t_slice(kt, E.dims[1] * M4.dims[2] * F.dims[1] * kr);
+  // every slice reuses F and Theta as B operands: their digit planes are split once
+  PlaneScope ps(c);
+  {
+    const int64_t kA = E.dims[1], k4 = M4.dims[2], kX = F.dims[1];
+    const int64_t alq = F.dims[0] * F.dims[2];
+    ps.share(Fg.p, false, false, ts * kA * k4, kX * kr, alq, kX * kr);
+    ps.share(Theta.p, false, false, ts * k4 * kr, Theta.dims[2] * Theta.dims[3], kA * kX,
+             Theta.dims[2] * Theta.dims[3]);
+  }
   for (int64_t t0 = 0; t0 < kt; t0 += ts) {
     const int64_t tn = std::min(ts, kt - t0);
     Arena::Mark ms = c.arena.mark();
     Tensor Es = view(E.p + t0 * e_t, {tn, E.dims[1], E.dims[2], E.dims[3]});
-    Tensor EM = contract(c, "tkda,dDm->tkamD", Es, M4);           // (t kA al k4 q4)
-    Tensor Phi1 = contract(c, "tkamD,alDg->tkmlg", EM, F);        // (t kA k4 kX g)
-    Tensor r = contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta);     // (t k2 k3 k4 g)
-    TRG_CUDA(cudaMemcpyAsync(out.p + t0 * out_t, r.p, r.size() * 8, cudaMemcpyDeviceToDevice,
-                             c.stream));
+    Tensor EM = contract(c, "tkda,dDm->tkmaD", Es, M4);           // (t kA k4 al q4)
+    Tensor Phi1 = contract(c, "tkmaD,aDlg->tkmlg", EM, Fg);       // (t kA k4 kX g)
+    Tensor dst = view(out.p + t0 * out_t, {tn, out.dims[1], out.dims[2], out.dims[3], kr});
+    contract(c, "tkmlg,klKL->tKLmg", Phi1, Theta, &dst);          // (t k2 k3 k4 g)
     c.arena.release(ms);
   }
   c.arena.release(mk);
   return out;
+}
+
+// Theta of the lower block in the order (kD kY k2' k3') that the slices' GEMMs read
+static Tensor theta_lower(Ctx &c, const Tensor &K_, const Tensor &L_, const Tensor &N2,
+                          const Tensor &N3) {
+  Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);              // (c kY B k2)
+  Tensor LN3 = contract(c, "BCl,cCn->Blcn", L_, N3);              // (B kD c k3)
+  return contract(c, "ckBm,Blcn->lkmn", KN2, LN3);                // (kD kY k2 k3)
 }
 
 // Psi (eq. makeMH), sliced over its first leg w
@@ -693,19 +891,60 @@ static Tensor contract_lower(Ctx &c, const Tensor &G, const Tensor &H, const Ten
   Tensor out = c.alloc({kt, N2.dims[2], N3.dims[2], N4.dims[2], kr});
   const int64_t out_t = out.size() / kt, h_t = H.size() / kt;
   Arena::Mark mk = c.arena.mark();
-  Tensor KN2 = contract(c, "bck,bBm->ckBm", K_, N2);              // (c kY B k2)
-  Tensor LN3 = contract(c, "BCl,cCn->Blcn", L_, N3);              // (B kD c k3)
-  Tensor Theta = contract(c, "ckBm,Blcn->klmn", KN2, LN3);        // (kY kD k2 k3)
+  Tensor ThetaT = theta_lower(c, K_, L_, N2, N3);                 // (kD kY k2 k3)
+  Tensor Gg = permuted(c, G, {0, 2, 1, 3});                       // (be P4 kY g)
   const int64_t ts = t_slice(kt, H.dims[1] * N4.dims[2] * G.dims[1] * kr);
+  PlaneScope ps(c);
+  {
+    const int64_t kD = H.dims[1], k4 = N4.dims[2], kY = G.dims[1];
+    const int64_t beq = G.dims[0] * G.dims[2];
+    ps.share(Gg.p, false, false, ts * kD * k4, kY * kr, beq, kY * kr);
+    ps.share(ThetaT.p, false, false, ts * k4 * kr, ThetaT.dims[2] * ThetaT.dims[3], kD * kY,
+             ThetaT.dims[2] * ThetaT.dims[3]);
+  }
   for (int64_t t0 = 0; t0 < kt; t0 += ts) {
     const int64_t tn = std::min(ts, kt - t0);
     Arena::Mark ms = c.arena.mark();
     Tensor Hs = view(H.p + t0 * h_t, {tn, H.dims[1], H.dims[2], H.dims[3]});
-    Tensor HN = contract(c, "wkdb,Ddm->wkbmD", Hs, N4);           // (w kD be k4 P4)
-    Tensor Psi1 = contract(c, "wkbmD,bjDg->wkmjg", HN, G);        // (w kD k4 kY g)
-    Tensor r = contract(c, "wkmjg,jkKL->wKLmg", Psi1, Theta);     // (w k2 k3 k4 g)
-    TRG_CUDA(cudaMemcpyAsync(out.p + t0 * out_t, r.p, r.size() * 8, cudaMemcpyDeviceToDevice,
-                             c.stream));
+    Tensor HN = contract(c, "wkdb,Ddm->wkmbD", Hs, N4);           // (w kD k4 be P4)
+    Tensor Psi1 = contract(c, "wkmbD,bDjg->wkmjg", HN, Gg);       // (w kD k4 kY g)
+    Tensor dst = view(out.p + t0 * out_t, {tn, out.dims[1], out.dims[2], out.dims[3], kr});
+    contract(c, "wkmjg,kjKL->wKLmg", Psi1, ThetaT, &dst);         // (w k2 k3 k4 g)
+    c.arena.release(ms);
+  }
+  c.arena.release(mk);
+  return out;
+}
+
+// w (Psi(G1, H1) + Psi(G2, H2)) in one pass (eq. makeMH is linear in each of G and H):
+// per slice the two first contractions accumulate into one Psi1, so the second
+// contraction with Theta (the larger GEMM of the chain) runs once
+static Tensor contract_lower_sum(Ctx &c, const Tensor &G1, const Tensor &H1, const Tensor &G2,
+                                 const Tensor &H2, const Tensor &K_, const Tensor &L_,
+                                 const Tensor &N2, const Tensor &N3, const Tensor &N4,
+                                 double w) {
+  const int64_t kt = H1.dims[0], kr = G1.dims[3];
+  Tensor out = c.alloc({kt, N2.dims[2], N3.dims[2], N4.dims[2], kr});
+  const int64_t out_t = out.size() / kt, h_t = H1.size() / kt;
+  Arena::Mark mk = c.arena.mark();
+  Tensor ThetaT = theta_lower(c, K_, L_, N2, N3);                 // (kD kY k2 k3)
+  axpby(ThetaT.p, ThetaT.p, w, 0.0, ThetaT.size(), c.stream);     // w folded into Theta
+  Tensor G1g = permuted(c, G1, {0, 2, 1, 3}), G2g = permuted(c, G2, {0, 2, 1, 3});
+  const int64_t ts = t_slice(kt, H1.dims[1] * N4.dims[2] * G1.dims[1] * kr);
+  for (int64_t t0 = 0; t0 < kt; t0 += ts) {
+    const int64_t tn = std::min(ts, kt - t0);
+    Arena::Mark ms = c.arena.mark();
+    Tensor H1s = view(H1.p + t0 * h_t, {tn, H1.dims[1], H1.dims[2], H1.dims[3]});
+    Tensor H2s = view(H2.p + t0 * h_t, {tn, H2.dims[1], H2.dims[2], H2.dims[3]});
+    Tensor Psi1 = contract(c, "wkmbD,bDjg->wkmjg", contract(c, "wkdb,Ddm->wkmbD", H1s, N4), G1g);
+    {
+      Arena::Mark m2 = c.arena.mark();
+      contract(c, "wkmbD,bDjg->wkmjg", contract(c, "wkdb,Ddm->wkmbD", H2s, N4), G2g, &Psi1,
+               1.0);
+      c.arena.release(m2);
+    }
+    Tensor dst = view(out.p + t0 * out_t, {tn, out.dims[1], out.dims[2], out.dims[3], kr});
+    contract(c, "wkmjg,kjKL->wKLmg", Psi1, ThetaT, &dst);         // (w k2 k3 k4 g)
     c.arena.release(ms);
   }
   c.arena.release(mk);
@@ -732,66 +971,162 @@ static void replace_state(double *&dst, int64_t old_size, const Tensor &src, cud
 
 // bring the slot of physical `axis` to the front, keeping the cyclic leg order
 static void rotate(Ctx &c, int axis) {
+  const int d = c.d;
   int slot = -1;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < d; ++i)
     if (c.axes[i] == axis) slot = i;
   if (slot < 0) throw Error(TRG_ERR_ARG, "axis out of range");
   if (slot == 0) return;
-  std::vector<int> perm = {slot, (slot + 1) % 4, (slot + 2) % 4, (slot + 3) % 4, 4};
+  std::vector<int> perm(d + 1);
+  for (int i = 0; i < d; ++i) perm[i] = (slot + i) % d;
+  perm[d] = d;
   for (double **buf : {&c.phi, &c.psi, &c.psi_imp}) {
     if (!*buf) continue;
     Tensor t = permuted(c, view(*buf, c.dims), perm);
     TRG_CUDA(cudaMemcpyAsync(*buf, t.p, t.size() * sizeof(double), cudaMemcpyDeviceToDevice,
                              c.stream));
   }
-  std::vector<int64_t> nd(5);
-  int na[4];
-  for (int i = 0; i < 5; ++i) nd[i] = c.dims[perm[i]];
-  for (int i = 0; i < 4; ++i) na[i] = c.axes[perm[i]];
+  std::vector<int64_t> nd(d + 1);
+  int na[4] = {-1, -1, -1, -1};
+  for (int i = 0; i <= d; ++i) nd[i] = c.dims[perm[i]];
+  for (int i = 0; i < d; ++i) na[i] = c.axes[perm[i]];
   c.dims = nd;
   std::memcpy(c.axes, na, sizeof(na));
 }
 
-// ----------------------------------------------------------------------- the step
-static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
+// (a) of the step, shared by the 3D and 4D triad steps: re-split T = Phi Psi^T =
+// A s D^T (eq. ABCD; SVD of T) of the current state, A and Dm as (legs, k)
+struct Resplit {
+  Tensor A, Dm, sv;
+  int64_t k = 0, Db = 0;
+};
+static Resplit resplit(Ctx &c, int64_t D) {
   cudaStream_t s = c.stream;
-  c.mark(0);
-  rotate(c, axis);
-  const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], d4 = c.dims[3], r = c.dims[4];
-  const int64_t Nf = d1 * d2 * d3 * d4;
-  const int n = c.nsteps;
-  // mixed forms: tensor cores from the fourth step on; the first three steps carry
-  // weights 1, 1/2, 1/4 of the free energy and have small legs, so they stay in FP64
-  c.mixed_now = c.precision != TRG_PREC_FP64 && n >= 3;
-  auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
-
-  // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
+  const int64_t r = c.dims.back(), Nf = prod(c.dims) / r;
   Tensor P2 = view(c.phi, {Nf, r}), S2 = view(c.psi, {Nf, r});
-  std::unique_ptr<Crit> crit_resplit(new Crit(c));
+  Crit crit_resplit(c);
+  Resplit out;
   // the bond lines (re-split alpha/beta, swapped gamma) keep Db = r_bond D values; the
   // ILO form (Sec. II C, Appendix A) has r_bond > 1, the pair legs stay at D
   const int64_t Db = D * c.r_bond;
   const int64_t k = std::min<int64_t>(Db, r);
+  out.Db = Db;
+  out.k = k;
   // only A, D and s outlive the re-split (its orthonormal factors are released)
   Tensor A = c.alloc({Nf, k}), Dm = c.alloc({Nf, k}), svT = c.alloc({r});
   {
     Arena::Mark mk = c.arena.mark();
-    auto [Qp, Rp] = orth_qr(c, P2);
-    auto [Qs, Rs] = orth_qr(c, S2);
-    Svd rs = svd_small(c, mm(c, Rp, Rs, false, true));
-    gemm(c, false, false, Nf, k, r, 1.0, Qp.p, r, 0, rs.U.p, r, 0, 0.0, A.p, k, 0, 1);
-    gemm(c, false, false, Nf, k, r, 1.0, Qs.p, r, 0, rs.V.p, r, 0, 0.0, Dm.p, k, 0, 1);
+    FoldedQR fp = orth_qr_folded(c, P2), fs = orth_qr_folded(c, S2);
+    Svd rs = svd_small(c, mm(c, fp.R, fs.R, false, true));
+    // A = Q_Phi U[:, :k] = Q2_Phi (Ri3_Phi U[:, :k]), D likewise with V
+    Tensor Wp = c.alloc({r, k}), Ws = c.alloc({r, k});
+    gemm(c, false, false, r, k, r, 1.0, fp.Ri3.p, r, 0, rs.U.p, r, 0, 0.0, Wp.p, k, 0, 1);
+    gemm(c, false, false, r, k, r, 1.0, fs.Ri3.p, r, 0, rs.V.p, r, 0, 0.0, Ws.p, k, 0, 1);
+    gemm(c, false, false, Nf, k, r, 1.0, fp.Q2.p, r, 0, Wp.p, k, 0, 0.0, A.p, k, 0, 1);
+    gemm(c, false, false, Nf, k, r, 1.0, fs.Q2.p, r, 0, Ws.p, k, 0, 0.0, Dm.p, k, 0, 1);
     TRG_CUDA(cudaMemcpyAsync(svT.p, rs.S.p, r * sizeof(double), cudaMemcpyDeviceToDevice, s));
     c.arena.release(mk);
   }
   sign_gauge(A.p, Nf, Dm.p, Nf, k, s);
-  double *sv = svT.p;  // first k entries used
-  kill_dead(sv, k, kRankTol, A.p, Nf, Dm.p, Nf, s);
-  A.dims = {d1, d2, d3, d4, k};
-  Dm.dims = {d1, d2, d3, d4, k};
-  crit_resplit.reset();
+  kill_dead(svT.p, k, kRankTol, A.p, Nf, Dm.p, Nf, s);
+  out.A = A;
+  out.Dm = Dm;
+  out.sv = svT;
+  return out;
+}
 
-  c.mark(1);
+// (c) of the step, shared by the 3D and 4D triad steps: the four triad isometries U^A,
+// U^X, U^Y, U^D (eq. HOSVD), ranges of width chi of rho = F F^T over the leg pair
+// (d2, d3).  src[i] holds the tensor whose permutation `perm` (pair legs first) is the
+// factor F_i, or, with W[i] given, the tensor T with F_i = perm(T R^T), R^T R = W[i].
+// With the plain Gaussian sketch and no row collection, factors of one shape run their
+// range finders as one batch; otherwise each runs range_factor_full (learned sketch,
+// collection).  chi >= pair dimension: the identity.
+static std::vector<Tensor> triad_isometries(Ctx &c, const Tensor *src[4], const Tensor *W[4],
+                                            const std::vector<int> &perm, int64_t d2,
+                                            int64_t d3, int64_t chi, int n) {
+  const int64_t npair = d2 * d3;
+  const int tags[4] = {TAG_RHO_A, TAG_RHO_X, TAG_RHO_Y, TAG_RHO_D};
+  auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
+  std::vector<Tensor> U(4);
+  for (int i = 0; i < 4; ++i) {
+    U[i] = c.alloc({npair, std::min(chi, npair)});
+    if (chi >= npair) fill_identity(U[i].p, npair, npair, c.stream);
+  }
+  if (chi < npair) {
+    Arena::Mark mk = c.arena.mark();
+    // the factor of isometry i, written to dst (npair x m_i)
+    auto write_factor = [&](int i, double *dst) {
+      const Tensor &T = *src[i];
+      Arena::Mark m2 = c.arena.mark();
+      Tensor TT = T;
+      if (W[i]) {
+        const int64_t k = T.dims.back(), rows = T.size() / k;
+        Tensor R = c.alloc({k, k}), Ri = c.alloc({k, k});
+        chol_rinv(W[i]->p, R.p, Ri.p, (int)k, 1, kPivotTol, 0.0, c.stream);
+        TT = mm(c, view(T.p, {rows, k}), R, false, true);
+        TT.dims = T.dims;
+      }
+      permute(TT.p, dst, TT.dims, perm, c.stream);
+      c.arena.release(m2);
+    };
+    const bool batchable = c.sketch_mode == 0 && c.col_cap == 0;
+    std::vector<bool> done(4, false);
+    for (int i = 0; i < 4 && batchable; ++i) {
+      if (done[i]) continue;
+      const int64_t mi = src[i]->size() / npair;
+      // a batch member holds its factor (8 B per value) and digit planes of both
+      // orientations (up to 2 x 5 x 2 B per value): at most 24 GB of them at once
+      const int64_t per = npair * mi * 28;
+      const int64_t max_grp = std::max<int64_t>(1, (int64_t(24) << 30) / per);
+      std::vector<int> grp;
+      for (int j = i; j < 4 && (int64_t)grp.size() < max_grp; ++j)
+        if (!done[j] && src[j]->size() / npair == mi) grp.push_back(j);
+      Arena::Mark mg = c.arena.mark();
+      const int64_t nb = (int64_t)grp.size();
+      Tensor Fs = c.alloc({nb, npair, mi});
+      std::vector<uint64_t> keys;
+      for (int64_t b = 0; b < nb; ++b) {
+        write_factor(grp[b], Fs.p + b * npair * mi);
+        keys.push_back(key(tags[grp[b]]));
+      }
+      Tensor Q = rsvd_factor_batched(c, Fs, chi, c.q_rho, keys);
+      for (int64_t b = 0; b < nb; ++b) {
+        TRG_CUDA(cudaMemcpyAsync(U[grp[b]].p, Q.p + b * npair * chi, npair * chi * 8,
+                                 cudaMemcpyDeviceToDevice, c.stream));
+        done[grp[b]] = true;
+      }
+      c.arena.release(mg);
+    }
+    for (int i = 0; i < 4; ++i) {
+      if (done[i]) continue;
+      Arena::Mark m2 = c.arena.mark();
+      const int64_t mi = src[i]->size() / npair;
+      Tensor F = c.alloc({npair, mi});
+      write_factor(i, F.p);
+      Tensor Q = range_factor_full(c, F, d2, d3, chi, c.q_rho, key(tags[i]),
+                                   key(TAG_PROBE_A + tags[i] - TAG_RHO_A));
+      TRG_CUDA(cudaMemcpyAsync(U[i].p, Q.p, npair * chi * 8, cudaMemcpyDeviceToDevice,
+                               c.stream));
+      c.arena.release(m2);
+    }
+    c.arena.release(mk);
+  }
+  for (auto &u : U) u.dims = {d2, d3, u.dims[1]};
+  return U;
+}
+
+// (b) of the step, shared by the 3D and 4D triad steps: the bond swap
+//     sum_x C[x I be] B[x J al] ~ X sigma Y of the re-split factors A (x, I, k) and
+//     Dm (x, J, k) with singular values sv; returns X (k, I, Dg), Y (k, J, Dg), sigma
+//     (w values, the first Dg kept) and the relative gap at the cut.
+struct SwapOut {
+  Tensor X, Y, sig;
+  int64_t Dg = 0;
+  double gap = INFINITY;
+};
+static SwapOut bond_swap(Ctx &c, const Tensor &A, const Tensor &Dm, const double *sv, int64_t k,
+                         int64_t x, int64_t I, int64_t Db, int64_t p, int n) {
   // (b) bond swap: M[(I al),(J be)] = sum_x C[x I be] B[x J al] ~ X sigma Y (Appendix A).
   //     The randomized SVD of M runs in the compressed space of Appendix A, written in
   //     Gram coordinates: a left vector is Y = (C (x) 1) Y' and a right vector
@@ -801,13 +1136,19 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   //         Y^T Y = Y'^T (G^C (x) 1) Y',        V^T V = W^T (G^B (x) 1) W,
   //     with P the swap of the two bond legs.  Only the two Grams and the final
   //     X = (C (x) 1) X', Y = (B (x) 1) Y' cost D^7; the power rounds cost D^6.
-  const int64_t x = d1, I = d2 * d3 * d4, J = I;
+  cudaStream_t s = c.stream;
+  auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
+  const int64_t J = I;
   const int64_t w = std::min<int64_t>(Db + p, k * I);
   const int64_t xk = x * k, rows = x * k * k;     // coordinate rows (x, leg, leg)
   const int64_t Dg = std::min<int64_t>(Db, w);
-  Tensor X = c.alloc({k, d2, d3, d4, Dg}), Y = c.alloc({k, d2, d3, d4, Dg});
-  Tensor sigT = c.alloc({w});
-  double *sig = sigT.p;
+  SwapOut out;
+  out.Dg = Dg;
+  out.X = c.alloc({k, I, Dg});
+  out.Y = c.alloc({k, I, Dg});
+  out.sig = c.alloc({w});
+  Tensor &X = out.X, &Y = out.Y;
+  double *sig = out.sig.p;
   Arena::Mark mk_swap = c.arena.mark();
   Tensor C = copy(c, A), B = copy(c, Dm);         // C = A s, B = D s (released after)
   scale_last(c, C, sv);
@@ -819,7 +1160,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     // the compression Grams square the spectra of C and B: more digits (or FP64)
     const int gd = c.swap_gram_digits;
     if (gd >= 64) ++c.ortho;
-    else if (c.precision >= TRG_PREC_OZ4) c.digits_override = std::max(gd, c.precision);
+    else if (is_digit_form(c.precision)) c.digits_override = std::max(gd, digits_of(c.precision));
     gemm(c, false, true, xk, xk, I, 1.0, Cq.p, I, 0, Cq.p, I, 0, 0.0, GC.p, xk, 0, 1);
     gemm(c, false, true, xk, xk, J, 1.0, Bq.p, J, 0, Bq.p, J, 0, 0.0, GB.p, xk, 0, 1);
     if (gd >= 64) --c.ortho;
@@ -921,7 +1262,7 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     c.arena.release(mk);
   }
   crit_core.reset();
-  double gap_swap = INFINITY;
+  double &gap_swap = out.gap;
   {
     std::vector<double> hs(w);
     TRG_CUDA(cudaMemcpyAsync(hs.data(), cs.S.p, w * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -929,6 +1270,82 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
     if (w > Dg && hs[Dg - 1] > 0) gap_swap = (hs[Dg - 1] - hs[Dg]) / hs[Dg - 1];
   }
   c.arena.release(mk_swap);
+  return out;
+}
+
+// (g) of the step, shared by the 3D and 4D triad steps: normalisation c_n = ||T||_F,
+// Psi /= c_n, ln Z bookkeeping, the new state, and the step's status read back
+static void finish_step(Ctx &c, Tensor &PhiN, Tensor &PsiN, Tensor &PsiImpN, int n, double gap) {
+  c.mark(7);
+  // normalisation c_n = ||T||_F and ln Z bookkeeping
+  Crit crit_norm(c);
+  cudaStream_t s = c.stream;
+  const int64_t rn = PhiN.dims.back(), Nn = PhiN.size() / rn;
+  Tensor Gp = mm(c, view(PhiN.p, {Nn, rn}), view(PhiN.p, {Nn, rn}), true, false);
+  Tensor Gs = mm(c, view(PsiN.p, {Nn, rn}), view(PsiN.p, {Nn, rn}), true, false);
+  dot(Gp.p, Gs.p, rn * rn, c.dscal + 2, c.scratch(), s);
+  norm_update(c.dscal + 2, c.dscal + 1, c.dscal + 0, std::ldexp(1.0, -(n + 1)), c.dflag, s);
+  scale_by_scalar(PsiN.p, PsiN.size(), c.dscal + 1, 1, s);
+  if (c.have_imp) scale_by_scalar(PsiImpN.p, PsiImpN.size(), c.dscal + 1, 1, s);
+
+  const int64_t old_size = prod(c.dims);
+  replace_state(c.phi, old_size, PhiN, s);
+  replace_state(c.psi, old_size, PsiN, s);
+  if (c.have_imp) replace_state(c.psi_imp, old_size, PsiImpN, s);
+  c.dims = PhiN.dims;
+  c.nsteps = n + 1;
+  if (c.imp_pair == 1) c.imp_pair = 2;
+  double hc = 1.0;
+  int flag = 0;
+  TRG_CUDA(cudaMemcpyAsync(&hc, c.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRG_CUDA(cudaMemcpyAsync(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  c.mark(8);
+  TRG_CUDA(cudaStreamSynchronize(s));
+  c.collect_tc();
+  for (int i = 0; i < Ctx::kPhases; ++i) {
+    float ms = 0.f;
+    TRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
+    c.phase_ms[i] = ms;
+  }
+  c.last_logc = std::log(hc);
+  c.last_gap = gap;
+  c.arena.reset();
+  if (flag) throw Error(flag, "non-finite norm in the coarse-graining step");
+  if (linalg_error_flag(true))
+    throw Error(TRG_ERR_TIMEOUT, "grid barrier of the cooperative Jacobi SVD timed out");
+  if (c.mixed_now && (tc_error_flag(true) | oz_error_flag(true)))
+    throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
+}
+
+// ----------------------------------------------------------------------- the step
+static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
+  cudaStream_t s = c.stream;
+  c.mark(0);
+  rotate(c, axis);
+  const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], d4 = c.dims[3], r = c.dims[4];
+  const int64_t Nf = d1 * d2 * d3 * d4;
+  const int n = c.nsteps;
+  // mixed forms: tensor cores from the fourth step on; the first three steps carry
+  // weights 1, 1/2, 1/4 of the free energy and have small legs, so they stay in FP64
+  c.mixed_now = c.precision != TRG_PREC_FP64 && n >= 3;
+  auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
+
+  // (a) re-split T = Phi Psi^T = A s D^T (eq. ABCD; SVD of T)
+  Resplit rsp = resplit(c, D);
+  const int64_t Db = rsp.Db, k = rsp.k;
+  Tensor A = rsp.A, Dm = rsp.Dm;
+  double *sv = rsp.sv.p;  // first k entries used
+  A.dims = {d1, d2, d3, d4, k};
+  Dm.dims = {d1, d2, d3, d4, k};
+
+  c.mark(1);
+  SwapOut sw = bond_swap(c, A, Dm, sv, k, d1, d2 * d3 * d4, Db, p, n);
+  const int64_t x = d1, I = d2 * d3 * d4, J = I, Dg = sw.Dg;
+  Tensor X = sw.X, Y = sw.Y;
+  X.dims = {k, d2, d3, d4, Dg};
+  Y.dims = {k, d2, d3, d4, Dg};
+  double *sig = sw.sig.p;
+  const double gap_swap = sw.gap;
 
   c.mark(2);
   // (c) triad isometries from the canonical-form Grams (eq. HOSVD)
@@ -939,32 +1356,18 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
   Tensor Wbe = mm(c, view(Ys.p, {k, J * Dg}), view(Ys.p, {k, J * Dg}), false, true);
   const int64_t npair = d2 * d3;
   const int64_t chi = std::min<int64_t>(D + p, npair);
+  // rho = F F^T for each of the four; the range finders run on the factors F
+  // (rho^X: Xs over (al, q4, g); rho^Y: Ys; rho^A = A W_al A^T: F = A R^T with
+  // R^T R = W_al; rho^D likewise with W_be)
   Tensor UA, UX, UY, UD;
   {
-    // rho = F F^T for each of the four; the range finders run on the factors F
-    // (rho^X: Xs over (al, q4, g); rho^Y: Ys; rho^A = A W_al A^T: F = A R^T with
-    // R^T R = W_al; rho^D likewise with W_be).  chi >= pair dimension: identity.
-    auto factor_w = [&](const Tensor &T, const Tensor &W) {   // T (t b c d a), W (a a')
-      Tensor R = c.alloc({k, k}), Ri = c.alloc({k, k});
-      chol_rinv(W.p, R.p, Ri.p, (int)k, 1, kPivotTol, 0.0, s);
-      Tensor TR = mm(c, view(T.p, {Nf, k}), R, false, true);  // (t b c d l)
-      TR.dims = {d1, d2, d3, d4, k};
-      return permuted(c, TR, {1, 2, 0, 3, 4});
-    };
-    auto range = [&](int tag, auto &&make_factor) {
-      Tensor U = keep(c, {npair, std::min(chi, npair)}, [&] {
-        if (chi >= npair) return identity(c, npair);
-        Tensor F = make_factor();
-        return range_factor_full(c, view(F.p, {npair, F.size() / npair}), d2, d3, chi,
-                                 c.q_rho, key(tag), key(TAG_PROBE_A + tag - TAG_RHO_A));
-      });
-      U.dims = {d2, d3, U.dims[1]};
-      return U;
-    };
-    UA = range(TAG_RHO_A, [&] { return factor_w(A, Wal); });
-    UX = range(TAG_RHO_X, [&] { return permuted(c, Xs, {1, 2, 0, 3, 4}); });
-    UY = range(TAG_RHO_Y, [&] { return permuted(c, Ys, {1, 2, 0, 3, 4}); });
-    UD = range(TAG_RHO_D, [&] { return factor_w(Dm, Wbe); });
+    const Tensor *src[4] = {&A, &Xs, &Ys, &Dm};
+    const Tensor *Ws[4] = {&Wal, nullptr, nullptr, &Wbe};
+    std::vector<Tensor> U = triad_isometries(c, src, Ws, {1, 2, 0, 3, 4}, d2, d3, chi, n);
+    UA = U[0];
+    UX = U[1];
+    UY = U[2];
+    UD = U[3];
   }
 
   c.mark(3);
@@ -1082,59 +1485,171 @@ static void step_impl(Ctx &c, int axis, int64_t D, int64_t p) {
       PsiImpN = contract_lower(c, Gimp, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
     } else {
       // one impurity, at slot n+1 or at slot n with equal weight
-      PsiImpN = contract_lower(c, Gimp, H, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
-      Tensor Pb = contract_lower(c, G, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4]);
-      axpby(PsiImpN.p, Pb.p, 0.5, 0.5, PsiImpN.size(), s);
+      PsiImpN = contract_lower_sum(c, Gimp, H, G, Himp, K_, L_, Nsq[2], Nsq[3], Nsq[4], 0.5);
     }
   }
 
-  c.mark(7);
-  // normalisation c_n = ||T||_F and ln Z bookkeeping
-  Crit crit_norm(c);
-  const int64_t rn = PhiN.dims[4], Nn = PhiN.size() / rn;
-  Tensor Gp = mm(c, view(PhiN.p, {Nn, rn}), view(PhiN.p, {Nn, rn}), true, false);
-  Tensor Gs = mm(c, view(PsiN.p, {Nn, rn}), view(PsiN.p, {Nn, rn}), true, false);
-  dot(Gp.p, Gs.p, rn * rn, c.dscal + 2, c.scratch(), s);
-  norm_update(c.dscal + 2, c.dscal + 1, c.dscal + 0, std::ldexp(1.0, -(n + 1)), c.dflag, s);
-  scale_by_scalar(PsiN.p, PsiN.size(), c.dscal + 1, 1, s);
-  if (c.have_imp) scale_by_scalar(PsiImpN.p, PsiImpN.size(), c.dscal + 1, 1, s);
+  finish_step(c, PhiN, PsiN, PsiImpN, n, std::min(gap_swap, gap_sq));
+}
 
-  const int64_t old_size = prod(c.dims);
-  replace_state(c.phi, old_size, PhiN, s);
-  replace_state(c.psi, old_size, PsiN, s);
-  if (c.have_imp) replace_state(c.psi_imp, old_size, PsiImpN, s);
-  c.dims = PhiN.dims;
-  c.nsteps = n + 1;
-  if (c.imp_pair == 1) c.imp_pair = 2;
-  double hc = 1.0;
-  int flag = 0;
-  TRG_CUDA(cudaMemcpyAsync(&hc, c.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-  TRG_CUDA(cudaMemcpyAsync(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  c.mark(8);
-  TRG_CUDA(cudaStreamSynchronize(s));
-  c.collect_tc();
-  for (int i = 0; i < Ctx::kPhases; ++i) {
-    float ms = 0.f;
-    TRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
-    c.phase_ms[i] = ms;
+// ------------------------------------------------------------- the step in three dimensions
+// The triad step for d = 3 (the case the paper costs at O(r^2 D^6), end of Sec. II B): the
+// state is Phi (i1, i2, i3, g) and Psi (j1, j2, j3, g).  Re-split, bond swap and
+// normalisation are the 4D step's; the pair (i2, i3) of each of A, X, Y, D is compressed
+// by a triad isometry (ranges of the canonical-form Grams of eq. HOSVD); the triads are
+// E (t, kA, al), F (al, kX, g), G (be, kY, g), H (w, kD, be); two squeezers (mu = 2, 3)
+// come from the block environments; Phi = (E F)(I J M2 M3), Psi = (H G)(K L N2 N3).
+static void step3_impl(Ctx &c, int axis, int64_t D, int64_t p) {
+  cudaStream_t s = c.stream;
+  c.mark(0);
+  rotate(c, axis);
+  const int64_t d1 = c.dims[0], d2 = c.dims[1], d3 = c.dims[2], r = c.dims[3];
+  const int64_t Nf = d1 * d2 * d3;
+  const int n = c.nsteps;
+  c.mixed_now = c.precision != TRG_PREC_FP64 && n >= 3;
+  auto key = [&](int tag) { return sketch_key(c.seed, n, tag); };
+
+  Resplit rsp = resplit(c, D);
+  const int64_t Db = rsp.Db, k = rsp.k;
+  Tensor A = rsp.A, Dm = rsp.Dm;
+  double *sv = rsp.sv.p;
+  A.dims = {d1, d2, d3, k};
+  Dm.dims = {d1, d2, d3, k};
+
+  c.mark(1);
+  SwapOut sw = bond_swap(c, A, Dm, sv, k, d1, d2 * d3, Db, p, n);
+  const int64_t x = d1, I = d2 * d3, Dg = sw.Dg;
+  Tensor X = sw.X, Y = sw.Y;
+  X.dims = {k, d2, d3, Dg};
+  Y.dims = {k, d2, d3, Dg};
+  double *sig = sw.sig.p;
+
+  c.mark(2);
+  // (c) triad isometries from the canonical-form Grams (eq. HOSVD), range finders on the
+  // factors F with rho = F F^T, as in 4D
+  Tensor Xs = copy(c, X), Ys = copy(c, Y);
+  scale_last(c, Xs, sig);
+  scale_last(c, Ys, sig);
+  Tensor Wal = mm(c, view(Xs.p, {k, I * Dg}), view(Xs.p, {k, I * Dg}), false, true);
+  Tensor Wbe = mm(c, view(Ys.p, {k, I * Dg}), view(Ys.p, {k, I * Dg}), false, true);
+  const int64_t npair = d2 * d3;
+  const int64_t chi = std::min<int64_t>(D + p, npair);
+  Tensor UA, UX, UY, UD;
+  {
+    const Tensor *src[4] = {&A, &Xs, &Ys, &Dm};
+    const Tensor *Ws[4] = {&Wal, nullptr, nullptr, &Wbe};
+    std::vector<Tensor> U = triad_isometries(c, src, Ws, {1, 2, 0, 3}, d2, d3, chi, n);
+    UA = U[0];
+    UX = U[1];
+    UY = U[2];
+    UD = U[3];
   }
-  c.last_logc = std::log(hc);
-  c.last_gap = std::min(gap_swap, gap_sq);
-  c.arena.reset();
-  if (flag) throw Error(flag, "non-finite norm in the coarse-graining step");
-  if (linalg_error_flag(true))
-    throw Error(TRG_ERR_TIMEOUT, "grid barrier of the cooperative Jacobi SVD timed out");
-  if (c.mixed_now && (tc_error_flag(true) | oz_error_flag(true)))
-    throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
+
+  c.mark(3);
+  // (d) triads
+  Tensor E = contract(c, "tbca,bck->tka", A, UA);
+  Tensor F = contract(c, "abcg,bck->akg", X, UX);
+  scale_last(c, F, sig);
+  Tensor G = contract(c, "bPQg,PQk->bkg", Y, UY);
+  Tensor H = contract(c, "wPQb,PQk->wkb", Dm, UD);
+  const Tensor &I_ = UA, &J_ = UX, &K_ = UY, &L_ = UD;
+
+  // (e) Grams O (upper block E F I J) and P (lower block G H K L) on the bond gamma, the
+  // environments of the two pairs, squeezers
+  Tensor Ig = contract(c, "bck,bcl->kl", I_, I_), Jg = contract(c, "bck,bcl->kl", J_, J_);
+  Tensor Kg = contract(c, "bck,bcl->kl", K_, K_), Lg = contract(c, "bck,bcl->kl", L_, L_);
+  Tensor EEI = contract(c, "tla,tle->ae", contract(c, "tka,kl->tla", E, Ig), E);
+  Tensor O = contract(c, "akg,akh->gh", F,
+                      contract(c, "ae,ekh->akh", EEI, contract(c, "elh,kl->ekh", F, Jg)));
+  Tensor HHL = contract(c, "wlb,wle->be", contract(c, "wkb,kl->wlb", H, Lg), H);
+  Tensor Pm = contract(c, "bkg,bkh->gh", G,
+                       contract(c, "be,ekh->bkh", HHL, contract(c, "elh,kl->ekh", G, Kg)));
+  Tensor EE2 = contract(c, "tka,tle->kale", E, E);                          // (kA al kA' al')
+  Tensor FPF2 = contract(c, "akh,elh->akel", contract(c, "akg,gh->akh", F, Pm), F);
+  Tensor GOG2 = contract(c, "bkh,elh->kble", contract(c, "bkg,gh->bkh", G, O), G);
+  Tensor HH2 = contract(c, "wkb,wle->kble", H, H);                          // (kD be kD' be')
+  std::map<int, Tensor> rf, rb;
+  for (int mu : {2, 3}) {
+    const char *sub = mu == 2 ? "bck,Bcl->bkBl" : "cbk,cBl->bkBl";
+    Tensor II = contract(c, sub, I_, I_), JJ = contract(c, sub, J_, J_);
+    Tensor KK = contract(c, sub, K_, K_), LL = contract(c, sub, L_, L_);
+    rf[mu] = contract(c, "paPe,aqeQ->pqPQ", contract(c, "pkPl,kale->paPe", II, EE2),
+                      contract(c, "qkQl,akel->aqeQ", JJ, FPF2));
+    rb[mu] = contract(c, "PbRe,bQeS->PQRS", contract(c, "PkRl,kble->PbRe", KK, GOG2),
+                      contract(c, "QkSl,kble->bQeS", LL, HH2));
+  }
+  c.mark(4);
+  const int64_t dmu[4] = {0, 0, d2, d3};
+  std::map<int, Tensor> Msq, Nsq;
+  double gap_sq = INFINITY;
+  for (int mu : {2, 3}) {
+    const int64_t nn = dmu[mu] * dmu[mu];
+    double g;
+    auto [M, N] = squeezer(c, view(rf[mu].p, {nn, nn}), view(rb[mu].p, {nn, nn}), D,
+                           std::min<int64_t>(D + p, nn), c.q_rho, key(TAG_SQ_F2 + mu - 2),
+                           key(TAG_SQ_B2 + mu - 2), &g);
+    gap_sq = std::min(gap_sq, g);
+    M.dims = {dmu[mu], dmu[mu], M.dims[1]};
+    N.dims = {dmu[mu], dmu[mu], N.dims[1]};
+    Msq[mu] = M;
+    Nsq[mu] = N;
+  }
+
+  c.mark(5);
+  // (f) coarse contraction: Phi[t, k2, k3, g] = (E F)[t kA kX g] Theta_U[kA kX k2 k3]
+  auto theta = [&](const Tensor &P, const Tensor &Q, const Tensor &S2, const Tensor &S3) {
+    Tensor PS = contract(c, "bck,bBm->ckBm", P, S2);
+    Tensor QS = contract(c, "BCl,cCn->Blcn", Q, S3);
+    return contract(c, "ckBm,Blcn->klmn", PS, QS);
+  };
+  Tensor ThU = theta(I_, J_, Msq[2], Msq[3]);                                // (kA kX k2 k3)
+  Tensor ThL = theta(K_, L_, Nsq[2], Nsq[3]);                                // (kY kD k2 k3)
+  Tensor PhiN = contract(c, "tklg,klmn->tmng", contract(c, "tka,alg->tklg", E, F), ThU);
+  // Psi[w, k2', k3', g] = (H G)[w kD kY g] Theta_L[kY kD k2' k3']
+  auto lower = [&](const Tensor &Gx, const Tensor &Hx) {
+    return contract(c, "wlkg,klmn->wmng", contract(c, "wlb,bkg->wlkg", Hx, Gx), ThL);
+  };
+  Tensor PsiN = lower(G, H);
+
+  c.mark(6);
+  Tensor PsiImpN;
+  if (c.have_imp) {
+    Cheap ch(c);
+    // frozen pure projectors, as in 4D: slot n+1 gives B_imp = T_imp^T A and
+    // Y_imp = M_imp^T X / sigma; slot n gives D_imp = T_imp^T A s^+
+    Tensor PA = mm(c, view(c.phi, {Nf, r}), view(A.p, {Nf, k}), true, false);
+    Tensor Bimp = mm(c, view(c.psi_imp, {Nf, r}), PA, false, false);
+    Bimp.dims = {x, d2, d3, k};
+    Tensor CX = contract(c, "xIJb,aIJg->xbag", A, X);
+    scale_axis(CX.p, CX.size(), (int64_t)CX.dims[2] * CX.dims[3], k, sv, 0, nullptr, 0.0, s);
+    Tensor Ytil = contract(c, "xPQa,xbag->bPQg", Bimp, CX);
+    scale_last(c, Ytil, sig, 1, sig, 0.0);
+    Tensor Gimp = contract(c, "bPQg,PQk->bkg", Ytil, UY);
+    Tensor Dimp = copy(c, Bimp);
+    scale_last(c, Dimp, sv, 1, sv, 0.0);
+    Tensor Himp = contract(c, "wPQb,PQk->wkb", Dimp, UD);
+    if (c.imp_pair == 1) {
+      PsiImpN = lower(Gimp, Himp);
+    } else {
+      // (H G_imp + H_imp G) Theta_L / 2: the two slots share the Theta_L product
+      Tensor HG = contract(c, "wlb,bkg->wlkg", H, Gimp);
+      contract(c, "wlb,bkg->wlkg", Himp, G, &HG, 1.0);
+      axpby(HG.p, HG.p, 0.5, 0.0, HG.size(), s);
+      PsiImpN = contract(c, "wlkg,klmn->wmng", HG, ThL);
+    }
+  }
+  finish_step(c, PhiN, PsiN, PsiImpN, n, std::min(sw.gap, gap_sq));
 }
 
 // -------------------------------------------------------------------- init helpers
 static void ensure_ctx(Ctx &c) {
-  if (const char *e = getenv("TRG_DECOMP_FP64")) c.crit_fp64 = e[0] == '1';
-  if (const char *e = getenv("TRG_TC_PHASES")) c.phase_mask = (unsigned)strtoul(e, nullptr, 0);
-  if (const char *e = getenv("TRG_EXACT_EVERYWHERE")) c.cheap_policy = e[0] != '1';
-  if (const char *e = getenv("TRG_TC_MIN_MAX")) c.tc_min_max = atoll(e);
-  if (const char *e = getenv("TRG_SWAP_GRAM_DIGITS")) c.swap_gram_digits = atoi(e);
+  std::string e;
+  if (!(e = study_opt("decomp_fp64")).empty()) c.crit_fp64 = e[0] == '1';
+  if (!(e = study_opt("tc_phases")).empty()) c.phase_mask = (unsigned)strtoul(e.c_str(), nullptr, 0);
+  if (!(e = study_opt("exact_everywhere")).empty()) c.cheap_policy = e[0] != '1';
+  if (!(e = study_opt("tc_min_max")).empty()) c.tc_min_max = atoll(e.c_str());
+  if (!(e = study_opt("swap_gram_digits")).empty()) c.swap_gram_digits = atoi(e.c_str());
+  if (!(e = study_opt("decomp_cuda_fp64")).empty()) c.x7_policy = e[0] != '1';
   if (!c.dscal) {
     TRG_CUDA(cudaMalloc(&c.dscal, 512 * sizeof(double)));
     TRG_CUDA(cudaMalloc(&c.dflag, sizeof(int)));
@@ -1157,24 +1672,28 @@ static void free_state(Ctx &c) {
 
 // T0 from a CP factor W (rows: site states, columns: bond index), weights and observable
 static void init_cp(Ctx &c, double beta, const std::vector<double> &W, int nstate, int nb,
-                    const std::vector<double> &weight, const std::vector<double> &obs) {
+                    const std::vector<double> &weight, const std::vector<double> &obs,
+                    int d = 4) {
   ensure_ctx(c);
   TRG_CUDA(cudaStreamSynchronize(c.stream));
   free_state(c);
-  int64_t nf = (int64_t)nb * nb * nb * nb;
+  int64_t nf = 1;
+  for (int mu = 0; mu < d; ++mu) nf *= nb;
   std::vector<double> phi(nf * nstate), psi(nf * nstate), imp(nf * nstate);
   for (int64_t i = 0; i < nf; ++i) {
-    int64_t leg[4] = {i / (nb * nb * nb), (i / (nb * nb)) % nb, (i / nb) % nb, i % nb};
     for (int a = 0; a < nstate; ++a) {
       double v = 1.0;
-      for (int mu = 0; mu < 4; ++mu) v *= W[a * nb + leg[mu]];
+      int64_t rem = i;
+      for (int mu = d - 1; mu >= 0; --mu, rem /= nb) v *= W[a * nb + rem % nb];
       phi[i * nstate + a] = v;
       psi[i * nstate + a] = v * weight[a];
       imp[i * nstate + a] = v * weight[a] * obs[a];
     }
   }
-  c.dims = {nb, nb, nb, nb, nstate};
-  for (int i = 0; i < 4; ++i) c.axes[i] = i;
+  c.d = d;
+  c.dims.assign(d, nb);
+  c.dims.push_back(nstate);
+  for (int i = 0; i < 4; ++i) c.axes[i] = i < d ? i : -1;
   for (auto pr : {std::make_pair(&c.phi, &phi), std::make_pair(&c.psi, &psi),
                   std::make_pair(&c.psi_imp, &imp)}) {
     TRG_CUDA(cudaMalloc(pr.first, pr.second->size() * sizeof(double)));
@@ -1199,13 +1718,13 @@ static void init_cp(Ctx &c, double beta, const std::vector<double> &W, int nstat
   c.init = true;
 }
 
-static void init_ising_ctx(Ctx &c, double beta, double h) {
+static void init_ising_ctx(Ctx &c, double beta, double h, int d = 4) {
   double cb = std::sqrt(std::cosh(beta)), sb = std::sqrt(std::sinh(beta));
-  init_cp(c, beta, {cb, sb, cb, -sb}, 2, 2, {std::exp(h), std::exp(-h)}, {1.0, -1.0});
+  init_cp(c, beta, {cb, sb, cb, -sb}, 2, 2, {std::exp(h), std::exp(-h)}, {1.0, -1.0}, d);
   c.ising = true;
 }
 
-static void init_clock_ctx(Ctx &c, int q, double beta, double h) {
+static void init_clock_ctx(Ctx &c, int q, double beta, double h, int d = 4) {
   // real Fourier basis diagonalises the circulant bond matrix exp(beta cos(th - th'))
   std::vector<std::vector<double>> F;
   std::vector<double> th(q);
@@ -1238,7 +1757,7 @@ static void init_clock_ctx(Ctx &c, int q, double beta, double h) {
     obs[a] = std::cos(th[a]);
     wt[a] = std::exp(h * obs[a]);
   }
-  init_cp(c, beta, W, q, q, wt, obs);
+  init_cp(c, beta, W, q, q, wt, obs, d);
 }
 
 // ln Z/V and f of the current state (synchronises the stream)
@@ -1271,9 +1790,9 @@ static double magnetisation_ctx(Ctx &c) {
 static double gu_wen_ctx(Ctx &c) {
   if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
   int slot = 0;
-  for (int i = 0; i < 4; ++i)
-    if (c.axes[i] == 3) slot = i;
-  std::string fa = "abcdg", fb = "abcdg";
+  for (int i = 0; i < c.d; ++i)
+    if (c.axes[i] == c.d - 1) slot = i;
+  std::string fa = std::string("abcd").substr(0, c.d) + "g", fb = fa;
   fa[slot] = 'k';
   fb[slot] = 'l';
   Arena::Mark mk = c.arena.mark();
@@ -1295,7 +1814,10 @@ static double gu_wen_ctx(Ctx &c) {
 // one step with the error context of the phase that failed
 static void step_ctx(Ctx &c, int axis, int D, int p) {
   try {
-    step_impl(c, axis, D, p);
+    if (c.d == 3)
+      step3_impl(c, axis, D, p);
+    else
+      step_impl(c, axis, D, p);
   } catch (const Error &e) {
     cudaStreamSynchronize(c.stream);
     c.arena.reset();
@@ -1318,6 +1840,7 @@ struct InstState {
   double *phi = nullptr, *psi = nullptr, *psi_imp = nullptr;
   std::vector<int64_t> dims;
   int axes[4] = {0, 1, 2, 3};
+  int d = 4;                   // lattice dimension (3 or 4)
   int nsteps = 0;
   double *dscal = nullptr;
   int *dflag = nullptr;
@@ -1734,19 +2257,19 @@ extern "C" {
 
 trg_status trg_init_ising(int d, double beta, double h) {
   return guarded([&] {
-    if (d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 4");
+    if (d != 3 && d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 3, 4");
     if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
       throw Error(TRG_ERR_ARG, "need finite beta >= 0 and finite h");
-    init_ising_ctx(ctx(), beta, h);
+    init_ising_ctx(ctx(), beta, h, d);
   });
 }
 
 trg_status trg_init_clock(int d, int q, double beta, double h) {
   return guarded([&] {
-    if (d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 4");
+    if (d != 3 && d != 4) throw Error(TRG_ERR_ARG, "the triad step is implemented for d = 3, 4");
     if (q < 2 || q > 8 || !(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h))
       throw Error(TRG_ERR_ARG, "need 2 <= q <= 8, finite beta >= 0 and finite h");
-    init_clock_ctx(ctx(), q, beta, h);
+    init_clock_ctx(ctx(), q, beta, h, d);
   });
 }
 
@@ -1754,8 +2277,8 @@ trg_status trg_step(int axis, int D, int sketch_oversample) {
   return guarded([&] {
     Ctx &c = ctx();
     if (!c.init) throw Error(TRG_ERR_NOINIT, "no model initialised");
-    if (axis < 0 || axis > 3 || D < 1 || sketch_oversample < 0)
-      throw Error(TRG_ERR_ARG, "need 0 <= axis < 4, D >= 1, p >= 0");
+    if (axis < 0 || axis >= c.d || D < 1 || sketch_oversample < 0)
+      throw Error(TRG_ERR_ARG, "need 0 <= axis < d, D >= 1, p >= 0");
     step_ctx(c, axis, D, sketch_oversample);
   });
 }
@@ -1773,8 +2296,8 @@ trg_status trg_magnetisation_impurity(double *m) {
 
 trg_status trg_set_params(int q_swap, int q_rho, unsigned long long seed, int precision) {
   return guarded([&] {
-    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > 6)
-      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..6");
+    if (q_swap < 1 || q_rho < 0 || precision < 0 || precision > TRG_PREC_OZ7)
+      throw Error(TRG_ERR_ARG, "need q_swap >= 1, q_rho >= 0, precision in 0..8");
     Ctx &c = ctx();
     c.q_swap = q_swap;
     c.q_rho = q_rho;
@@ -1838,7 +2361,7 @@ trg_status trg_internal_energy(double *u) {
     if (c.imp_pair != 2)
       throw Error(TRG_ERR_NOINIT, "no merged impurity pair (trg_set_impurity_pair, then a step)");
     if (!c.ising) throw Error(TRG_ERR_ARG, "the pair gives the internal energy of the Ising model");
-    *u = -4.0 * magnetisation_ctx(c);
+    *u = -(double)c.d * magnetisation_ctx(c);
   });
 }
 
@@ -1874,7 +2397,9 @@ trg_status trg_get_state(int which, int *dims_out, int *axes_out, double *host,
     if (which < 0 || which > 2 || !dims_out) throw Error(TRG_ERR_ARG, "bad which / dims_out");
     double *src = which == 0 ? c.phi : which == 1 ? c.psi : c.psi_imp;
     if (!src) throw Error(TRG_ERR_ARG, "factor not present");
-    for (int i = 0; i < 5; ++i) dims_out[i] = (int)c.dims[i];
+    // a 3D state (d1, d2, d3, r) is reported as (d1, d2, d3, 1, r): the same memory layout
+    for (int i = 0; i < 5; ++i)
+      dims_out[i] = c.d == 4 ? (int)c.dims[i] : i < 3 ? (int)c.dims[i] : i == 3 ? 1 : (int)c.dims[3];
     if (axes_out)
       for (int i = 0; i < 4; ++i) axes_out[i] = c.axes[i];
     if (host) {
@@ -1906,10 +2431,13 @@ trg_status trg_set_state(double beta, const int *dims, const double *phi, const 
     // everything is checked before the current state is released
     for (int i = 0; i < 5; ++i)
       if (dims[i] < 1) throw Error(TRG_ERR_ARG, "dims must be >= 1");
+    // axes[3] = -1 with dims[3] = 1 marks a three-dimensional state (d1, d2, d3, r)
+    const int dd = (axes[3] == -1 && dims[3] == 1) ? 3 : 4;
     int seen = 0;
-    for (int i = 0; i < 4; ++i)
-      if (axes[i] >= 0 && axes[i] < 4) seen |= 1 << axes[i];
-    if (seen != 0xF) throw Error(TRG_ERR_ARG, "axes must be a permutation of 0..3");
+    for (int i = 0; i < dd; ++i)
+      if (axes[i] >= 0 && axes[i] < dd) seen |= 1 << axes[i];
+    if (seen != (1 << dd) - 1)
+      throw Error(TRG_ERR_ARG, "axes must be a permutation of 0..3 (or of 0..2 with axes[3] = -1)");
     if (!std::isfinite(beta) || !(beta >= 0.0) || !std::isfinite(logsum))
       throw Error(TRG_ERR_ARG, "need finite beta >= 0 and finite logsum");
     int64_t total = 1;
@@ -1925,7 +2453,13 @@ trg_status trg_set_state(double beta, const int *dims, const double *phi, const 
     ensure_ctx(c);
     TRG_CUDA(cudaStreamSynchronize(c.stream));
     free_state(c);
-    c.dims.assign(dims, dims + 5);
+    c.d = dd;
+    if (dd == 4) {
+      c.dims.assign(dims, dims + 5);
+    } else {
+      c.dims.assign(dims, dims + 3);
+      c.dims.push_back(dims[4]);
+    }
     for (int i = 0; i < 4; ++i) c.axes[i] = axes[i];
     int64_t n = prod(c.dims);
     for (auto pr : {std::make_pair(&c.phi, phi), std::make_pair(&c.psi, psi),
@@ -1990,7 +2524,7 @@ trg_status trg_batch_create(int n, const int *model, const double *beta, const d
                             int lanes, int q_swap, int q_rho, int precision) {
   return guarded([&] {
     if (n < 1 || !model || !beta || !h || !D || lanes < 1 || q_swap < 1 || q_rho < 0 ||
-        precision < 0 || precision > 6)
+        precision < 0 || precision > TRG_PREC_OZ7)
       throw Error(TRG_ERR_ARG, "trg_batch_create: bad arguments");
     for (int i = 0; i < n; ++i)
       if (!(model[i] == 0 || (model[i] >= 2 && model[i] <= 8)) || !(beta[i] >= 0.0) ||
@@ -2308,7 +2842,8 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
                     double alpha, const double *A, long long lda, const double *B,
                     long long ldb, double beta, double *C, long long ldc) {
   return guarded([&] {
-    if (!A || !B || !C || M < 0 || N < 0 || K < 0 || precision < 0 || precision > 6)
+    if (!A || !B || !C || M < 0 || N < 0 || K < 0 || precision < 0 ||
+        precision > TRG_PREC_OZ7)
       throw Error(TRG_ERR_ARG, "bad gemm arguments");
     Ctx &c = ctx();
     ensure_ctx(c);
@@ -2323,14 +2858,14 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
     TRG_CUDA(cudaMemcpyAsync(dC.p, C, M * ldc * 8, cudaMemcpyHostToDevice, c.stream));
     if (precision == TRG_PREC_FP64) {
       gemm_f64(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1, c.stream);
-    } else if (precision >= TRG_PREC_OZ4) {
+    } else if (is_digit_form(precision)) {
       ArenaScratch scr(c.arena);
       gemm_oz(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
-              precision, scr, c.stream);
+              digits_of(precision), scr, c.stream);
     } else {
       ArenaScratch scr(c.arena);
       gemm_tc(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
-              slices_of(precision), scr, c.stream);
+              slices_of(precision), scr, c.stream, nullptr, precision == TRG_PREC_TF32X3);
     }
     TRG_CUDA(cudaMemcpyAsync(C, dC.p, M * ldc * 8, cudaMemcpyDeviceToHost, c.stream));
     TRG_CUDA(cudaStreamSynchronize(c.stream));
@@ -2340,17 +2875,20 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
   });
 }
 
-trg_status trg_kernel_stats(double *tc_ms, double *tc_flop, long long *tc_launches,
-                            long long *all_launches, int reset) {
+trg_status trg_kernel_stats(double *out, int n, int reset) {
   return guarded([&] {
+    if (n < 0 || (n > 0 && !out)) throw Error(TRG_ERR_ARG, "trg_kernel_stats: bad buffer");
     Ctx &c = ctx();
-    if (tc_ms) *tc_ms = c.tc_ms;
-    if (tc_flop) *tc_flop = c.tc_flop;
-    if (tc_launches) *tc_launches = c.tc_launches;
-    if (all_launches) *all_launches = g_kernel_launches.load();
+    const double v[13] = {c.k_ms[0], c.k_alg[0], c.k_pipe[0], (double)c.k_launches[0],
+                          c.k_ms[1], c.k_alg[1], c.k_pipe[1], (double)c.k_launches[1],
+                          c.k_ms[2], c.k_alg[2], c.k_pipe[2], (double)c.k_launches[2],
+                          (double)g_kernel_launches.load()};
+    for (int i = 0; i < std::min(n, 13); ++i) out[i] = v[i];
     if (reset) {
-      c.tc_ms = c.tc_flop = 0.0;
-      c.tc_launches = 0;
+      for (int k = 0; k < 3; ++k) {
+        c.k_ms[k] = c.k_alg[k] = c.k_pipe[k] = 0.0;
+        c.k_launches[k] = 0;
+      }
       g_kernel_launches.store(0);
     }
   });
