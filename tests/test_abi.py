@@ -45,7 +45,7 @@ def test_argument_errors_without_gpu(lib):
     lib.trg_set_params.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int]
     assert lib.trg_set_params(0, 4, 1, 0) == -1          # q_swap >= 1
     assert lib.trg_set_params(4, -1, 1, 0) == -1         # q_rho >= 0
-    assert lib.trg_set_params(4, 4, 1, 7) == -1          # precision
+    assert lib.trg_set_params(4, 4, 1, 9) == -1          # precision (0..8)
     assert lib.trg_set_params(4, 4, 0x5EED, 0) == 0
     lib.trg_set_bond_overspan.argtypes = [ctypes.c_int]
     assert lib.trg_set_bond_overspan(0) == -1            # r_bond >= 1

@@ -83,7 +83,7 @@ def test_ilo_mixed_form_oz5_within_1e8_of_oracle(trg):
         for n in range(N):
             trg.trg_step(n % 4, D, 2 * D)
         f_gpu, _ = trg.trg_free_energy()
-        assert trg.trg_kernel_stats(reset=True)["tc_launches"] > 0
+        assert trg.trg_kernel_stats(reset=True)["oz_launches"] > 0
     finally:
         trg.trg_set_bond_overspan(1)
         trg.trg_set_params(4, 4, 0x5EED, trg.TRG_PREC_FP64)
