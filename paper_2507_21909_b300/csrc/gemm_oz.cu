@@ -7,11 +7,11 @@
 // Slices are stored pre-scaled as BF16 values  ^a_s = d_s 2^(-7(s-1))  (exact: 8-bit
 // integers times powers of two), so that  a' b' = 2^-28 sum_{i,j} ^a_i ^b_j  and the
 // digit products fall into three levels of tensor-memory accumulators:
-//     L0 = sum ^a_0 ^b_0            (integers x 2^14,  |chunk sum| <= 2^36)
+//     L0 = sum ^a_0 ^b_0            (integers x 2^14,  |chunk sum| <= 2^37)
 //     L1 = sum ^a_0 ^b_1 + ^a_1 ^b_0 (integers x 2^7)
 //     H  = sum over i + j in [2, ns-1] of ^a_i ^b_j   (carries 2^-14 of the result)
-// Over a chunk of 256 K the FP32 sums L0 / L1 are exact integers (|L0 2^-14| and
-// |L1 2^-7| <= 2^22); every chunk they and that chunk's H are drained into one int64
+// Over a chunk of 512 K the FP32 sums L0 / L1 are exact integers (|L0 2^-14| and
+// |L1 2^-7| <= 2^23 < 2^24); every chunk they and that chunk's H are drained into one int64
 // fixed-point accumulator per output with 12 fractional bits (integer units on the
 // ALU: B300 issues few FP64 adds), so only H carries the FP32 rounding of one chunk.
 // |acc| <= K 2^41, so K per split stays below 2^21.  H is double-buffered in tensor
@@ -42,7 +42,7 @@ namespace oz {
 constexpr int BM = 128, BN = 128;
 constexpr int BK = 64;                      // K padding granule of the digit planes
 constexpr int KS = 16;                      // K per pipeline stage (= one MMA, 32-byte rows)
-constexpr int CHUNK_K = 256;                // exact chunk of levels 0 / 1
+constexpr int CHUNK_K = 512;                // exact chunk of the exact levels
 constexpr int CHUNK_KS = CHUNK_K / KS;      // stages per chunk
 constexpr uint32_t SLICE_TILE = BM * KS * 2;    // 4 KB: 128 rows x 16 K of one slice
 constexpr size_t kStageBudget = 200 * 1024;     // shared memory for the stage ring
@@ -140,11 +140,6 @@ __device__ __forceinline__ void tld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // row exponent codes: e + 4096, 0 for an all-zero row
 __device__ __forceinline__ int decode_exp(unsigned code) { return code ? (int)code - 4096 : 0; }
-
-// exact integer of an FP32 value v with |v| <= 2^22 (v an integer)
-__device__ __forceinline__ int exact_int(float v) {
-  return __float_as_int(v + 12582912.0f) - 0x4B400000;
-}
 
 __device__ __forceinline__ void umma(uint32_t acc_t, uint64_t da, uint64_t db, uint32_t accum) {
   asm volatile(
@@ -336,8 +331,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int i0 = exact_int(__uint_as_float(r0[j]) * 0x1.0p-14f);
-            const int i1 = exact_int(__uint_as_float(r1[j]) * 0x1.0p-7f);
+            const int i0 = __float2int_rn(__uint_as_float(r0[j]) * 0x1.0p-14f);
+            const int i1 = __float2int_rn(__uint_as_float(r1[j]) * 0x1.0p-7f);
             acc[c * 16 + j] += ((long long)i0 << 26) + ((long long)i1 << 19);
           }
         }
@@ -394,8 +389,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 // ------------------------------------------------------ the FP64-equivalent form
 // Seven digits (49 bits of every row of op(A) and column of op(B)) with levels 0..3 exact
-// per chunk: over a 256-deep chunk a level l sums l + 1 digit products of at most
-// 128 x 64 per k (<= 6.3e6 < 2^24 for l = 3), so levels 0..3 are exact FP32 integers;
+// per chunk: over a 512-deep chunk a level l sums l + 1 digit products of at most
+// 128 x 64 per k (<= 1.26e7 < 2^24 for l = 3), so levels 0..3 are exact FP32 integers;
 // the levels >= 4 (2^-14 and below of the result, ^a ^b units) share one FP32
 // accumulator per chunk (two buffers, alternating chunks).  Every chunk all five are
 // drained into an int64 fixed-point accumulator with XFRAC = 16 fractional bits:
@@ -712,8 +707,10 @@ __device__ __forceinline__ void store_pairs(__nv_bfloat16 *o, int64_t plane, con
   }
 }
 
-// Digit planes of op(X) = X (rows contiguous along K): one warp per row, each lane two
-// consecutive k (coalesced loads, one 4-byte store of two BF16 digits per plane)
+// Digit planes of op(X) = X (rows contiguous along K): one warp per segment of up to
+// kSplitSeg k of one row, each lane two consecutive k (coalesced loads, one 4-byte store
+// of two BF16 digits per plane)
+constexpr int64_t kSplitSeg = 4096;
 template <int NS>
 __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
                                      int64_t ld, int64_t sX, const unsigned *__restrict__ e,
@@ -721,14 +718,17 @@ __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows,
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t plane = batch * rows * Kp;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < batch * rows;
-       w += nwarps) {
+  const int64_t nseg = (Kp + kSplitSeg - 1) / kSplitSeg;
+  for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       item < batch * rows * nseg; item += nwarps) {
+    const int64_t w = item / nseg, seg = item - w * nseg;
     const int64_t b = w / rows, r = w - b * rows;
     const double *x = X + b * sX + r * ld;
     const int ex = decode_exp(e[w]);
     const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
     __nv_bfloat16 *o = out + w * Kp;
-    for (int64_t k = 2 * lane; k < Kp; k += 64) {
+    const int64_t kend = min(Kp, (seg + 1) * kSplitSeg);
+    for (int64_t k = seg * kSplitSeg + 2 * lane; k < kend; k += 64) {
       const double v0 = k < K ? x[k] : 0.0, v1 = k + 1 < K ? x[k + 1] : 0.0;
       int d0[NS], d1[NS];
       balanced_digits<NS>(__double2ll_rn(v0 * scale), d0);
@@ -782,7 +782,7 @@ static void launch_split(const double *X, int64_t rows, int64_t K, int64_t ld, i
     oz_split_cols_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32),
                                dim3(32, 8), 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
   } else {
-    const int64_t warps = rows * batch;
+    const int64_t warps = rows * batch * ((Kp + kSplitSeg - 1) / kSplitSeg);
     oz_split_rows_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>((warps + 7) / 8, 1),
                                                             148 * 16),
                                256, 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);

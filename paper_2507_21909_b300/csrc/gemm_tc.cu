@@ -127,7 +127,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int64_t z = blockIdx.z;
   const int64_t b = z % p.batch, split = z / p.batch;
   const int kb0 = (int)split * p.nkb;
-  const int nkb_total = (int)(p.Kp / BK);
+  const int nkb_total = (int)(p.Kp / BKE);
   const int kb1 = min(kb0 + p.nkb, nkb_total);
   const int nk = max(kb1 - kb0, 0);
   const int iters = nk * p.npairs;

@@ -26,7 +26,7 @@ def trg(require_gpu):
     return pkg
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("M,N,K,ta,tb", SHAPES)
 def test_gemm_against_numpy(trg, prec, M, N, K, ta, tb):
     rng = np.random.default_rng(M * 7 + N * 3 + K)
