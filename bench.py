@@ -64,6 +64,9 @@ def args_():
                     help="comma-separated D list: time the triad step against the plain "
                          "ATRG step (4D Ising, same precision and sketches) at each D "
                          "instead of the single D=48 step; ATRG holds D^8 tensors, so D <= 12")
+    ap.add_argument("--triad-d", default="",
+                    help="with --compare-atrg: further D (comma-separated) at which only the "
+                         "triad step is timed (ATRG holds D^8 tensors beyond D = 12)")
     ap.add_argument("--r-bond", type=int, default=1,
                     help="ILO form: bond lines overspanned to r_bond D (1 = plain method)")
     ap.add_argument("--gemm", default="",
@@ -323,25 +326,29 @@ def precision_at_size(trg, prec, D, beta, nsteps, stream, others=()):
     for pr in (0, prec) + tuple(others):
         trg.trg_set_params(4, 4, 0x5EED, pr)
         trg.trg_init_ising(4, beta, 0.0)
-        fs, ms = [], []
+        fs, ms, gaps = [], [], []
         for k in range(nsteps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             trg.trg_step(k % 4, D, 2 * D)
             e1.record(stream)
             fs.append(trg.trg_free_energy()[0])
+            gaps.append(trg.trg_diag()[1])
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-        out[pr] = (fs, ms, list(trg.trg_state_dims(0)))
-    f64, ms64, dims64 = out[0]
-    fmx, msmx, _ = out[prec]
+        out[pr] = (fs, ms, list(trg.trg_state_dims(0)), gaps)
+    f64, ms64, dims64, gaps64 = out[0]
+    fmx, msmx, _, _ = out[prec]
     per = [abs(x - y) / abs(y) for x, y in zip(fmx, f64)]
     res = {"steps": nsteps, "per_step": per, "max": max(per),
            "fp64_form_ms_last_step": ms64[-1], "mixed_form_ms_last_step": msmx[-1],
-           "last_step_input_dims": dims64, "fp64_form_steps_per_s": 1e3 / ms64[-1]}
+           "last_step_input_dims": dims64, "fp64_form_steps_per_s": 1e3 / ms64[-1],
+           # smallest relative singular-value gap at the bond-swap and squeezer cuts of
+           # each FP64-form step: a near-degenerate cut amplifies rounding differences
+           "fp64_form_min_gap_per_step": gaps64}
     names = {v: k for k, v in PREC.items()}
     for pr in others:
-        fo, mso, _ = out[pr]
+        fo, mso, _, _ = out[pr]
         po = [abs(x - y) / abs(y) for x, y in zip(fo, f64)]
         res.setdefault("other_forms", {})[names[pr]] = {
             "per_step": po, "max": max(po), "ms_last_step": mso[-1]}
@@ -428,11 +435,15 @@ def run_compare_atrg(a):
     trg.trg_set_stream(stream.cuda_stream)
     prec = PREC[a.precision]
     rows = []
-    for D in [int(v) for v in a.compare_atrg.split(",") if v.strip()]:
+    both = [int(v) for v in a.compare_atrg.split(",") if v.strip()]
+    only = [int(v) for v in a.triad_d.split(",") if v.strip()]
+    for D in both + only:
         row = {"D": D, "p": 2 * D}
-        for name, init, step in (
-                ("triad", lambda: trg.trg_init_ising(4, a.beta, 0.0), trg.trg_step),
-                ("atrg", lambda: trg.trg_atrg_init_ising(4, a.beta, 0.0), trg.trg_atrg_step)):
+        methods = [("triad", lambda: trg.trg_init_ising(4, a.beta, 0.0), trg.trg_step)]
+        if D in both:
+            methods.append(("atrg", lambda: trg.trg_atrg_init_ising(4, a.beta, 0.0),
+                            trg.trg_atrg_step))
+        for name, init, step in methods:
             trg.trg_set_params(4, 4, 0x5EED, prec)
             init()
             n = 0
@@ -450,16 +461,26 @@ def run_compare_atrg(a):
             torch.cuda.synchronize()
             row[f"{name}_ms_per_step"] = ev0.elapsed_time(ev1) / a.steps
         row["f_triad"] = trg.trg_free_energy()[0]
-        row["f_atrg"] = trg.trg_atrg_free_energy()[0]
-        row["atrg_over_triad"] = row["atrg_ms_per_step"] / row["triad_ms_per_step"]
+        if D in both:
+            row["f_atrg"] = trg.trg_atrg_free_energy()[0]
+            row["atrg_over_triad"] = row["atrg_ms_per_step"] / row["triad_ms_per_step"]
         rows.append(row)
+    # power-law exponents of the step time in D (least squares on log-log), per method
+    import numpy as np
+    fits = {}
+    for name in ("triad", "atrg"):
+        pts = [(r["D"], r[name + "_ms_per_step"]) for r in rows if name + "_ms_per_step" in r]
+        if len(pts) >= 2:
+            x = np.log([d for d, _ in pts])
+            y = np.log([t for _, t in pts])
+            fits[name] = float(np.polyfit(x, y, 1)[0])
     print(json.dumps({
         "metric": "ms per RG step, triad-ATRG vs plain ATRG, 4D Ising", "unit": "ms",
         "higher_is_better": False, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
         "dtype": a.precision, "data": "synthetic",
         "config": {"workload": f"4D Ising beta={a.beta}, h=0, p=2D, q_swap=4, q_rho=4",
                    "precision": a.precision, "D": [r["D"] for r in rows]},
-        "rows": rows}), flush=True)
+        "time_exponent_in_D": fits, "rows": rows}), flush=True)
 
 
 def run_gemm(a):
@@ -474,17 +495,25 @@ def run_gemm(a):
     for _ in range(a.warmup):
         trg.trg_gemm(A, B, precision=prec)
     t = []
+    trg.trg_kernel_stats(reset=True)
     for _ in range(max(a.steps, 1)):
         t0 = time.time()
         C = trg.trg_gemm(A, B, precision=prec)
         t.append(time.time() - t0)
+    ks = trg.trg_kernel_stats(reset=True)
+    kind = "x7" if a.precision == "oz7" else "oz" if a.precision.startswith("oz") else "tc"
+    kms = ks[kind + "_ms"] / max(ks[kind + "_launches"], 1)
     rows = rng.choice(M, 8, replace=False)
     ref = A[rows] @ B
     err = float(np.abs(C[rows] - ref).max() / (np.abs(A[rows]) @ np.abs(B)).max())
     print(json.dumps({"metric": "trg_gemm wall time (upload + product + download)",
                       "unit": "ms", "value": 1e3 * statistics.median(t), "M": M, "N": N, "K": K,
                       "precision": a.precision, "sampled_rel_err": err,
-                      "alg_flop": 2.0 * M * N * K}), flush=True)
+                      "alg_flop": 2.0 * M * N * K,
+                      "kernel_ms": kms, "kernel_launches": ks[kind + "_launches"],
+                      "kernel_alg_tflops": 2.0 * M * N * K / kms / 1e9 if kms > 0 else None,
+                      "kernel_pipe_tflops": (ks[kind + "_pipe_flop"] / max(ks[kind + "_launches"], 1)
+                                             / kms / 1e9) if kms > 0 else None}), flush=True)
 
 
 def reduce_timing(ms, steps, world, dist=None, device="cpu"):
@@ -643,6 +672,7 @@ def run_ours(a):
         dfr = line.setdefault("delta_f_rel", {})
         dfr[f"vs_fp64_form_D{D}_per_step"] = chk["per_step"]
         dfr[f"vs_fp64_form_D{D}_max"] = chk["max"]
+        dfr[f"fp64_form_D{D}_min_cut_gap_per_step"] = chk["fp64_form_min_gap_per_step"]
         line["fp64_form"] = {
             "value": chk["fp64_form_steps_per_s"], "unit": "RG steps/s",
             "measured": f"step {a.precision_steps - 1} of the FP64-form run above (input legs "

@@ -601,14 +601,15 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
     } else if (is_digit_form(precision)) {
       ArenaScratch scr(c.arena);
       gemm_oz(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
-              digits_of(precision), scr, c.stream);
+              digits_of(precision), scr, c.stream, &c.timing);
     } else {
       ArenaScratch scr(c.arena);
       gemm_tc(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
-              slices_of(precision), scr, c.stream, nullptr, precision == TRG_PREC_TF32X3);
+              slices_of(precision), scr, c.stream, &c.timing, precision == TRG_PREC_TF32X3);
     }
     TRG_CUDA(cudaMemcpyAsync(C, dC.p, M * ldc * 8, cudaMemcpyDeviceToHost, c.stream));
     TRG_CUDA(cudaStreamSynchronize(c.stream));
+    c.collect_tc();   // the product kernel's device time into trg_kernel_stats
     c.arena.reset();
     if (tc_error_flag(true) | oz_error_flag(true))
       throw Error(TRG_ERR_TIMEOUT, "tensor-core GEMM wait timed out");

@@ -20,10 +20,17 @@
 //
 // CTA = 12 warps: warp 0 TMA producer, warp 1 MMA issuer (M = 128, N = 128, K = 16),
 // warps 2..9 drain TMEM (two warps per 32-lane quadrant, 64 columns each).  A pipeline
-// stage holds one 16-wide K block of every digit slice of A and of B (32-byte rows,
-// 32-byte swizzle), so each slice tile is loaded once and serves all pairs (i, j) that
-// use it; at the first stage of a chunk the lower-level pairs are issued before waiting
-// for the drain of the previous chunk, which hides the drain behind them.
+// stage holds one 16-wide K block of every digit slice of A and of B, so each slice tile
+// is loaded once and serves all pairs (i, j) that use it.  The digit planes are stored
+// pre-tiled in the tensor cores' unswizzled K-major layout (8-row x 16-byte core
+// matrices, the two K halves of a 16-wide block 128 bytes apart, the digit slices of one
+// 8-row group side by side): one TMA box per operand and stage then moves 256-byte
+// contiguous runs, where a row-major plane would need one 32-byte request per row and
+// slice, which saturates the SM-to-L2 request path before the tensor pipe.  At the first
+// stage of a chunk the lower-level pairs are issued before waiting
+// for the drain of the previous chunk's exact levels, and the drain warps read those
+// first and signal them separately from the H buffer (which is reused two chunks later),
+// so the issuer waits only for the exact levels.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -45,6 +52,7 @@ constexpr int KS = 16;                      // K per pipeline stage (= one MMA, 
 constexpr int CHUNK_K = 512;                // exact chunk of the exact levels
 constexpr int CHUNK_KS = CHUNK_K / KS;      // stages per chunk
 constexpr uint32_t SLICE_TILE = BM * KS * 2;    // 4 KB: 128 rows x 16 K of one slice
+constexpr uint32_t CHUNK_BYTES = 256;           // one 8-row group x 16 K of one slice
 constexpr size_t kStageBudget = 200 * 1024;     // shared memory for the stage ring
 constexpr int MAX_STAGES = 8;
 // 12 warps: registers are allocated in groups of four warps, so a 10-warp block costs
@@ -99,18 +107,21 @@ __device__ __forceinline__ bool mb_wait(uint32_t b, uint32_t parity) {
     }
   }
 }
-__device__ __forceinline__ void tma4(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c0,
-                                     int c1, int c2, int c3) {
+// one box of the 5-d plane map {256-byte run, slice, K block, 8-row group, batch}: the
+// x coordinate is always 0 (16-byte aligned)
+__device__ __forceinline__ void tma5(uint32_t dst, const CUtensorMap *m, uint32_t bar, int kb,
+                                     int g, int b) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(m)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(bar), "r"(0), "r"(0), "r"(kb), "r"(g), "r"(b)
       : "memory");
 }
-// K-major tile with 32-byte rows, 32-byte swizzle: 8-row groups 256 bytes apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+// unswizzled K-major operand: 8 x 16-byte core matrices, the K-adjacent one 128 bytes on
+// (leading offset), the next 8-row group `sbo` bytes on (stride offset)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46);
 }
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
@@ -195,9 +206,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int nst = p.stages;
   const uint32_t STAGE = 2u * (uint32_t)ns * SLICE_TILE;   // all A slices, then all B slices
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * STAGE);
-  // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] chunk
-  // drained, bar[2nst+2] all done
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * MAX_STAGES + 3);
+  // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] exact
+  // levels of the chunk drained, bar[2nst+2] all done, bar[2nst+3+j] H buffer j drained
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * MAX_STAGES + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // CTA order: groups of kGroupM row tiles, column tiles within a group, so that the CTAs
   // resident at one time cover a near-square patch of output tiles and share their A and
@@ -226,6 +237,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     mb_init(su32(&bar[2 * nst]), 1);
     mb_init(su32(&bar[2 * nst + 1]), 8 * 32);
     mb_init(su32(&bar[2 * nst + 2]), 1);
+    mb_init(su32(&bar[2 * nst + 3]), 8 * 32);
+    mb_init(su32(&bar[2 * nst + 4]), 8 * 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -248,11 +261,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t base = su32(smem + (size_t)st * STAGE);
         const uint32_t full = su32(&bar[st]);
         mb_expect(full, STAGE);
-        const int kc = (ks0 + it) * KS;
-        for (int sl = 0; sl < ns; ++sl) {
-          tma4(base + sl * SLICE_TILE, &tmA, full, kc, (int)m0, (int)b, sl);
-          tma4(base + (ns + sl) * SLICE_TILE, &tmB, full, kc, (int)n0, (int)b, sl);
-        }
+        // [16 groups][ns slices][256 B] of A, then the same of B
+        tma5(base, &tmA, full, ks0 + it, (int)(m0 >> 3), (int)b);
+        tma5(base + ns * SLICE_TILE, &tmB, full, ks0 + it, (int)(n0 >> 3), (int)b);
       }
     }
   } else if (warp == 1) {
@@ -261,7 +272,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       // exact per chunk and drained by warps 2..9; at the first stage of a chunk the
       // lower-level pairs go first, so they overlap the drain of the previous chunk.
       // descriptors of slice tiles: the stage base's descriptor plus the byte offset / 16
-      constexpr uint64_t kTileStep = SLICE_TILE >> 4;
+      // (slices of one 8-row group are 256 bytes apart, groups ns x 256 bytes)
+      constexpr uint64_t kTileStep = CHUNK_BYTES >> 4;
       bool ok = true;
       int it = 0;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
@@ -270,10 +282,18 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const int st = it % nst;
           if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t da = sdesc(su32(smem + (size_t)st * STAGE));
-          const uint64_t db = da + (uint64_t)ns * kTileStep;
-          // lower levels (i + j >= 2) into this chunk's H buffer (H of chunk ch - 2 was
-          // drained before chunk ch - 1 started, so the buffer is free)
+          const uint64_t da = sdesc(su32(smem + (size_t)st * STAGE), ns * CHUNK_BYTES);
+          const uint64_t db = da + (uint64_t)((ns * SLICE_TILE) >> 4);
+          // lower levels (i + j >= 2) into this chunk's H buffer; that buffer last held
+          // chunk ch - 2, whose H pass the drain warps finish before they start on the
+          // exact levels of chunk ch - 1 (one barrier per H buffer, one completion per use)
+          if (ks == kbeg && ch >= 2) {
+            if (!mb_wait(su32(&bar[2 * nst + 3 + (ch & 1)]), (uint32_t)((ch - 2) >> 1) & 1u)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
           const uint32_t acc_h = tmem + (uint32_t)((2 + (ch & 1)) * BN);
 #pragma unroll
           for (int t = 2; t < ns; ++t)
@@ -281,7 +301,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int i = 0; i <= t; ++i)
               umma(acc_h, da + i * kTileStep, db + (t - i) * kTileStep,
                    (ks > kbeg || t > 2 || i > 0) ? 1u : 0u);
-          // levels 0 / 1 restart every chunk; the previous chunk must be drained first
+          // levels 0 / 1 restart every chunk: the previous chunk's exact levels must be
+          // drained first (its H buffer is drained afterwards, behind these products)
           if (ks == kbeg && ch > 0) {
             if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -320,34 +341,37 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+      // levels 0 and 1 (ns >= 3, so both have pairs): exact integers of this chunk; once
+      // read, the issuer may restart them for the next chunk
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const uint32_t col = (uint32_t)(half * 64 + c * 16);
-        {
-          // levels 0 and 1 (ns >= 3, so both have pairs): exact integers of this chunk
-          uint32_t r0[16], r1[16];
-          tld16(lane_base + col, r0);
-          tld16(lane_base + BN + col, r1);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t r0[16], r1[16];
+        tld16(lane_base + col, r0);
+        tld16(lane_base + BN + col, r1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int i0 = __float2int_rn(__uint_as_float(r0[j]) * 0x1.0p-14f);
-            const int i1 = __float2int_rn(__uint_as_float(r1[j]) * 0x1.0p-7f);
-            acc[c * 16 + j] += ((long long)i0 << 26) + ((long long)i1 << 19);
-          }
-        }
-        {
-          // this chunk's lower levels, rounded to 2^-12
-          uint32_t rh[16];
-          tld16(lane_base + (uint32_t)((2 + (ch & 1)) * BN) + col, rh);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * 4096.0f);
+        for (int j = 0; j < 16; ++j) {
+          const int i0 = __float2int_rn(__uint_as_float(r0[j]) * 0x1.0p-14f);
+          const int i1 = __float2int_rn(__uint_as_float(r1[j]) * 0x1.0p-7f);
+          acc[c * 16 + j] += ((long long)i0 << 26) + ((long long)i1 << 19);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mb_arrive(su32(&bar[2 * nst + 1]));
+      // this chunk's lower levels, rounded to 2^-12, from H buffer ch & 1
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t col = (uint32_t)(half * 64 + c * 16);
+        uint32_t rh[16];
+        tld16(lane_base + (uint32_t)((2 + (ch & 1)) * BN) + col, rh);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * 4096.0f);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mb_arrive(su32(&bar[2 * nst + 3 + (ch & 1)]));
     }
     // warp-uniform (the staged store below synchronises the warp)
     const bool done =
@@ -426,7 +450,9 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * XSTAGE);
   // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] chunk
   // drained, bar[2nst+2] all done
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * nst + 3);
+  // bar[2nst] chunk ready, bar[2nst+1] exact levels drained, bar[2nst+2] all done,
+  // bar[2nst+3+j] H buffer j drained
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * nst + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t mt, nt;
   {
@@ -452,6 +478,8 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     mb_init(su32(&bar[2 * nst]), 1);
     mb_init(su32(&bar[2 * nst + 1]), 8 * 32);
     mb_init(su32(&bar[2 * nst + 2]), 1);
+    mb_init(su32(&bar[2 * nst + 3]), 8 * 32);
+    mb_init(su32(&bar[2 * nst + 4]), 8 * 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -474,16 +502,13 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const uint32_t base = su32(smem + (size_t)st * XSTAGE);
         const uint32_t full = su32(&bar[st]);
         mb_expect(full, XSTAGE);
-        const int kc = (ks0 + it) * KS;
-        for (int sl = 0; sl < XNS; ++sl) {
-          tma4(base + sl * XA_TILE, &tmA, full, kc, (int)m0, (int)b, sl);
-          tma4(base + XNS * XA_TILE + sl * XB_TILE, &tmB, full, kc, (int)n0, (int)b, sl);
-        }
+        tma5(base, &tmA, full, ks0 + it, (int)(m0 >> 3), (int)b);
+        tma5(base + XNS * XA_TILE, &tmB, full, ks0 + it, (int)(n0 >> 3), (int)b);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------ MMA issuer
-      constexpr uint64_t stepA = XA_TILE >> 4, stepB = XB_TILE >> 4;
+      constexpr uint64_t stepA = CHUNK_BYTES >> 4, stepB = CHUNK_BYTES >> 4;
       bool ok = true;
       int it = 0;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
@@ -493,9 +518,16 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sbase = su32(smem + (size_t)st * XSTAGE);
-          const uint64_t da = sdesc(sbase);
-          const uint64_t db = sdesc(sbase + XNS * XA_TILE);
-          // levels >= 4 into this chunk's H buffer (drained before chunk ch - 1 began)
+          const uint64_t da = sdesc(sbase, XNS * CHUNK_BYTES);
+          const uint64_t db = sdesc(sbase + XNS * XA_TILE, XNS * CHUNK_BYTES);
+          // levels >= 4 into this chunk's H buffer, once chunk ch - 2's H pass is drained
+          if (ks == kbeg && ch >= 2) {
+            if (!mb_wait(su32(&bar[2 * nst + 3 + (ch & 1)]), (uint32_t)((ch - 2) >> 1) & 1u)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
           const uint32_t acc_h = tmem + (uint32_t)((XNL + (ch & 1)) * XBN);
 #pragma unroll
           for (int t = XNL; t < XNS; ++t)
@@ -503,7 +535,7 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             for (int i = 0; i <= t; ++i)
               umma_x(acc_h, da + i * stepA, db + (t - i) * stepB,
                      (ks > kbeg || t > XNL || i > 0) ? 1u : 0u);
-          // exact levels restart every chunk: the previous chunk must be drained first
+          // exact levels restart every chunk: the previous chunk's must be drained first
           if (ks == kbeg && ch > 0) {
             if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -543,6 +575,7 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+      // the exact levels first (the issuer restarts them once they are read), then H
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const uint32_t col = (uint32_t)(half * 32 + c * 16);
@@ -558,6 +591,12 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             acc[c * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * unit)
                                << (14 - 7 * t + XFRAC);
         }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mb_arrive(su32(&bar[2 * nst + 1]));
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t col = (uint32_t)(half * 32 + c * 16);
         uint32_t rh[16];
         tld16(lane_base + (uint32_t)((XNL + (ch & 1)) * XBN) + col, rh);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -566,7 +605,7 @@ ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * (float)(1 << XFRAC));
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mb_arrive(su32(&bar[2 * nst + 1]));
+      mb_arrive(su32(&bar[2 * nst + 3 + (ch & 1)]));
     }
     // warp-uniform (the staged store below synchronises the warp)
     const bool done =
@@ -669,8 +708,13 @@ __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int
 // [-64, 63] from the bottom (d_s = ((q + 64) mod 128) - 64, q <- (q - d_s) / 128) and d_0
 // the remaining top digit (|d_0| <= 128).  The recursion only reads the low 7 bits and
 // divides exact multiples of 128, so the low three digits come from the low 21 bits in
-// 32-bit arithmetic and the rest from the high part plus the carry.  Planes are laid out
-// [slice][batch][rows][Kp] (K-major), zero padded for k >= K.
+// 32-bit arithmetic and the rest from the high part plus the carry.
+//
+// Plane layout (pre-tiled for the MMA, zero padded for k >= K and for the rows of the
+// last 8-row group beyond `rows`): value (b, r, k) of slice s at BF16 index
+//     ((((b G + r/8) KB + k/16) ns + s) 2 + (k/8) % 2) 64 + (r % 8) 8 + k % 8,
+// G = ceil(rows / 8), KB = Kp / 16: one 256-byte run per (8-row group, 16-wide K block,
+// slice) holding the two 8 x 8 core matrices of the block.
 template <int NS>
 __device__ __forceinline__ void balanced_digits(long long q, int (&d)[NS]) {
   constexpr int NLOW = NS - 1 < 3 ? NS - 1 : 3;
@@ -698,57 +742,80 @@ __device__ __forceinline__ float digit_value(int d) {
 }
 
 template <int NS, int S = 0>
-__device__ __forceinline__ void store_pairs(__nv_bfloat16 *o, int64_t plane, const int (&d0)[NS],
+__device__ __forceinline__ void store_pairs(__nv_bfloat16 *o, const int (&d0)[NS],
                                             const int (&d1)[NS]) {
   if constexpr (S < NS) {
-    *reinterpret_cast<__nv_bfloat162 *>(o + S * plane) =
+    *reinterpret_cast<__nv_bfloat162 *>(o + S * (CHUNK_BYTES / 2)) =
         __floats2bfloat162_rn(digit_value<S>(d0[S]), digit_value<S>(d1[S]));
-    store_pairs<NS, S + 1>(o, plane, d0, d1);
+    store_pairs<NS, S + 1>(o, d0, d1);
   }
 }
 
-// Digit planes of op(X) = X (rows contiguous along K): one warp per segment of up to
-// kSplitSeg k of one row, each lane two consecutive k (coalesced loads, one 4-byte store
-// of two BF16 digits per plane)
-constexpr int64_t kSplitSeg = 4096;
+// planes are written in units of one 8-row group x one 8-wide K half: 32 lanes, lane =
+// 4 (r % 8) + j, two consecutive k = 8 h + 2 j, 8 h + 2 j + 1, so that each store of a
+// slice is one contiguous 128-byte core matrix
+template <int NS>
+__device__ __forceinline__ void split_pair(double v0, double v1, double scale,
+                                           __nv_bfloat16 *chunk, int h, int lane) {
+  int d0[NS], d1[NS];
+  balanced_digits<NS>(__double2ll_rn(v0 * scale), d0);
+  balanced_digits<NS>(__double2ll_rn(v1 * scale), d1);
+  store_pairs<NS>(chunk + h * 64 + (lane >> 2) * 8 + (lane & 3) * 2, d0, d1);
+}
+
+// Digit planes of op(X) = X (rows contiguous along K): one warp per (8-row group, run of
+// kSplitSeg K), one K half (8 wide) of the group per step, four steps in flight
+constexpr int64_t kSplitSeg = 1024;
 template <int NS>
 __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
                                      int64_t ld, int64_t sX, const unsigned *__restrict__ e,
                                      __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t plane = batch * rows * Kp;
+  const int64_t G = (rows + 7) / 8, KB = Kp / 16;
   const int64_t nseg = (Kp + kSplitSeg - 1) / kSplitSeg;
   for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-       item < batch * rows * nseg; item += nwarps) {
-    const int64_t w = item / nseg, seg = item - w * nseg;
-    const int64_t b = w / rows, r = w - b * rows;
-    const double *x = X + b * sX + r * ld;
-    const int ex = decode_exp(e[w]);
+       item < batch * G * nseg; item += nwarps) {
+    const int64_t bg = item / nseg, seg = item - bg * nseg;
+    const int64_t b = bg / G, g = bg - b * G;
+    const int64_t r = g * 8 + (lane >> 2);
+    const bool live = r < rows;
+    const double *x = X + b * sX + (live ? r : 0) * ld;
+    const int ex = live ? decode_exp(e[b * rows + r]) : 0;
     const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
-    __nv_bfloat16 *o = out + w * Kp;
-    const int64_t kend = min(Kp, (seg + 1) * kSplitSeg);
-    for (int64_t k = seg * kSplitSeg + 2 * lane; k < kend; k += 64) {
-      const double v0 = k < K ? x[k] : 0.0, v1 = k + 1 < K ? x[k + 1] : 0.0;
-      int d0[NS], d1[NS];
-      balanced_digits<NS>(__double2ll_rn(v0 * scale), d0);
-      balanced_digits<NS>(__double2ll_rn(v1 * scale), d1);
-      store_pairs<NS>(o + k, plane, d0, d1);
+    const int64_t h0 = seg * (kSplitSeg / 8), h1 = min(Kp, (seg + 1) * kSplitSeg) / 8;
+    for (int64_t hb = h0; hb < h1; hb += 4) {   // K halves hb .. hb + 3 (h1 - h0 is even)
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = (hb + u) * 8 + (lane & 3) * 2;
+        const bool in = live && hb + u < h1;
+        v[2 * u] = (in && k < K) ? x[k] : 0.0;
+        v[2 * u + 1] = (in && k + 1 < K) ? x[k + 1] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (hb + u >= h1) break;
+        const int64_t kb = (hb + u) >> 1;
+        __nv_bfloat16 *chunk = out + ((bg * KB + kb) * NS) * (CHUNK_BYTES / 2);
+        split_pair<NS>(v[2 * u], v[2 * u + 1], scale, chunk, (int)((hb + u) & 1), lane);
+      }
     }
   }
 }
 
 // Digit planes of op(X) = X^T (X stored K x rows): 32 rows x 64 k tiles transposed
-// through shared memory, then each lane two consecutive k of one row, as above
+// through shared memory (loads coalesced along the rows), then each warp writes whole
+// core matrices as above
 template <int NS>
 __global__ void oz_split_cols_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
                                      int64_t ld, int64_t sX, const unsigned *__restrict__ e,
                                      __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
-  __shared__ double tile[32][65];   // [row][k]
-  const int64_t rt = (rows + 31) / 32, kt = (Kp + 63) / 64;
+  __shared__ double tile[64][33];   // [k][row]
+  const int64_t G = (rows + 7) / 8, KB = Kp / 16;
+  const int64_t rt = (G + 3) / 4, kt = Kp / 64;   // Kp is a multiple of 64
   const int64_t ntiles = rt * kt * batch;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  const int64_t plane = batch * rows * Kp;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t b = t / (rt * kt), rem = t % (rt * kt);
     const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 64;
@@ -756,19 +823,23 @@ __global__ void oz_split_cols_kernel(const double *__restrict__ X, int64_t rows,
     __syncthreads();
     for (int i = ty; i < 64; i += 8) {   // k = k0 + i, lanes along the rows (contiguous)
       const int64_t k = k0 + i, r = r0 + tx;
-      tile[tx][i] = (k < K && r < rows) ? Xb[k * ld + r] : 0.0;
+      tile[i][tx] = (k < K && r < rows) ? Xb[k * ld + r] : 0.0;
     }
     __syncthreads();
-    const int64_t k = k0 + 2 * tx;
-    for (int i = ty; i < 32; i += 8) {
-      const int64_t r = r0 + i;
-      if (r >= rows || k >= Kp) continue;
-      const int ex = decode_exp(e[b * rows + r]);
+    // 4 groups x 8 K halves = 32 core matrices per tile, four per warp
+    const int rr = tx >> 2, jj = tx & 3;
+    for (int c = ty; c < 32; c += 8) {
+      const int gl = c >> 3, hl = c & 7;   // group within the tile, K half within the tile
+      const int64_t g = (r0 >> 3) + gl;
+      if (g >= G) continue;
+      const int64_t r = g * 8 + rr;
+      const int ex = r < rows ? decode_exp(e[b * rows + r]) : 0;
       const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
-      int d0[NS], d1[NS];
-      balanced_digits<NS>(__double2ll_rn(tile[i][2 * tx] * scale), d0);
-      balanced_digits<NS>(__double2ll_rn(tile[i][2 * tx + 1] * scale), d1);
-      store_pairs<NS>(out + (b * rows + r) * Kp + k, plane, d0, d1);
+      const int kl = hl * 8 + jj * 2;
+      const int64_t kb = (k0 >> 4) + (hl >> 1);
+      __nv_bfloat16 *chunk = out + (((b * G + g) * KB + kb) * NS) * (CHUNK_BYTES / 2);
+      split_pair<NS>(tile[kl][gl * 8 + rr], tile[kl + 1][gl * 8 + rr], scale, chunk, hl & 1,
+                     tx);
     }
   }
 }
@@ -777,12 +848,13 @@ template <int NS>
 static void launch_split(const double *X, int64_t rows, int64_t K, int64_t ld, int64_t sX,
                          bool trans, const unsigned *e, __nv_bfloat16 *out, int64_t Kp,
                          int64_t batch, cudaStream_t s) {
+  const int64_t G = (rows + 7) / 8;
   if (trans) {
-    const int64_t t = ((rows + 31) / 32) * ((Kp + 63) / 64) * batch;
+    const int64_t t = ((G + 3) / 4) * (Kp / 64) * batch;
     oz_split_cols_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32),
                                dim3(32, 8), 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
   } else {
-    const int64_t warps = rows * batch * ((Kp + kSplitSeg - 1) / kSplitSeg);
+    const int64_t warps = G * batch * ((Kp + kSplitSeg - 1) / kSplitSeg);
     oz_split_rows_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>((warps + 7) / 8, 1),
                                                             148 * 16),
                                256, 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
@@ -819,17 +891,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
+// the pre-tiled planes as a 5-d tensor {128 BF16 (one 256-byte run), slice, K block,
+// 8-row group, batch}; a box is every slice of box_rows / 8 groups at one K block, landing
+// in shared memory as [group][slice][256 B]; groups beyond G read as zeros
 static CUtensorMap tmap(const void *base, int64_t Kp, int64_t rows, int64_t batch, int ns,
                         int box_rows = 128) {
   CUtensorMap m;
-  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch, (cuuint64_t)ns};
-  cuuint64_t strides[3] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2),
-                           (cuuint64_t)(batch * rows * Kp * 2)};
-  cuuint32_t box[4] = {(cuuint32_t)KS, (cuuint32_t)box_rows, 1, 1};   // 16 BF16 = 32-byte rows
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims,
+  const int64_t G = (rows + 7) / 8, KB = Kp / 16, run = CHUNK_BYTES;
+  cuuint64_t dims[5] = {(cuuint64_t)(CHUNK_BYTES / 2), (cuuint64_t)ns, (cuuint64_t)KB,
+                        (cuuint64_t)G, (cuuint64_t)batch};
+  cuuint64_t strides[4] = {(cuuint64_t)run, (cuuint64_t)(ns * run), (cuuint64_t)(KB * ns * run),
+                           (cuuint64_t)(G * KB * ns * run)};
+  cuuint32_t box[5] = {(cuuint32_t)(CHUNK_BYTES / 2), (cuuint32_t)ns, 1, (cuuint32_t)(box_rows / 8),
+                       1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(TRG_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return m;
@@ -882,7 +960,8 @@ OzOperand oz_prepare(const double *X, int64_t rows, int64_t K, int64_t ld, int64
   o.batch = batch;
   o.ns = ns;
   unsigned *e = (unsigned *)scr.alloc((size_t)batch * rows * sizeof(unsigned));
-  __nv_bfloat16 *pl = (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * rows * o.Kp * 2);
+  __nv_bfloat16 *pl =
+      (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * ((rows + 7) / 8 * 8) * o.Kp * 2);
   if (!trans && K <= 128) {
     const int64_t t = (rows * batch + 255) / 256;
     oz_rowexp_small_kernel<<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 64),

@@ -5,8 +5,10 @@
 namespace trg {
 
 // Digit planes of one operand op(X) (rows x K; trans: X stored K x rows) as the kernel
-// reads them: exponent codes [batch][rows] and planes [ns][batch][rows][Kp].  An operand
-// that several products share can be split once (oz_prepare) and passed to each.
+// reads them: exponent codes [batch][rows] and planes pre-tiled per (batch, 8-row group,
+// 16-wide K block, slice) in 256-byte runs (the MMA's core-matrix layout; gemm_oz.cu).
+// An operand that several products share can be split once (oz_prepare) and passed to
+// each.
 struct OzOperand {
   const unsigned *e = nullptr;
   const void *planes = nullptr;
