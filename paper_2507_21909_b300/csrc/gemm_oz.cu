@@ -18,24 +18,29 @@
 // memory (two accumulators, alternating chunks) so the next chunk's products do not
 // wait for the drain.  The epilogue forms C = alpha 2^(e_r + e_c - 40) acc + beta C.
 //
-// CTA = 12 warps: warp 0 TMA producer, warp 1 MMA issuer (M = 128, N = 128, K = 16),
-// warps 2..9 drain TMEM (two warps per 32-lane quadrant, 64 columns each).  A pipeline
-// stage holds one 16-wide K block of every digit slice of A and of B, so each slice tile
-// is loaded once and serves all pairs (i, j) that use it.  The digit planes are stored
-// pre-tiled in the tensor cores' unswizzled K-major layout (8-row x 16-byte core
-// matrices, the two K halves of a 16-wide block 128 bytes apart, the digit slices of one
-// 8-row group side by side): one TMA box per operand and stage then moves 256-byte
-// contiguous runs, where a row-major plane would need one 32-byte request per row and
-// slice, which saturates the SM-to-L2 request path before the tensor pipe.  At the first
-// stage of a chunk the lower-level pairs are issued before waiting
-// for the drain of the previous chunk's exact levels, and the drain warps read those
-// first and signal them separately from the H buffer (which is reused two chunks later),
-// so the issuer waits only for the exact levels.
+// Persistent kernel, one CTA (12 warps) per SM walking the output tiles: warp 0 TMA
+// producer, warp 1 MMA issuer (M = 128, N = 128, K = 16), warps 2..9 drain TMEM (two
+// warps per 32-lane quadrant, 64 columns each) and write the outputs from their
+// registers while the next tile's products already run.  A pipeline stage holds one
+// 16-wide K block of every digit slice of A and of B, so each slice tile is loaded once
+// and serves all pairs (i, j) that use it.  The digit planes are stored pre-tiled in the
+// tensor cores' unswizzled K-major layout (8-row x 16-byte core matrices, the two K halves
+// of a 16-wide block 128 bytes apart, the digit slices of one 8-row group side by side):
+// one TMA box per operand and stage then moves 256-byte contiguous runs, where a
+// row-major plane would need one 32-byte request per row and slice, which saturates the
+// SM-to-L2 request path before the tensor pipe.  At the first stage of a chunk the
+// lower-level pairs are issued before waiting for the drain of the previous chunk's exact
+// levels, and the drain warps read those first and signal them separately from the H
+// buffer (which is reused two chunks later), so the issuer waits only for the exact
+// levels.  Every wait is bounded (2^31 cycles): on a timeout the device flag is set, the
+// roles stop, the CTA waits (bounded) for its loads and products in flight and frees its
+// tensor memory; the output is then undefined and the host reports TRG_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
@@ -46,28 +51,26 @@
 namespace trg {
 namespace oz {
 
-constexpr int BM = 128, BN = 128;
+constexpr int BM = 128;
 constexpr int BK = 64;                      // K padding granule of the digit planes
 constexpr int KS = 16;                      // K per pipeline stage (= one MMA, 32-byte rows)
 constexpr int CHUNK_K = 512;                // exact chunk of the exact levels
 constexpr int CHUNK_KS = CHUNK_K / KS;      // stages per chunk
-constexpr uint32_t SLICE_TILE = BM * KS * 2;    // 4 KB: 128 rows x 16 K of one slice
 constexpr uint32_t CHUNK_BYTES = 256;           // one 8-row group x 16 K of one slice
-constexpr size_t kStageBudget = 200 * 1024;     // shared memory for the stage ring
+constexpr size_t kSmemOptin = 232448;           // dynamic shared memory per block (opt-in)
 constexpr int MAX_STAGES = 8;
-// 12 warps: registers are allocated in groups of four warps, so a 10-warp block costs
-// as much as 12; warps 10 and 11 only take part in the block-wide barriers
-constexpr int NWARPS = 12, THREADS = NWARPS * 32;
-constexpr int MAX_PAIRS = 36;
+// 18 warps: producer, issuer and 16 drain warps (four per 32-lane TMEM quadrant, a
+// quarter of the tile's columns each, so that a drain warp's int64 accumulators fit its
+// registers: 65536 / 576 threads)
+constexpr int NDRAIN = 16, NWARPS = 2 + NDRAIN, THREADS = NWARPS * 32;
 constexpr int kGroupM = 12;                 // row tiles per CTA-order group (~sqrt(148))
 constexpr uint32_t TMEM_COLS = 512;         // L0 @0, L1 @128, H @256 / @384 (alternating)
 
 struct Params {
   int64_t M, N, Kp, batch;
   int nks;                                  // K stages per split (multiple of CHUNK_KS)
-  int ns, stages;                           // digit slices; stages in the ring
-  int npairs;
-  int pi[MAX_PAIRS], pj[MAX_PAIRS], pl[MAX_PAIRS];  // slice of A, slice of B, level 0/1/2
+  int ksplit;                               // K splits (tiles per output tile)
+  int stages;                               // stages in the ring
   const unsigned *ea, *eb;                  // row exponent codes [batch][M], [batch][N]
   double alpha, beta;
   double *C;
@@ -123,9 +126,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) |
          ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46);
 }
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
 __device__ __forceinline__ void tld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -152,82 +152,94 @@ __device__ __forceinline__ void tld32(uint32_t taddr, uint32_t (&r)[32]) {
 // row exponent codes: e + 4096, 0 for an all-zero row
 __device__ __forceinline__ int decode_exp(unsigned code) { return code ? (int)code - 4096 : 0; }
 
-__device__ __forceinline__ void umma(uint32_t acc_t, uint64_t da, uint64_t db, uint32_t accum) {
+// Tile shape of a digit form: NL exact levels (one accumulator each), the lower levels in
+// one FP32 accumulator per chunk (two buffers, alternating chunks), TBN output columns,
+// FRAC fractional bits of the int64 fixed-point accumulator.
+//   ns = 3..6: NL = 2, TBN = 128, FRAC = 12   (L0 @ 0, L1 @ 128, H @ 256 / 384)
+//   ns = 7:    NL = 4, TBN = 64,  FRAC = 16   (L0..L3 @ 0, 64, 128, 192, H @ 256 / 320)
+// The seven-digit form is the FP64-equivalent one: over a 512-deep chunk a level l sums
+// l + 1 digit products of at most 128 x 64 per k (<= 1.26e7 < 2^24 for l = 3), so levels
+// 0..3 are exact FP32 integers, and the levels >= 4 (2^-14 and below of the result, in
+// ^a ^b units) carry the FP32 rounding of one chunk; |acc| <= K 2^44, so K per split stays
+// <= 2^18, and the error of a product is about 2^-50 of max|a| max|b| per chunk, the level
+// of an FP64 dot product, from 28 digit products.  Its tiles are 128 x 64 so that six
+// 64-column accumulators fit the 512 TMEM columns.
+template <int NS>
+struct Form {
+  static constexpr int NL = NS == 7 ? 4 : 2;
+  static constexpr int TBN = NS == 7 ? 64 : 128;
+  static constexpr int FRAC = NS == 7 ? 16 : 12;
+  static constexpr uint32_t A_TILE = BM * KS * 2;            // 4 KB per slice
+  static constexpr uint32_t B_TILE = TBN * KS * 2;
+  static constexpr uint32_t STAGE = NS * (A_TILE + B_TILE);
+  // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+constexpr int64_t kXMaxKSplit = int64_t(1) << 18;   // K per split of the seven-digit form
+
+// epilogue staging: every drain warp stages 32 rows x kEpiCols doubles at a time
+constexpr int kEpiCols = 4;
+constexpr uint32_t kEpiBytes = (uint32_t)NDRAIN * 32u * (kEpiCols + 1) * 8u;
+
+__device__ __forceinline__ void umma(uint32_t acc_t, uint64_t da, uint64_t db, uint32_t idesc,
+                                     uint32_t accum) {
   asm volatile(
       "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc_t),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+      "l"(da), "l"(db), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
 
-// Store one warp's 32 x W output block, staged in shared memory as st[row][W + 1] (one
-// row per lane, as the TMEM lane layout delivers it), with consecutive lanes on
-// consecutive columns, so every row leaves as contiguous doubles: C = alpha v + beta C,
-// or v into a split-K workspace (to_ws).  With beta != 0 the old values of 8 rows are
-// loaded before any of them is stored, so those loads overlap.
-template <int W>
-__device__ __forceinline__ void store_block(const double *st, int lane, int64_t row0,
-                                            int64_t col0, int64_t M, int64_t N, double *Cbase,
-                                            int64_t ldc, bool to_ws, double alpha,
-                                            double beta) {
-  constexpr int Q = W / 32;
-  const bool rd = !to_ws && beta != 0.0;
-#pragma unroll 1
-  for (int r0 = 0; r0 < 32; r0 += 8) {
-    double old[8 * Q];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int64_t row = row0 + r0 + r, col = col0 + q * 32 + lane;
-        old[r * Q + q] = (rd && row < M && col < N) ? Cbase[row * ldc + col] : 0.0;
-      }
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int64_t row = row0 + r0 + r, col = col0 + q * 32 + lane;
-        if (row < M && col < N) {
-          const double x = st[(r0 + r) * (W + 1) + q * 32 + lane];
-          Cbase[row * ldc + col] = to_ws ? x : rd ? alpha * x + beta * old[r * Q + q] : alpha * x;
-        }
-      }
-  }
-}
-
+// The digit GEMM as a persistent kernel: one CTA per SM walks the output tiles t =
+// blockIdx.x, blockIdx.x + gridDim.x, ... (tile order: per batch member and K split,
+// groups of kGroupM row tiles, column tiles within a group, so that the tiles in flight
+// at one time share their A and B tiles in L2).  The three roles keep running counters
+// across tiles (stages, chunks), so the next tile's loads and products start while the
+// drain warps still write the previous tile's outputs from their registers.
 template <int NS>
 __global__ void __launch_bounds__(THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const Params p) {
+  using F = Form<NS>;
+  constexpr int NL = F::NL, TBN = F::TBN, FRAC = F::FRAC, WC = TBN / 4;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  constexpr int ns = NS;
   const int nst = p.stages;
-  const uint32_t STAGE = 2u * (uint32_t)ns * SLICE_TILE;   // all A slices, then all B slices
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * STAGE);
-  // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] exact
-  // levels of the chunk drained, bar[2nst+2] all done, bar[2nst+3+j] H buffer j drained
+  double *epi = reinterpret_cast<double *>(smem + (size_t)nst * F::STAGE);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * F::STAGE + kEpiBytes);
+  // bar[0..nst) stage full, bar[nst..2nst) stage empty, bar[2nst] products of a chunk
+  // done, bar[2nst+1] exact levels of a chunk drained, bar[2nst+2] every product issued
+  // by this CTA done, bar[2nst+3+j] H buffer j drained (drain barriers: NDRAIN warps)
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * MAX_STAGES + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // CTA order: groups of kGroupM row tiles, column tiles within a group, so that the CTAs
-  // resident at one time cover a near-square patch of output tiles and share their A and
-  // B tiles in L2 (row-tile-fastest order would stream all of A once per few column tiles)
-  int64_t mt, nt;
-  {
-    const int64_t gx = gridDim.x, gy = gridDim.y;
-    const int64_t lin = (int64_t)blockIdx.y * gx + blockIdx.x;
+  const int64_t gx = (p.M + BM - 1) / BM, gy = (p.N + TBN - 1) / TBN;
+  const int64_t per_z = gx * gy, ntiles = per_z * p.batch * p.ksplit;
+  const int nks_total = (int)(p.Kp / KS);
+  struct Tile {
+    int64_t m0, n0, b, split;
+    int ks0, nk, nchunks;
+  };
+  auto tile_of = [&](int64_t t) {
+    Tile o;
+    const int64_t z = t / per_z, lin = t - z * per_z;
     const int64_t g = lin / ((int64_t)kGroupM * gy), idx = lin % ((int64_t)kGroupM * gy);
     const int64_t first = g * kGroupM, gsz = min((int64_t)kGroupM, gx - first);
-    mt = first + idx % gsz;
-    nt = idx / gsz;
-  }
-  const int64_t m0 = mt * BM, n0 = nt * BN;
-  const int64_t b = blockIdx.z % p.batch, split = blockIdx.z / p.batch;
-  const int nks_total = (int)(p.Kp / KS);
-  const int ks0 = (int)split * p.nks;
-  const int nk = max(min(ks0 + p.nks, nks_total) - ks0, 0);
-  const int nchunks = (nk + CHUNK_KS - 1) / CHUNK_KS;
+    o.m0 = (first + idx % gsz) * BM;
+    o.n0 = (idx / gsz) * TBN;
+    o.b = z % p.batch;
+    o.split = z / p.batch;
+    o.ks0 = (int)o.split * p.nks;
+    o.nk = max(min(o.ks0 + p.nks, nks_total) - o.ks0, 0);
+    o.nchunks = (o.nk + CHUNK_KS - 1) / CHUNK_KS;
+    return o;
+  };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < nst; ++st) {
@@ -235,10 +247,10 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mb_init(su32(&bar[nst + st]), 1);
     }
     mb_init(su32(&bar[2 * nst]), 1);
-    mb_init(su32(&bar[2 * nst + 1]), 8 * 32);
+    mb_init(su32(&bar[2 * nst + 1]), NDRAIN * 32);
     mb_init(su32(&bar[2 * nst + 2]), 1);
-    mb_init(su32(&bar[2 * nst + 3]), 8 * 32);
-    mb_init(su32(&bar[2 * nst + 4]), 8 * 32);
+    mb_init(su32(&bar[2 * nst + 3]), NDRAIN * 32);
+    mb_init(su32(&bar[2 * nst + 4]), NDRAIN * 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -255,383 +267,193 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (warp == 0) {
     if (lane == 0) {  // ------------------------------------------ TMA producer
-      for (int it = 0; it < nk; ++it) {
-        const int st = it % nst;
-        if (!mb_wait(su32(&bar[nst + st]), ((uint32_t)(it / nst) & 1u) ^ 1u)) break;
-        const uint32_t base = su32(smem + (size_t)st * STAGE);
-        const uint32_t full = su32(&bar[st]);
-        mb_expect(full, STAGE);
-        // [16 groups][ns slices][256 B] of A, then the same of B
-        tma5(base, &tmA, full, ks0 + it, (int)(m0 >> 3), (int)b);
-        tma5(base + ns * SLICE_TILE, &tmB, full, ks0 + it, (int)(n0 >> 3), (int)b);
+      int it = 0;     // stages loaded by this CTA so far
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const Tile tl = tile_of(t);
+        for (int i = 0; i < tl.nk; ++i, ++it) {
+          const int st = it % nst;
+          if (!mb_wait(su32(&bar[nst + st]), ((uint32_t)(it / nst) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t base = su32(smem + (size_t)st * F::STAGE);
+          const uint32_t full = su32(&bar[st]);
+          mb_expect(full, F::STAGE);
+          // [16 groups][NS slices][256 B] of A, then [TBN / 8 groups][NS slices][256 B] of B
+          tma5(base, &tmA, full, tl.ks0 + i, (int)(tl.m0 >> 3), (int)tl.b);
+          tma5(base + NS * F::A_TILE, &tmB, full, tl.ks0 + i, (int)(tl.n0 >> 3), (int)tl.b);
+        }
       }
+      // the CTA may not exit with loads in flight: wait for the last load of every stage
+      for (int j = max(it - nst, 0); j < it; ++j)
+        mb_wait(su32(&bar[j % nst]), (uint32_t)(j / nst) & 1u);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------ MMA issuer
-      // per stage: every digit pair (i, j) from the resident slices.  Levels 0 / 1 are
-      // exact per chunk and drained by warps 2..9; at the first stage of a chunk the
-      // lower-level pairs go first, so they overlap the drain of the previous chunk.
-      // descriptors of slice tiles: the stage base's descriptor plus the byte offset / 16
-      // (slices of one 8-row group are 256 bytes apart, groups ns x 256 bytes)
-      constexpr uint64_t kTileStep = CHUNK_BYTES >> 4;
-      bool ok = true;
-      int it = 0;
-      for (int ch = 0; ch < nchunks && ok; ++ch) {
-        const int kbeg = ch * CHUNK_KS, kend = min((ch + 1) * CHUNK_KS, nk);
-        for (int ks = kbeg; ks < kend; ++ks, ++it) {
-          const int st = it % nst;
-          if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t da = sdesc(su32(smem + (size_t)st * STAGE), ns * CHUNK_BYTES);
-          const uint64_t db = da + (uint64_t)((ns * SLICE_TILE) >> 4);
-          // lower levels (i + j >= 2) into this chunk's H buffer; that buffer last held
-          // chunk ch - 2, whose H pass the drain warps finish before they start on the
-          // exact levels of chunk ch - 1 (one barrier per H buffer, one completion per use)
-          if (ks == kbeg && ch >= 2) {
-            if (!mb_wait(su32(&bar[2 * nst + 3 + (ch & 1)]), (uint32_t)((ch - 2) >> 1) & 1u)) {
-              ok = false;
-              break;
+      // per stage: every digit pair (i, j) from the resident slices.  The exact levels
+      // restart every chunk and are drained by warps 2..9; at the first stage of a chunk
+      // the lower-level pairs go first, so they overlap the drain of the previous chunk.
+      // Descriptors of slice tiles: the stage base's plus the byte offset / 16 (slices of
+      // one 8-row group 256 bytes apart, groups NS x 256 bytes).
+      constexpr uint64_t kSl = CHUNK_BYTES >> 4;
+      int it = 0, gch = 0;   // stages consumed, chunks issued (all tiles of this CTA)
+      bool ok = true, issued = false;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const Tile tl = tile_of(t);
+        for (int ch = 0; ch < tl.nchunks && ok; ++ch, ++gch) {
+          const int kbeg = ch * CHUNK_KS, kend = min(kbeg + CHUNK_KS, tl.nk);
+          for (int ks = kbeg; ks < kend; ++ks, ++it) {
+            const int st = it % nst;
+            if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sbase = su32(smem + (size_t)st * F::STAGE);
+            const uint64_t da = sdesc(sbase, NS * CHUNK_BYTES);
+            const uint64_t db = sdesc(sbase + NS * F::A_TILE, NS * CHUNK_BYTES);
+            // lower levels into this chunk's H buffer; that buffer last held chunk gch - 2,
+            // whose H pass the drain warps finish before they start on the exact levels
+            // of chunk gch - 1 (one barrier per H buffer, one completion per use)
+            if (ks == kbeg && gch >= 2) {
+              if (!mb_wait(su32(&bar[2 * nst + 3 + (gch & 1)]),
+                           (uint32_t)((gch - 2) >> 1) & 1u)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          }
-          const uint32_t acc_h = tmem + (uint32_t)((2 + (ch & 1)) * BN);
+            const uint32_t acc_h = tmem + (uint32_t)((NL + (gch & 1)) * TBN);
 #pragma unroll
-          for (int t = 2; t < ns; ++t)
+            for (int l = NL; l < NS; ++l)
 #pragma unroll
-            for (int i = 0; i <= t; ++i)
-              umma(acc_h, da + i * kTileStep, db + (t - i) * kTileStep,
-                   (ks > kbeg || t > 2 || i > 0) ? 1u : 0u);
-          // levels 0 / 1 restart every chunk: the previous chunk's exact levels must be
-          // drained first (its H buffer is drained afterwards, behind these products)
-          if (ks == kbeg && ch > 0) {
-            if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          }
-          const uint32_t acc_l = ks > kbeg ? 1u : 0u;
-          umma(tmem, da, db, acc_l);
-          umma(tmem + BN, da, db + kTileStep, acc_l);
-          umma(tmem + BN, da + kTileStep, db, 1u);
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  su32(&bar[nst + st]))
-              : "memory");
-        }
-        if (!ok) break;
-        // levels 0 / 1 of this chunk complete -> drain
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                su32(&bar[2 * nst]))
-            : "memory");
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bar[2 * nst + 2]))
-          : "memory");
-    }
-  } else if (warp < 10) {  // ------------------------------------------ drain warps 2..9
-    const int ew = warp - 2;                  // 0..7
-    const int quad = warp & 3;                // TMEM lane quadrant of this warp
-    const int half = ew >> 2;                 // columns [64 half, 64 half + 64)
-    const int64_t row = m0 + quad * 32 + lane;
-    long long acc[64];   // fixed point, 12 fractional bits
-#pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0;
-    bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-      // levels 0 and 1 (ns >= 3, so both have pairs): exact integers of this chunk; once
-      // read, the issuer may restart them for the next chunk
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t col = (uint32_t)(half * 64 + c * 16);
-        uint32_t r0[16], r1[16];
-        tld16(lane_base + col, r0);
-        tld16(lane_base + BN + col, r1);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int i0 = __float2int_rn(__uint_as_float(r0[j]) * 0x1.0p-14f);
-          const int i1 = __float2int_rn(__uint_as_float(r1[j]) * 0x1.0p-7f);
-          acc[c * 16 + j] += ((long long)i0 << 26) + ((long long)i1 << 19);
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mb_arrive(su32(&bar[2 * nst + 1]));
-      // this chunk's lower levels, rounded to 2^-12, from H buffer ch & 1
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t col = (uint32_t)(half * 64 + c * 16);
-        uint32_t rh[16];
-        tld16(lane_base + (uint32_t)((2 + (ch & 1)) * BN) + col, rh);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * 4096.0f);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mb_arrive(su32(&bar[2 * nst + 3 + (ch & 1)]));
-    }
-    // warp-uniform (the staged store below synchronises the warp)
-    const bool done =
-        __all_sync(0xffffffffu, ok && nchunks > 0 && mb_wait(su32(&bar[2 * nst + 2]), 0));
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
-    const int64_t ldc = p.to_ws ? p.N : p.ldc;
-    const int er = row < p.M ? decode_exp(p.ea[b * p.M + row]) : 0;
-    if (done) {
-      // every MMA has completed, so the stage ring is free: stage this warp's 32 x 64
-      // block there and store it row-contiguously
-      double *st = reinterpret_cast<double *>(smem) + (size_t)ew * 32 * 65;
-#pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int64_t col = n0 + half * 64 + j;
-        st[lane * 65 + j] = (row < p.M && col < p.N)
-                                ? ldexp((double)acc[j], er + decode_exp(p.eb[b * p.N + col]) - 40)
-                                : 0.0;
-      }
-      __syncwarp();
-      store_block<64>(st, lane, m0 + quad * 32, n0 + half * 64, p.M, p.N, Cbase, ldc, p.to_ws,
-                      p.alpha, p.beta);
-    } else if (row < p.M) {
-      // a pipeline wait gave up (flag set): the output is zeroed, row by row
-      double *crow = Cbase + row * ldc;
-      for (int j = 0; j < 64; ++j) {
-        const int64_t col = n0 + half * 64 + j;
-        if (col < p.N) crow[col] = 0.0;
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
-                 : "memory");
-}
-
-// ------------------------------------------------------ the FP64-equivalent form
-// Seven digits (49 bits of every row of op(A) and column of op(B)) with levels 0..3 exact
-// per chunk: over a 512-deep chunk a level l sums l + 1 digit products of at most
-// 128 x 64 per k (<= 1.26e7 < 2^24 for l = 3), so levels 0..3 are exact FP32 integers;
-// the levels >= 4 (2^-14 and below of the result, ^a ^b units) share one FP32
-// accumulator per chunk (two buffers, alternating chunks).  Every chunk all five are
-// drained into an int64 fixed-point accumulator with XFRAC = 16 fractional bits:
-// |acc| <= K 2^44, so K per split stays <= 2^18.  The error of a product is then about
-// 2^-50 of max|a| max|b| per chunk, the level of an FP64 dot product, from 28 digit
-// products; tiles are 128 x 64 so that six 64-column accumulators fit the 512 TMEM
-// columns (L0..L3 @ 0, 64, 128, 192; H @ 256 / 320).
-constexpr int XNS = 7, XNL = 4, XBN = 64, XFRAC = 16;
-constexpr uint32_t XA_TILE = BM * KS * 2;                  // 4 KB
-constexpr uint32_t XB_TILE = XBN * KS * 2;                 // 2 KB
-constexpr uint32_t XSTAGE = XNS * (XA_TILE + XB_TILE);     // 42 KB
-constexpr int XSTAGES = 4;
-constexpr int64_t kXMaxKSplit = int64_t(1) << 18;
-constexpr uint32_t kIdescX = (1u << 4) | (1u << 7) | (1u << 10) |
-                             ((uint32_t)(XBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void umma_x(uint32_t acc_t, uint64_t da, uint64_t db,
-                                       uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(acc_t),
-      "l"(da), "l"(db), "r"(kIdescX), "r"(accum)
-      : "memory");
-}
-
-__global__ void __launch_bounds__(THREADS, 1)
-ozx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const Params p) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                              ~uintptr_t(1023));
-  constexpr int nst = XSTAGES;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * XSTAGE);
-  // bar[0..nst) full, bar[nst..2nst) empty, bar[2nst] chunk ready, bar[2nst+1] chunk
-  // drained, bar[2nst+2] all done
-  // bar[2nst] chunk ready, bar[2nst+1] exact levels drained, bar[2nst+2] all done,
-  // bar[2nst+3+j] H buffer j drained
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * nst + 5);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t mt, nt;
-  {
-    const int64_t gx = gridDim.x, gy = gridDim.y;
-    const int64_t lin = (int64_t)blockIdx.y * gx + blockIdx.x;
-    const int64_t g = lin / ((int64_t)kGroupM * gy), idx = lin % ((int64_t)kGroupM * gy);
-    const int64_t first = g * kGroupM, gsz = min((int64_t)kGroupM, gx - first);
-    mt = first + idx % gsz;
-    nt = idx / gsz;
-  }
-  const int64_t m0 = mt * BM, n0 = nt * XBN;
-  const int64_t b = blockIdx.z % p.batch, split = blockIdx.z / p.batch;
-  const int nks_total = (int)(p.Kp / KS);
-  const int ks0 = (int)split * p.nks;
-  const int nk = max(min(ks0 + p.nks, nks_total) - ks0, 0);
-  const int nchunks = (nk + CHUNK_KS - 1) / CHUNK_KS;
-
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < nst; ++st) {
-      mb_init(su32(&bar[st]), 1);
-      mb_init(su32(&bar[nst + st]), 1);
-    }
-    mb_init(su32(&bar[2 * nst]), 1);
-    mb_init(su32(&bar[2 * nst + 1]), 8 * 32);
-    mb_init(su32(&bar[2 * nst + 2]), 1);
-    mb_init(su32(&bar[2 * nst + 3]), 8 * 32);
-    mb_init(su32(&bar[2 * nst + 4]), 8 * 32);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     su32(tmem_holder)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_holder;
-
-  if (warp == 0) {
-    if (lane == 0) {  // ------------------------------------------ TMA producer
-      for (int it = 0; it < nk; ++it) {
-        const int st = it % nst;
-        if (!mb_wait(su32(&bar[nst + st]), ((uint32_t)(it / nst) & 1u) ^ 1u)) break;
-        const uint32_t base = su32(smem + (size_t)st * XSTAGE);
-        const uint32_t full = su32(&bar[st]);
-        mb_expect(full, XSTAGE);
-        tma5(base, &tmA, full, ks0 + it, (int)(m0 >> 3), (int)b);
-        tma5(base + XNS * XA_TILE, &tmB, full, ks0 + it, (int)(n0 >> 3), (int)b);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ------------------------------------------ MMA issuer
-      constexpr uint64_t stepA = CHUNK_BYTES >> 4, stepB = CHUNK_BYTES >> 4;
-      bool ok = true;
-      int it = 0;
-      for (int ch = 0; ch < nchunks && ok; ++ch) {
-        const int kbeg = ch * CHUNK_KS, kend = min((ch + 1) * CHUNK_KS, nk);
-        for (int ks = kbeg; ks < kend; ++ks, ++it) {
-          const int st = it % nst;
-          if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sbase = su32(smem + (size_t)st * XSTAGE);
-          const uint64_t da = sdesc(sbase, XNS * CHUNK_BYTES);
-          const uint64_t db = sdesc(sbase + XNS * XA_TILE, XNS * CHUNK_BYTES);
-          // levels >= 4 into this chunk's H buffer, once chunk ch - 2's H pass is drained
-          if (ks == kbeg && ch >= 2) {
-            if (!mb_wait(su32(&bar[2 * nst + 3 + (ch & 1)]), (uint32_t)((ch - 2) >> 1) & 1u)) {
-              ok = false;
-              break;
+              for (int i = 0; i <= l; ++i)
+                umma(acc_h, da + i * kSl, db + (l - i) * kSl, F::IDESC,
+                     (ks > kbeg || l > NL || i > 0) ? 1u : 0u);
+            // exact levels restart every chunk: the previous chunk's must be drained first
+            // (its H buffer is drained afterwards, behind these products)
+            if (ks == kbeg && gch > 0) {
+              if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(gch - 1) & 1u)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          }
-          const uint32_t acc_h = tmem + (uint32_t)((XNL + (ch & 1)) * XBN);
 #pragma unroll
-          for (int t = XNL; t < XNS; ++t)
+            for (int l = 0; l < NL; ++l)
 #pragma unroll
-            for (int i = 0; i <= t; ++i)
-              umma_x(acc_h, da + i * stepA, db + (t - i) * stepB,
-                     (ks > kbeg || t > XNL || i > 0) ? 1u : 0u);
-          // exact levels restart every chunk: the previous chunk's must be drained first
-          if (ks == kbeg && ch > 0) {
-            if (!mb_wait(su32(&bar[2 * nst + 1]), (uint32_t)(ch - 1) & 1u)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          }
-#pragma unroll
-          for (int t = 0; t < XNL; ++t)
-#pragma unroll
-            for (int i = 0; i <= t; ++i)
-              umma_x(tmem + (uint32_t)(t * XBN), da + i * stepA, db + (t - i) * stepB,
+              for (int i = 0; i <= l; ++i)
+                umma(tmem + (uint32_t)(l * TBN), da + i * kSl, db + (l - i) * kSl, F::IDESC,
                      (ks > kbeg || i > 0) ? 1u : 0u);
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  su32(&bar[nst + st]))
-              : "memory");
+            umma_commit(su32(&bar[nst + st]));
+            issued = true;
+          }
+          if (!ok) break;
+          umma_commit(su32(&bar[2 * nst]));   // this chunk's products complete -> drain
         }
-        if (!ok) break;
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                su32(&bar[2 * nst]))
-            : "memory");
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bar[2 * nst + 2]))
-          : "memory");
+      // every product has completed before the tensor memory is released
+      if (issued) {
+        umma_commit(su32(&bar[2 * nst + 2]));
+        mb_wait(su32(&bar[2 * nst + 2]), 0);
+      }
     }
-  } else if (warp < 10) {  // ------------------------------------------ drain warps 2..9
-    const int ew = warp - 2;                  // 0..7
+  } else {  // ------------------------------------------ drain warps 2..17
+    const int ew = warp - 2;                  // 0..15
     const int quad = warp & 3;                // TMEM lane quadrant of this warp
-    const int half = ew >> 2;                 // columns [32 half, 32 half + 32)
-    const int64_t row = m0 + quad * 32 + lane;
-    long long acc[32];   // fixed point, XFRAC fractional bits
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
+    const int qc = ew >> 2;                   // columns [WC qc, WC qc + WC)
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    double *st = epi + (size_t)ew * 32 * (kEpiCols + 1);
+    int gch = 0;
     bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      if (!mb_wait(su32(&bar[2 * nst]), (uint32_t)ch & 1u)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-      // the exact levels first (the issuer restarts them once they are read), then H
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const Tile tl = tile_of(t);
+      long long acc[WC];   // fixed point, FRAC fractional bits
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const uint32_t col = (uint32_t)(half * 32 + c * 16);
+      for (int j = 0; j < WC; ++j) acc[j] = 0;
+      for (int ch = 0; ch < tl.nchunks; ++ch, ++gch) {
+        // warp-uniform: the tensor-memory loads below are warp-collective
+        ok = __all_sync(0xffffffffu, mb_wait(su32(&bar[2 * nst]), (uint32_t)gch & 1u));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // exact level l holds integers x 2^(14 - 7l): add them at 2^(14 - 7l + FRAC)
 #pragma unroll
-        for (int t = 0; t < XNL; ++t) {
-          uint32_t r[16];
-          tld16(lane_base + (uint32_t)(t * XBN) + col, r);
+        for (int c = 0; c < WC / 16; ++c) {
+          const uint32_t col = (uint32_t)(qc * WC + c * 16);
+#pragma unroll
+          for (int l = 0; l < NL; ++l) {
+            uint32_t r[16];
+            tld16(lane_base + (uint32_t)(l * TBN) + col, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const float unit = __int_as_float((127 - 14 + 7 * l) << 23);   // 2^(7l - 14)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              acc[c * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * unit)
+                                 << (14 - 7 * l + FRAC);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mb_arrive(su32(&bar[2 * nst + 1]));
+        // this chunk's lower levels, rounded to 2^-FRAC, from H buffer gch & 1
+#pragma unroll
+        for (int c = 0; c < WC / 16; ++c) {
+          const uint32_t col = (uint32_t)(qc * WC + c * 16);
+          uint32_t rh[16];
+          tld16(lane_base + (uint32_t)((NL + (gch & 1)) * TBN) + col, rh);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          // level t holds integers x 2^(14 - 7t); add them at 2^(14 - 7t + XFRAC)
-          const float unit = __int_as_float((127 - 14 + 7 * t) << 23);   // 2^(7t - 14)
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            acc[c * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * unit)
-                               << (14 - 7 * t + XFRAC);
+            acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * (float)(1 << FRAC));
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mb_arrive(su32(&bar[2 * nst + 3 + (gch & 1)]));
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mb_arrive(su32(&bar[2 * nst + 1]));
+      if (!ok) break;
+      // epilogue from registers (the tensor memory is already free for the next tile):
+      // C = alpha 2^(e_r + e_c - 28 - FRAC) acc + beta C, or the raw value into the
+      // split-K workspace; kEpiCols columns at a time are staged as st[row][kEpiCols + 1]
+      // (one row per lane, as the TMEM lane layout delivers it) and leave row-contiguous
+      const int64_t row = tl.m0 + quad * 32 + lane;
+      double *Cbase = p.to_ws ? p.C + ((tl.split * p.batch + tl.b) * p.M) * p.N
+                              : p.C + tl.b * p.sC;
+      const int64_t ldc = p.to_ws ? p.N : p.ldc;
+      const bool rd = !p.to_ws && p.beta != 0.0;
+      const int er = row < p.M ? decode_exp(p.ea[tl.b * p.M + row]) : 0;
+      const int64_t col0 = tl.n0 + qc * WC;
+      constexpr int RPI = 32 / kEpiCols;                 // rows per store instruction
+      const int rs = lane / kEpiCols, cs = lane % kEpiCols;
+      // one pass per kEpiCols columns, not unrolled: the accumulators shift down by
+      // kEpiCols after each pass, so every pass reads acc[0 .. kEpiCols) (registers)
+#pragma unroll 1
+      for (int q = 0; q < WC / kEpiCols; ++q) {
+        const int64_t cb = col0 + q * kEpiCols;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const uint32_t col = (uint32_t)(half * 32 + c * 16);
-        uint32_t rh[16];
-        tld16(lane_base + (uint32_t)((XNL + (ch & 1)) * XBN) + col, rh);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int j = 0; j < kEpiCols; ++j) {
+          const int64_t col = cb + j;
+          st[lane * (kEpiCols + 1) + j] =
+              (row < p.M && col < p.N)
+                  ? ldexp((double)acc[j], er + decode_exp(p.eb[tl.b * p.N + col]) - 28 - FRAC)
+                  : 0.0;
+        }
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          acc[c * 16 + j] += __float2ll_rn(__uint_as_float(rh[j]) * (float)(1 << XFRAC));
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mb_arrive(su32(&bar[2 * nst + 3 + (ch & 1)]));
-    }
-    // warp-uniform (the staged store below synchronises the warp)
-    const bool done =
-        __all_sync(0xffffffffu, ok && nchunks > 0 && mb_wait(su32(&bar[2 * nst + 2]), 0));
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    double *Cbase = p.to_ws ? p.C + ((split * p.batch + b) * p.M) * p.N : p.C + b * p.sC;
-    const int64_t ldc = p.to_ws ? p.N : p.ldc;
-    const int er = row < p.M ? decode_exp(p.ea[b * p.M + row]) : 0;
-    if (done) {
-      double *st = reinterpret_cast<double *>(smem) + (size_t)ew * 32 * 33;
+        for (int j = 0; j < WC - kEpiCols; ++j) acc[j] = acc[j + kEpiCols];
+        __syncwarp();
+        const int64_t col = cb + cs;
+        double old[32 / RPI];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t col = n0 + half * 32 + j;
-        st[lane * 33 + j] =
-            (row < p.M && col < p.N)
-                ? ldexp((double)acc[j], er + decode_exp(p.eb[b * p.N + col]) - 28 - XFRAC)
-                : 0.0;
-      }
-      __syncwarp();
-      store_block<32>(st, lane, m0 + quad * 32, n0 + half * 32, p.M, p.N, Cbase, ldc, p.to_ws,
-                      p.alpha, p.beta);
-    } else if (row < p.M) {
-      double *crow = Cbase + row * ldc;
-      for (int j = 0; j < 32; ++j) {
-        const int64_t col = n0 + half * 32 + j;
-        if (col < p.N) crow[col] = 0.0;
+        for (int u = 0; u < 32 / RPI; ++u) {
+          const int64_t rr = tl.m0 + quad * 32 + u * RPI + rs;
+          old[u] = (rd && rr < p.M && col < p.N) ? Cbase[rr * ldc + col] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 32 / RPI; ++u) {
+          const int lr = u * RPI + rs;
+          const int64_t rr = tl.m0 + quad * 32 + lr;
+          if (rr < p.M && col < p.N) {
+            const double x = st[lr * (kEpiCols + 1) + cs];
+            Cbase[rr * ldc + col] =
+                p.to_ws ? x : rd ? p.alpha * x + p.beta * old[u] : p.alpha * x;
+          }
+        }
+        __syncwarp();
       }
     }
   }
@@ -913,8 +735,8 @@ static CUtensorMap tmap(const void *base, int64_t Kp, int64_t rows, int64_t batc
   return m;
 }
 
-// stage ring + alignment slack + barriers and the TMEM address
-constexpr size_t kSmemMax = kStageBudget + 1024 + 256;
+// alignment slack, barriers and the TMEM address beside the stage ring and the staging
+constexpr size_t kSmemFixed = 1024 + 256 + kEpiBytes;
 
 }  // namespace oz
 
@@ -993,9 +815,9 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   using namespace oz;
   if (M == 0 || N == 0 || batch == 0) return;
   if (ns < 3 || ns > 7) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 7");
-  const bool x7 = ns == XNS;   // the FP64-equivalent form: its own kernel and tile width
-  const int bn = x7 ? XBN : BN;
-  if (batch > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: batch too large");
+  const bool x7 = ns == 7;     // the FP64-equivalent form: its own tile width
+  const int bn = x7 ? Form<7>::TBN : Form<5>::TBN;
+  const size_t stage_bytes = (size_t)ns * (BM + bn) * KS * 2;
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
   auto fits = [&](const OzOperand *o, int64_t rows) {
     return o && o->rows == rows && o->K == K && o->Kp == Kp && o->batch == batch && o->ns == ns;
@@ -1006,8 +828,6 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   const bool gram = A == B && ta != tb && M == N && lda == ldb && sA == sB;
   OzOperand oa = pa ? *pa : oz_prepare(A, M, K, lda, sA, ta, batch, ns, scr, s);
   OzOperand ob = pb ? *pb : gram ? oa : oz_prepare(B, N, K, ldb, sB, !tb, batch, ns, scr, s);
-  const unsigned *ea = oa.e, *eb = ob.e;
-  const void *As = oa.planes, *Bs = ob.planes;
   Params p{};
   p.M = M;
   p.N = N;
@@ -1015,26 +835,46 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   p.batch = batch;
   p.alpha = alpha;
   p.beta = beta;
-  p.ea = ea;
-  p.eb = eb;
-  p.npairs = 0;
-  for (int t = 0; t < ns; ++t)        // level order: L0, L1, then the rest
-    for (int i = 0; i <= t; ++i) {
-      p.pi[p.npairs] = i;
-      p.pj[p.npairs] = t - i;
-      p.pl[p.npairs] = t < 2 ? t : 2;
-      ++p.npairs;
-    }
+  p.ea = oa.e;
+  p.eb = ob.e;
+  const int npairs = ns * (ns + 1) / 2;    // digit pairs i + j <= ns - 1
   const int64_t gx = (M + BM - 1) / BM, gy = (N + bn - 1) / bn;
-  if (gy > 65535) throw Error(TRG_ERR_ARG, "gemm_oz: N too large");
   const int nks_total = (int)(Kp / KS);
-  int ksplit = 1;
+  // thread-safe one-time setup (function-local static initialisation): the shared-memory
+  // opt-in and the number of SMs (one persistent CTA each)
+  static const int n_sm = [] {
+    for (const void *k : {(const void *)oz_gemm_kernel<3>, (const void *)oz_gemm_kernel<4>,
+                          (const void *)oz_gemm_kernel<5>, (const void *)oz_gemm_kernel<6>,
+                          (const void *)oz_gemm_kernel<7>})
+      TRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemOptin));
+    int dev = 0, n = 0;
+    TRG_CUDA(cudaGetDevice(&dev));
+    TRG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(n, 1);
+  }();
+  // K splits: the count that minimises the estimated time, in K stages (about 0.5 us
+  // each), of ceil(tiles / SMs) rounds of (stages per split + 8 for a tile's fixed cost),
+  // plus the split-K workspace round trip at HBM speed; a further split must gain 3 %
   const int64_t tiles = gx * gy * batch;
-  if (tiles < 148 && nks_total >= 2 * CHUNK_KS) {
-    ksplit = (int)std::min<int64_t>(std::min<int64_t>((2 * 148 + tiles - 1) / tiles,
-                                                      nks_total / CHUNK_KS),
-                                    65535 / batch);
-    ksplit = std::max(ksplit, 1);
+  auto est = [&](int ks) {
+    int per = (nks_total + ks - 1) / ks;
+    per = (per + CHUNK_KS - 1) / CHUNK_KS * CHUNK_KS;
+    const int kse = (nks_total + per - 1) / per;
+    const double rounds = std::ceil((double)(tiles * kse) / n_sm);
+    const double ws = kse > 1 ? (2.0 * kse + 1) * (double)(batch * M * N) * 8 / 6e12 / 0.5e-6 : 0;
+    return rounds * (per + 8.0) + ws;
+  };
+  int ksplit = 1;
+  double t_best = est(1);
+  const int ks_hi = (int)std::min<int64_t>(
+      nks_total / CHUNK_KS, std::max<int64_t>(16, (2 * n_sm + tiles - 1) / tiles));
+  for (int ks = 2; ks <= ks_hi; ++ks) {
+    const double t = est(ks);
+    if (t < 0.97 * t_best) {
+      t_best = t;
+      ksplit = ks;
+    }
   }
   // the fixed-point accumulator holds K 2^41 < 2^63 (K 2^44 in the seven-digit form): at
   // most 2^21 (2^18) K per split
@@ -1044,11 +884,9 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   per = (per + CHUNK_KS - 1) / CHUNK_KS * CHUNK_KS;
   ksplit = (nks_total + per - 1) / per;
   p.nks = per;
-  p.ns = ns;
-  p.stages = x7 ? XSTAGES
-               : (int)std::min<size_t>(MAX_STAGES, kStageBudget / (2 * (size_t)ns * SLICE_TILE));
-  const size_t smem = x7 ? (size_t)XSTAGES * XSTAGE + 1024 + 256
-                         : (size_t)p.stages * 2 * ns * SLICE_TILE + 1024 + 256;
+  p.ksplit = ksplit;
+  p.stages = (int)std::min<size_t>(MAX_STAGES, (kSmemOptin - kSmemFixed) / stage_bytes);
+  const size_t smem = (size_t)p.stages * stage_bytes + kSmemFixed;
   if (ksplit > 1) {
     p.C = (double *)scr.alloc((size_t)ksplit * batch * M * N * sizeof(double));
     p.to_ws = 1;
@@ -1060,17 +898,9 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     p.ldc = ldc;
     p.sC = sC;
   }
-  CUtensorMap ma = tmap(As, Kp, M, batch, ns), mb = tmap(Bs, Kp, N, batch, ns, bn);
-  // thread-safe one-time setup (function-local static initialisation)
-  static const bool attr_done = [] {
-    for (const void *k : {(const void *)oz_gemm_kernel<3>, (const void *)oz_gemm_kernel<4>,
-                          (const void *)oz_gemm_kernel<5>, (const void *)oz_gemm_kernel<6>,
-                          (const void *)ozx_gemm_kernel})
-      TRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kSmemMax));
-    return true;
-  }();
-  (void)attr_done;
+  CUtensorMap ma = tmap(oa.planes, Kp, M, batch, ns), mb = tmap(ob.planes, Kp, N, batch, ns, bn);
+  const int64_t ntiles = gx * gy * batch * ksplit;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, n_sm);
   if (debug_opt("attr")) {
     const void *fns[4] = {(const void *)oz_gemm_kernel<5>, (const void *)oz_rowexp_kernel,
                           (const void *)oz_split_rows_kernel<5>, (const void *)oz_ws_reduce};
@@ -1081,22 +911,22 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
               i, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
               fa.maxDynamicSharedSizeBytes, fa.localSizeBytes);
     }
-    fprintf(stderr, "launch: grid %lld %lld %lld threads %d smem %zu params %zu\n", (long long)gx,
-            (long long)gy, (long long)(batch * ksplit), THREADS, smem, sizeof(Params));
+    fprintf(stderr, "launch: tiles %lld x %lld x %lld, grid %u threads %d smem %zu stages %d\n",
+            (long long)gx, (long long)gy, (long long)(batch * ksplit), grid, THREADS, smem,
+            p.stages);
   }
-  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(batch * ksplit));
   if (timing) timing->before(s);
   switch (ns) {
     case 3: oz_gemm_kernel<3><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
     case 4: oz_gemm_kernel<4><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
     case 5: oz_gemm_kernel<5><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
     case 6: oz_gemm_kernel<6><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
-    default: ozx_gemm_kernel<<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    default: oz_gemm_kernel<7><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
   }
   TRG_LAUNCH_CHECK();
   if (timing)
     timing->after(s, x7 ? 2 : 0, 2.0 * (double)M * N * K * batch,
-                  2.0 * (double)M * N * K * batch * p.npairs);
+                  2.0 * (double)M * N * K * batch * npairs);
   if (ksplit > 1) {
     const int64_t total = batch * M * N;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
