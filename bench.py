@@ -51,6 +51,10 @@ def args_():
     ap.add_argument("--also-forms", default="",
                     help="comma-separated precision forms also compared against the FP64 "
                          "form in the size-level precision check (e.g. oz4,oz7,tf32x3)")
+    ap.add_argument("--sensitivity", default="",
+                    help="comma-separated D: for each form of --precision and --also-forms, "
+                         "the relative change of f after each of --precision-steps steps when "
+                         "beta changes by a relative 1e-14 (the run's own conditioning)")
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "learned"],
                     help="learned: train the sketch network on rows collected from plain "
@@ -424,6 +428,42 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_sensitivity(a):
+    """Conditioning of the step sequence: f after each step from beta and from
+    beta (1 + 1e-14), same sketches, per form and D; with the smallest relative gap at the
+    step's cuts.  A perturbation of 1e-14 changes f directly by about 1e-14, so a larger
+    relative change measures how much the steps amplify differences at the rounding level."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2507_21909_b300 as trg
+    stream = torch.cuda.Stream()
+    trg.trg_set_stream(stream.cuda_stream)
+    forms = [a.precision] + [x for x in a.also_forms.split(",") if x.strip()]
+    nsteps = a.precision_steps if a.precision_steps > 0 else 6
+    rows = []
+    for D in [int(v) for v in a.sensitivity.split(",") if v.strip()]:
+        for name in forms:
+            runs = []
+            for beta in (a.beta, a.beta * (1 + 1e-14)):
+                trg.trg_set_params(4, 4, 0x5EED, PREC[name])
+                trg.trg_init_ising(4, beta, 0.0)
+                fs, gaps = [], []
+                for k in range(nsteps):
+                    trg.trg_step(k % 4, D, 2 * D)
+                    fs.append(trg.trg_free_energy()[0])
+                    gaps.append(trg.trg_diag()[1])
+                torch.cuda.synchronize()
+                runs.append((fs, gaps))
+            (f0, g0), (f1, _) = runs
+            rows.append({"D": D, "form": name,
+                         "df_rel_per_step": [abs(x - y) / abs(x) for x, y in zip(f0, f1)],
+                         "min_cut_gap_per_step": [g if math.isfinite(g) else None for g in g0]})
+    print(json.dumps({"metric": "relative change of f per step for a relative 1e-14 change of "
+                                "beta", "unit": "1", "steps": nsteps, "beta": a.beta,
+                      "config": {"workload": "4D Ising, h=0, p=2D, q_swap=4, q_rho=4"},
+                      "rows": rows}), flush=True)
+
+
 def run_compare_atrg(a):
     """Steady-state ms per step of the triad step and of the plain ATRG step (the paper's
     comparison, Sec. III C) at each D, 4D Ising, one GPU.  Each method grows its tensor
@@ -527,9 +567,11 @@ def reduce_timing(ms, steps, world, dist=None, device="cpu"):
     return ms_max, world * steps / (ms_max / 1e3)
 
 
-# Traffic of the dominant kernel per launch (dram__bytes_read.sum + dram__bytes_write.sum
-# from one ncu capture), keyed by kernel; None until captured on the current build.
-TRAFFIC = {}
+# Traffic of the dominant kernel per launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the launches of one timed D = 48 OZ5 step of this script, from a one-pass ncu
+# launch list with those two metrics), keyed by GEMM kind; a kind missing here has not
+# been captured on the current build of its kernel.
+TRAFFIC = {"oz": 2.679e9}
 
 
 def roofline(stats, step_ms_total, steps, prec, peak, peak_src):
@@ -547,7 +589,8 @@ def roofline(stats, step_ms_total, steps, prec, peak, peak_src):
     both_ms = stats["oz_ms"] + stats["tc_ms"] + stats["x7_ms"]
     return {
         "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-        "traffic": TRAFFIC.get(k), "peak_source": peak_src, "kernel": name,
+        "traffic": TRAFFIC.get(k), "traffic_unit": "DRAM bytes per launch (ncu, mean)",
+        "peak_source": peak_src, "kernel": name,
         "flop": "algorithmic: 2 M N K per GEMM the step issues (FP64-equivalent product), "
                 "digit/slice products not counted",
         "launches_per_step": n / steps, "alg_flop_per_launch": alg / n if n else 0.0,
@@ -708,5 +751,7 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.compare_atrg:
         run_compare_atrg(a)
+    elif a.sensitivity:
+        run_sensitivity(a)
     else:
         run_ours(a)
