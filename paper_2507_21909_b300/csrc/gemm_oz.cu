@@ -480,21 +480,21 @@ __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int
     const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * KT;
     const int64_t k1 = min(K, k0 + KT);
     const double *Xb = X + b * sX;
-    if (!trans) {  // warp per row, lanes along k, four independent loads in flight
+    if (!trans) {  // warp per row, lanes along k, eight independent loads in flight
       for (int i = warp; i < 32; i += nw) {
         const int64_t r = r0 + i;
         if (r >= rows) continue;
         const double *x = Xb + r * ld;
-        double m = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+        double mm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int64_t k = k0 + lane;
-        for (; k + 96 < k1; k += 128) {
-          m = fmax(m, fabs(x[k]));
-          m1 = fmax(m1, fabs(x[k + 32]));
-          m2 = fmax(m2, fabs(x[k + 64]));
-          m3 = fmax(m3, fabs(x[k + 96]));
+        for (; k + 224 < k1; k += 256) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) mm[u] = fmax(mm[u], fabs(x[k + 32 * u]));
         }
-        for (; k < k1; k += 32) m = fmax(m, fabs(x[k]));
-        m = fmax(fmax(m, m1), fmax(m2, m3));
+        for (; k < k1; k += 32) mm[0] = fmax(mm[0], fabs(x[k]));
+        double m = mm[0];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) m = fmax(m, mm[u]);
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0 && m > 0.0) {
           int ex;
@@ -502,19 +502,20 @@ __global__ void oz_rowexp_kernel(const double *__restrict__ X, int64_t rows, int
           atomicMax(&code[b * rows + r], (unsigned)(ex + 4096));
         }
       }
-    } else {  // lanes along r (contiguous), warps split the k range
+    } else {  // lanes along r (contiguous), warps split the k range, eight loads in flight
       const int64_t r = r0 + lane;
-      double m = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+      double m = 0.0;
       if (r < rows) {
+        double mm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int64_t k = k0 + warp;
-        for (; k + 3 * nw < k1; k += 4 * nw) {
-          m = fmax(m, fabs(Xb[k * ld + r]));
-          m1 = fmax(m1, fabs(Xb[(k + nw) * ld + r]));
-          m2 = fmax(m2, fabs(Xb[(k + 2 * nw) * ld + r]));
-          m3 = fmax(m3, fabs(Xb[(k + 3 * nw) * ld + r]));
+        for (; k + 7 * nw < k1; k += 8 * nw) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) mm[u] = fmax(mm[u], fabs(Xb[(k + u * nw) * ld + r]));
         }
-        for (; k < k1; k += nw) m = fmax(m, fabs(Xb[k * ld + r]));
-        m = fmax(fmax(m, m1), fmax(m2, m3));
+        for (; k < k1; k += nw) mm[0] = fmax(mm[0], fabs(Xb[k * ld + r]));
+        m = mm[0];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) m = fmax(m, mm[u]);
       }
       if (r < rows && m > 0.0) {
         int ex;
@@ -634,15 +635,22 @@ __global__ void oz_split_cols_kernel(const double *__restrict__ X, int64_t rows,
                                      int64_t ld, int64_t sX, const unsigned *__restrict__ e,
                                      __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
   __shared__ double tile[64][33];   // [k][row]
+  __shared__ int64_t s_t[3];         // batch member, first row, first k of the tile
   const int64_t G = (rows + 7) / 8, KB = Kp / 16;
   const int64_t rt = (G + 3) / 4, kt = Kp / 64;   // Kp is a multiple of 64
   const int64_t ntiles = rt * kt * batch;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
-    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 64;
-    const double *Xb = X + b * sX;
     __syncthreads();
+    if (tx == 0 && ty == 0) {   // one thread decodes the tile index
+      const int64_t bb = t / (rt * kt), rem = t % (rt * kt);
+      s_t[0] = bb;
+      s_t[1] = (rem / kt) * 32;
+      s_t[2] = (rem % kt) * 64;
+    }
+    __syncthreads();
+    const int64_t b = s_t[0], r0 = s_t[1], k0 = s_t[2];
+    const double *Xb = X + b * sX;
     for (int i = ty; i < 64; i += 8) {   // k = k0 + i, lanes along the rows (contiguous)
       const int64_t k = k0 + i, r = r0 + tx;
       tile[i][tx] = (k < K && r < rows) ? Xb[k * ld + r] : 0.0;

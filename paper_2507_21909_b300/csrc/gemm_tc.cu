@@ -275,14 +275,21 @@ __global__ void split_kernel(const double *__restrict__ X, int64_t rows, int64_t
                              int64_t sX, int trans, int ns, __nv_bfloat16 *__restrict__ out,
                              int64_t Kp, int64_t batch) {
   __shared__ double tile[32][33];
+  __shared__ int64_t s_t[3];         // batch member, first row, first k of the tile
   const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
   const int64_t ntiles = rt * kt * batch;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
-    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 32;
-    const double *Xb = X + b * sX;
     __syncthreads();
+    if (tx == 0 && ty == 0) {   // one thread decodes the tile index
+      const int64_t bb = t / (rt * kt), rem = t % (rt * kt);
+      s_t[0] = bb;
+      s_t[1] = (rem / kt) * 32;
+      s_t[2] = (rem % kt) * 32;
+    }
+    __syncthreads();
+    const int64_t b = s_t[0], r0 = s_t[1], k0 = s_t[2];
+    const double *Xb = X + b * sX;
     for (int i = ty; i < 32; i += 8) {
       double v = 0.0;
       if (trans) {
@@ -335,14 +342,21 @@ __global__ void split_tf32_kernel(const double *__restrict__ X, int64_t rows, in
                                   int64_t ld, int64_t sX, int trans, int ns,
                                   float *__restrict__ out, int64_t Kp, int64_t batch) {
   __shared__ double tile[32][33];
+  __shared__ int64_t s_t[3];         // batch member, first row, first k of the tile
   const int64_t rt = (rows + 31) / 32, kt = (Kp + 31) / 32;
   const int64_t ntiles = rt * kt * batch;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t b = t / (rt * kt), rem = t % (rt * kt);
-    const int64_t r0 = (rem / kt) * 32, k0 = (rem % kt) * 32;
-    const double *Xb = X + b * sX;
     __syncthreads();
+    if (tx == 0 && ty == 0) {   // one thread decodes the tile index
+      const int64_t bb = t / (rt * kt), rem = t % (rt * kt);
+      s_t[0] = bb;
+      s_t[1] = (rem / kt) * 32;
+      s_t[2] = (rem % kt) * 32;
+    }
+    __syncthreads();
+    const int64_t b = s_t[0], r0 = s_t[1], k0 = s_t[2];
+    const double *Xb = X + b * sX;
     for (int i = ty; i < 32; i += 8) {
       double v = 0.0;
       if (trans) {

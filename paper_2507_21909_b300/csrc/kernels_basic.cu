@@ -90,10 +90,12 @@ __device__ __forceinline__ void batch_offsets(const BatchMap &m, int64_t idx, in
 }
 
 // The innermost axis is kept: rows of L contiguous elements are copied, one block per
-// `rpb` rows; the row offsets are decoded once per row.
+// `rpb` rows; the row offsets are decoded once per row (one thread each), then every warp
+// copies whole rows with its lanes along the row (no index division per element).
 __global__ void permute_rows_kernel(const double *__restrict__ in, double *__restrict__ out,
                                     int64_t rows, int64_t L, int rpb, BatchMap m) {
   __shared__ int64_t s_off[256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int64_t r0 = (int64_t)blockIdx.x * rpb; r0 < rows; r0 += (int64_t)gridDim.x * rpb) {
     __syncthreads();
     if (threadIdx.x < rpb && r0 + threadIdx.x < rows) {
@@ -102,40 +104,72 @@ __global__ void permute_rows_kernel(const double *__restrict__ in, double *__res
       s_off[threadIdx.x] = oi;
     }
     __syncthreads();
-    const int64_t nrow = min((int64_t)rpb, rows - r0);
-    const int64_t n = nrow * L;
-    double *dst = out + r0 * L;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const int64_t r = i / L, j = i - r * L;
-      dst[i] = in[s_off[r] + j];
+    const int nrow = (int)min((int64_t)rpb, rows - r0);
+    if (L >= 32) {
+      for (int r = warp; r < nrow; r += nwarp) {
+        const double *src = in + s_off[r];
+        double *dst = out + (r0 + r) * L;
+        int64_t j = lane;
+        for (; j + 96 < L; j += 128) {   // four loads in flight per lane
+          const double v0 = src[j], v1 = src[j + 32], v2 = src[j + 64], v3 = src[j + 96];
+          dst[j] = v0;
+          dst[j + 32] = v1;
+          dst[j + 64] = v2;
+          dst[j + 96] = v3;
+        }
+        for (; j < L; j += 32) dst[j] = src[j];
+      }
+    } else {   // short rows: threads over the block's rows x L elements (32-bit indices)
+      const int n = nrow * (int)L, l = (int)L;
+      double *dst = out + r0 * L;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int r = i / l, j = i - r * l;
+        dst[i] = in[s_off[r] + j];
+      }
     }
   }
 }
 
-// 32 x 32 tiles through shared memory: reads run along the input's innermost axis (a),
-// writes along the output's innermost axis (b); the other axes are a batch decoded once
-// per tile.
+// 64 x 64 tiles through shared memory: reads run along the input's innermost axis (a),
+// writes along the output's innermost axis (b), 16 loads in flight per thread; the other
+// axes are a batch whose offsets one thread decodes per tile.
+constexpr int kPT = 64;
 __global__ void __launch_bounds__(256)
 permute_tile_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t na,
                     int64_t nbb, int64_t sa_out, int64_t sb_in, int64_t ntiles, BatchMap m) {
-  __shared__ double tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t ta_n = (na + 31) / 32, tb_n = (nbb + 31) / 32;
+  __shared__ double tile[kPT][kPT + 1];
+  __shared__ int64_t s_io[4];   // input offset, output offset, a0, b0 of the tile
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 64 x 4
+  const int64_t ta_n = (na + kPT - 1) / kPT, tb_n = (nbb + kPT - 1) / kPT;
+  const int64_t per = ta_n * tb_n;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t per = ta_n * tb_n;
-    const int64_t bi = t / per, rem = t - bi * per;
-    const int64_t a0 = (rem % ta_n) * 32, b0 = (rem / ta_n) * 32;
-    int64_t oi, oo;
-    batch_offsets(m, bi, oi, oo);
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const int64_t b = b0 + r, a = a0 + tx;
-      if (a < na && b < nbb) tile[r][tx] = in[oi + b * sb_in + a];
+    if (threadIdx.x == 0) {
+      const int64_t bi = t / per, rem = t - bi * per;
+      int64_t oi, oo;
+      batch_offsets(m, bi, oi, oo);
+      s_io[0] = oi;
+      s_io[1] = oo;
+      s_io[2] = (rem % ta_n) * kPT;
+      s_io[3] = (rem / ta_n) * kPT;
     }
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const int64_t a = a0 + r, b = b0 + tx;
-      if (a < na && b < nbb) out[oo + a * sa_out + b] = tile[tx][r];
+    const int64_t oi = s_io[0], oo = s_io[1], a0 = s_io[2], b0 = s_io[3];
+    const int64_t a = a0 + tx;
+    double v[kPT / 4];
+#pragma unroll
+    for (int u = 0; u < kPT / 4; ++u) {
+      const int64_t b = b0 + ty + 4 * u;
+      v[u] = (a < na && b < nbb) ? in[oi + b * sb_in + a] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kPT / 4; ++u) tile[ty + 4 * u][tx] = v[u];
+    __syncthreads();
+    const int64_t bo = b0 + tx;
+#pragma unroll
+    for (int u = 0; u < kPT / 4; ++u) {
+      const int64_t ao = a0 + ty + 4 * u;
+      if (ao < na && bo < nbb) out[oo + ao * sa_out + bo] = tile[tx][ty + 4 * u];
     }
   }
 }
@@ -191,7 +225,7 @@ void permute(const double *in, double *out, const std::vector<int64_t> &dims_in,
       m.s_in[j] = os[j];
       m.s_out[j] = ostr[j] / L;
     }
-    const int rpb = (int)std::max<int64_t>(1, std::min<int64_t>(256, 1024 / L));
+    const int rpb = (int)std::max<int64_t>(8, std::min<int64_t>(256, 4096 / L));
     const int64_t blocks = std::min<int64_t>((rows + rpb - 1) / rpb, 148 * 32);
     permute_rows_kernel<<<(int)blocks, 256, 0, s>>>(in, out, rows, L, rpb, m);
     TRG_LAUNCH_CHECK();
@@ -223,7 +257,7 @@ void permute(const double *in, double *out, const std::vector<int64_t> &dims_in,
     ++m.nb;
   }
   const int64_t nbatch = total / (na * nbb);
-  const int64_t ntiles = nbatch * ((na + 31) / 32) * ((nbb + 31) / 32);
+  const int64_t ntiles = nbatch * ((na + kPT - 1) / kPT) * ((nbb + kPT - 1) / kPT);
   const int64_t blocks = std::min<int64_t>(ntiles, 148 * 64);
   permute_tile_kernel<<<(int)blocks, 256, 0, s>>>(in, out, na, nbb, ostr[q], os[nd - 1],
                                                   ntiles, m);

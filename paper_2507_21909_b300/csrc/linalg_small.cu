@@ -76,16 +76,16 @@ __global__ void chol_rinv_kernel(const double *G, double *R, double *Rinv, int n
   }
 }
 
-// Same factorisation and inverse, held in shared memory as packed upper triangles (row a
-// starts at a n - a (a - 1) / 2): the per-column updates run at shared-memory latency
-// instead of L2 latency.  Every entry sees the same operations in the same order as in
-// chol_rinv_kernel, so the results are identical.  R^-1 lives in shared memory too when
-// both triangles fit, else in the output buffer.
+// Same factorisation, held in shared memory as a packed upper triangle (row a starts at
+// a n - a (a - 1) / 2): the per-column updates run at shared-memory latency instead of L2
+// latency, and every entry of R sees the same operations in the same order as in
+// chol_rinv_kernel.  The inverse is left to inv_upper_kernel (do_inv = 0), which spreads
+// its independent columns over many CTAs.
 __device__ __forceinline__ int pk(int a, int b, int n) { return a * n - (a * (a - 1)) / 2 + (b - a); }
 
 __global__ void __launch_bounds__(512)
 chol_rinv_smem_kernel(const double *G, double *R, double *Rinv, int n, double rel_tol,
-                      double shift_rel, int x_in_smem) {
+                      double shift_rel, int x_in_smem, int do_inv) {
   extern __shared__ double S[];
   double *X = S + (size_t)n * (n + 1) / 2;   // used when x_in_smem
   const int64_t off = (int64_t)blockIdx.x * n * n;
@@ -134,6 +134,7 @@ chol_rinv_smem_kernel(const double *G, double *R, double *Rinv, int n, double re
   }
   for (int a = warp; a < n; a += nw)
     for (int b = lane; b < n; b += 32) r[(int64_t)a * n + b] = b >= a ? S[pk(a, b, n)] : 0.0;
+  if (!do_inv) return;
   // inverse of the upper-triangular R, one thread per column; dead rows give zeros
   for (int c = tid; c < n; c += blockDim.x) {
     for (int i = c + 1; i < n; ++i) x[(int64_t)i * n + c] = 0.0;
@@ -160,6 +161,47 @@ chol_rinv_smem_kernel(const double *G, double *R, double *Rinv, int n, double re
   }
 }
 
+// X = R^-1 of an upper-triangular n x n R (row-major, batch of them), one warp per
+// column c of X (back substitution x_c = 1 / R_cc, x_i = -(sum_{k>i} R_ik x_k) / R_ii for
+// i = c-1 .. 0, lanes over k and a shuffle sum; a zero pivot gives x_i = 0, a dead row),
+// 8 columns per CTA; the triangle of R those columns need is staged in shared memory
+// (packed rows, m = last column + 1), the columns themselves per warp.
+constexpr int kInvCols = 8;
+__global__ void __launch_bounds__(32 * kInvCols)
+inv_upper_kernel(const double *__restrict__ R, double *__restrict__ X, int n) {
+  extern __shared__ double sm[];
+  const int64_t off = (int64_t)blockIdx.y * n * n;
+  const double *r = R + off;
+  double *x = X + off;
+  const int c0 = blockIdx.x * kInvCols, m = min(n, c0 + kInvCols);
+  double *Rs = sm;                                    // packed upper triangle of R[0..m)
+  double *xs = sm + (size_t)m * (m + 1) / 2;          // kInvCols columns of length m
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int a = warp; a < m; a += kInvCols)
+    for (int b = a + lane; b < m; b += 32) Rs[pk(a, b, m)] = r[(int64_t)a * n + b];
+  __syncthreads();
+  const int c = c0 + warp;
+  if (c >= n) return;
+  double *xc = xs + (size_t)warp * m;
+  if (lane == 0) {
+    const double rcc = Rs[pk(c, c, m)];
+    xc[c] = rcc == 0.0 ? 0.0 : 1.0 / rcc;
+  }
+  __syncwarp();
+  for (int i = c - 1; i >= 0; --i) {
+    const int row = pk(i, 0, m);
+    double sum = 0.0;
+    for (int k = i + 1 + lane; k <= c; k += 32) sum += Rs[row + k] * xc[k];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+      const double rii = Rs[row + i];
+      xc[i] = rii == 0.0 ? 0.0 : -sum / rii;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) x[(int64_t)i * n + c] = i <= c ? xc[i] : 0.0;
+}
+
 void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, double rel_tol,
                double shift_rel, cudaStream_t s) {
   if (n == 0 || batch == 0) return;
@@ -172,9 +214,28 @@ void chol_rinv(const double *G, double *R, double *Rinv, int n, int batch, doubl
       return true;
     }();
     (void)attr_done;
+    // the triangle of the last CTA's columns plus its column buffers (<= tri + 8 n doubles)
+    const size_t inv_smem = tri + (size_t)kInvCols * n * sizeof(double);
+    if (inv_smem <= kMaxSmem) {
+      static const bool inv_attr_done = [] {
+        TRG_CUDA(cudaFuncSetAttribute(inv_upper_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kMaxSmem));
+        return true;
+      }();
+      (void)inv_attr_done;
+      chol_rinv_smem_kernel<<<batch, 512, tri, s>>>(G, R, Rinv, n, rel_tol, shift_rel, 0, 0);
+      TRG_LAUNCH_CHECK();
+      inv_upper_kernel<<<dim3((n + kInvCols - 1) / kInvCols, batch), 32 * kInvCols, inv_smem,
+                         s>>>(R, Rinv, n);
+      TRG_LAUNCH_CHECK();
+      return;
+    }
+    // no room for the column buffers beside the triangle: the inverse in the factorising
+    // kernel's own loop (one thread per column)
     const int x_in_smem = 2 * tri <= kMaxSmem;
     chol_rinv_smem_kernel<<<batch, 512, x_in_smem ? 2 * tri : tri, s>>>(G, R, Rinv, n, rel_tol,
-                                                                       shift_rel, x_in_smem);
+                                                                       shift_rel, x_in_smem, 1);
     TRG_LAUNCH_CHECK();
     return;
   }
