@@ -55,6 +55,8 @@ def args_():
                     help="comma-separated D: for each form of --precision and --also-forms, "
                          "the relative change of f after each of --precision-steps steps when "
                          "beta changes by a relative 1e-14 (the run's own conditioning)")
+    ap.add_argument("--sensitivity-eps", type=float, default=1e-14,
+                    help="relative change of beta in --sensitivity (2e-16: one ulp of 0.1497)")
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "learned"],
                     help="learned: train the sketch network on rows collected from plain "
@@ -430,9 +432,11 @@ def run_batch(a):
 
 def run_sensitivity(a):
     """Conditioning of the step sequence: f after each step from beta and from
-    beta (1 + 1e-14), same sketches, per form and D; with the smallest relative gap at the
-    step's cuts.  A perturbation of 1e-14 changes f directly by about 1e-14, so a larger
-    relative change measures how much the steps amplify differences at the rounding level."""
+    beta (1 + eps), same sketches, per form and D; with the smallest relative gap at the
+    step's cuts.  A perturbation of eps changes f directly by about eps, so a larger
+    relative change measures how much the steps amplify differences at the rounding level
+    (eps = 2e-16 is one unit in the last place of 0.1497: two FP64 programs that round
+    differently disagree by about that much)."""
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     import paper_2507_21909_b300 as trg
@@ -444,7 +448,7 @@ def run_sensitivity(a):
     for D in [int(v) for v in a.sensitivity.split(",") if v.strip()]:
         for name in forms:
             runs = []
-            for beta in (a.beta, a.beta * (1 + 1e-14)):
+            for beta in (a.beta, a.beta * (1 + a.sensitivity_eps)):
                 trg.trg_set_params(4, 4, 0x5EED, PREC[name])
                 trg.trg_init_ising(4, beta, 0.0)
                 fs, gaps = [], []
@@ -458,8 +462,9 @@ def run_sensitivity(a):
             rows.append({"D": D, "form": name,
                          "df_rel_per_step": [abs(x - y) / abs(x) for x, y in zip(f0, f1)],
                          "min_cut_gap_per_step": [g if math.isfinite(g) else None for g in g0]})
-    print(json.dumps({"metric": "relative change of f per step for a relative 1e-14 change of "
-                                "beta", "unit": "1", "steps": nsteps, "beta": a.beta,
+    print(json.dumps({"metric": "relative change of f per step for a relative change of beta",
+                      "unit": "1", "steps": nsteps, "beta": a.beta,
+                      "beta_rel_change": a.sensitivity_eps,
                       "config": {"workload": "4D Ising, h=0, p=2D, q_swap=4, q_rho=4"},
                       "rows": rows}), flush=True)
 
@@ -571,7 +576,7 @@ def reduce_timing(ms, steps, world, dist=None, device="cpu"):
 # mean over the launches of one timed D = 48 OZ5 step of this script, from a one-pass ncu
 # launch list with those two metrics), keyed by GEMM kind; a kind missing here has not
 # been captured on the current build of its kernel.
-TRAFFIC = {"oz": 2.679e9}
+TRAFFIC = {"oz": 2.662e9}
 
 
 def roofline(stats, step_ms_total, steps, prec, peak, peak_src):
