@@ -18,9 +18,9 @@
 // memory (two accumulators, alternating chunks) so the next chunk's products do not
 // wait for the drain.  The epilogue forms C = alpha 2^(e_r + e_c - 40) acc + beta C.
 //
-// Persistent kernel, one CTA (12 warps) per SM walking the output tiles: warp 0 TMA
-// producer, warp 1 MMA issuer (M = 128, N = 128, K = 16), warps 2..9 drain TMEM (two
-// warps per 32-lane quadrant, 64 columns each) and write the outputs from their
+// Persistent kernel, one CTA (18 warps) per SM walking the output tiles: warp 0 TMA
+// producer, warp 1 MMA issuer (M = 128, N = 128, K = 16), warps 2..17 drain TMEM (four
+// warps per 32-lane quadrant, 32 columns each) and write the outputs from their
 // registers while the next tile's products already run.  A pipeline stage holds one
 // 16-wide K block of every digit slice of A and of B, so each slice tile is loaded once
 // and serves all pairs (i, j) that use it.  The digit planes are stored pre-tiled in the
