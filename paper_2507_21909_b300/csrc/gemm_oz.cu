@@ -292,7 +292,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------ MMA issuer
       // per stage: every digit pair (i, j) from the resident slices.  The exact levels
-      // restart every chunk and are drained by warps 2..9; at the first stage of a chunk
+      // restart every chunk and are drained by warps 2..17; at the first stage of a chunk
       // the lower-level pairs go first, so they overlap the drain of the previous chunk.
       // Descriptors of slice tiles: the stage base's plus the byte offset / 16 (slices of
       // one 8-row group 256 bytes apart, groups NS x 256 bytes).

@@ -201,7 +201,7 @@ def test_bench_configuration_full_size(trg):
 def test_mixed_form_oz5_at_size_vs_fp64_form(trg):
     """The exact-digit mixed form at a size where the tensor-core GEMMs run at scale
     (D = 32, p = 2D: split-K digit products with millions of rows, the int64 drain of
-    every 256-deep chunk) against the library's FP64 form (itself pinned to the oracle
+    every 512-deep chunk) against the library's FP64 form (itself pinned to the oracle
     at 1e-10): the bench's coupling (beta = 0.1497, h = 0), 8 steps, of which steps 3..7
     run on the tensor cores.  Per step: dF/F <= 1e-8 (the headline's tolerance) and
     ln c_n within 1e-6.  Both forms draw the same sketches."""
