@@ -393,6 +393,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uns
   return __syncthreads_and(ok) != 0;
 }
 
+// The rotation that zeroes the (i, j) entry of the 2 x 2 Gram [al ga; ga be] (the
+// smaller tangent, as in Hestenes' one-sided Jacobi)
+__device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double &c,
+                                                double &s) {
+  const double zeta = (be - al) / (2.0 * ga);
+  double t;
+  if (fabs(zeta) > 1e150)
+    t = 0.5 / zeta;
+  else
+    t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+}
+constexpr int kRegCols = 8;   // column elements per lane kept in registers (m, n <= 256)
+
 __global__ void __launch_bounds__(32)
 svd_jacobi_coop_kernel(const double *A, int m, int n, double *U, double *S, double *V,
                        double *work, unsigned *sync, int *info) {
@@ -422,34 +437,70 @@ svd_jacobi_coop_kernel(const double *A, int m, int n, double *U, double *S, doub
         int i = p < q ? p : q, j = p < q ? q : p;
         if (j >= n) continue;  // dummy partner
         double *ai = at + (int64_t)i * m, *aj = at + (int64_t)j * m;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < m; r += 32) {
-          double x = __ldcg(&ai[r]), y = __ldcg(&aj[r]);
-          al += x * x;
-          be += y * y;
-          ga += x * y;
-        }
-        al = wsum(al);
-        be = wsum(be);
-        ga = wsum(ga);
-        if (!(fabs(ga) > tol * sqrt(al * be))) continue;
-        double zeta = (be - al) / (2.0 * ga);
-        double t;
-        if (fabs(zeta) > 1e150)
-          t = 0.5 / zeta;
-        else
-          t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        for (int r = lane; r < m; r += 32) {
-          double x = __ldcg(&ai[r]), y = __ldcg(&aj[r]);
-          __stcg(&ai[r], c * x - s * y);
-          __stcg(&aj[r], s * x + c * y);
-        }
         double *vi = vt + (int64_t)i * n, *vj = vt + (int64_t)j * n;
-        for (int r = lane; r < n; r += 32) {
-          double x = __ldcg(&vi[r]), y = __ldcg(&vj[r]);
-          __stcg(&vi[r], c * x - s * y);
-          __stcg(&vj[r], s * x + c * y);
+        if (m <= 32 * kRegCols && n <= 32 * kRegCols) {
+          // both column pairs of A and V read once, together, and kept in registers for
+          // the rotation (one L2 round trip per round); same operations in the same order
+          double xa[kRegCols], ya[kRegCols], xv[kRegCols], yv[kRegCols];
+#pragma unroll
+          for (int u = 0; u < kRegCols; ++u) {
+            const int r = lane + 32 * u;
+            xa[u] = r < m ? __ldcg(&ai[r]) : 0.0;
+            ya[u] = r < m ? __ldcg(&aj[r]) : 0.0;
+            xv[u] = r < n ? __ldcg(&vi[r]) : 0.0;
+            yv[u] = r < n ? __ldcg(&vj[r]) : 0.0;
+          }
+          double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+          for (int u = 0; u < kRegCols; ++u) {
+            if (lane + 32 * u < m) {
+              al += xa[u] * xa[u];
+              be += ya[u] * ya[u];
+              ga += xa[u] * ya[u];
+            }
+          }
+          al = wsum(al);
+          be = wsum(be);
+          ga = wsum(ga);
+          if (!(fabs(ga) > tol * sqrt(al * be))) continue;
+          double c, s;
+          jacobi_rotation(al, be, ga, c, s);
+#pragma unroll
+          for (int u = 0; u < kRegCols; ++u) {
+            const int r = lane + 32 * u;
+            if (r < m) {
+              __stcg(&ai[r], c * xa[u] - s * ya[u]);
+              __stcg(&aj[r], s * xa[u] + c * ya[u]);
+            }
+            if (r < n) {
+              __stcg(&vi[r], c * xv[u] - s * yv[u]);
+              __stcg(&vj[r], s * xv[u] + c * yv[u]);
+            }
+          }
+        } else {
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int r = lane; r < m; r += 32) {
+            double x = __ldcg(&ai[r]), y = __ldcg(&aj[r]);
+            al += x * x;
+            be += y * y;
+            ga += x * y;
+          }
+          al = wsum(al);
+          be = wsum(be);
+          ga = wsum(ga);
+          if (!(fabs(ga) > tol * sqrt(al * be))) continue;
+          double c, s;
+          jacobi_rotation(al, be, ga, c, s);
+          for (int r = lane; r < m; r += 32) {
+            double x = __ldcg(&ai[r]), y = __ldcg(&aj[r]);
+            __stcg(&ai[r], c * x - s * y);
+            __stcg(&aj[r], s * x + c * y);
+          }
+          for (int r = lane; r < n; r += 32) {
+            double x = __ldcg(&vi[r]), y = __ldcg(&vj[r]);
+            __stcg(&vi[r], c * x - s * y);
+            __stcg(&vj[r], s * x + c * y);
+          }
         }
         if (lane == 0) atomicAdd(&rot[sweep], 1);
       }
