@@ -163,9 +163,12 @@ inline Tensor view(double *p, std::vector<int64_t> d) {
   return t;
 }
 
+// product of d[a .. min(b, size)) (1 for an empty range)
 inline int64_t prod(const std::vector<int64_t> &d, size_t a = 0, size_t b = SIZE_MAX) {
   int64_t n = 1;
-  for (size_t i = a; i < std::min(b, d.size()); ++i) n *= d[i];
+  const size_t e = std::min(b, d.size());
+  for (auto it = d.begin() + (ptrdiff_t)std::min(a, e); it != d.begin() + (ptrdiff_t)e; ++it)
+    n *= *it;
   return n;
 }
 
