@@ -602,10 +602,14 @@ trg_status trg_gemm(int precision, int ta, int tb, long long M, long long N, lon
       ArenaScratch scr(c.arena);
       gemm_oz(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
               digits_of(precision), scr, c.stream, &c.timing);
-    } else {
+    } else if (precision == TRG_PREC_TF32X3) {
       ArenaScratch scr(c.arena);
       gemm_tc(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
-              slices_of(precision), scr, c.stream, &c.timing, precision == TRG_PREC_TF32X3);
+              slices_of(precision), scr, c.stream, &c.timing, true);
+    } else {   // BF16x3 / x6 / x10: BF16 pieces on the persistent tensor-core GEMM
+      ArenaScratch scr(c.arena);
+      gemm_oz(ta, tb, M, N, K, alpha, dA.p, lda, 0, dB.p, ldb, 0, beta, dC.p, ldc, 0, 1,
+              slices_of(precision), scr, c.stream, &c.timing, nullptr, nullptr, true);
     }
     TRG_CUDA(cudaMemcpyAsync(C, dC.p, M * ldc * 8, cudaMemcpyDeviceToHost, c.stream));
     TRG_CUDA(cudaStreamSynchronize(c.stream));

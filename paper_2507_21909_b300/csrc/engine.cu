@@ -86,9 +86,13 @@ void gemm(Ctx &c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alph
     Arena::Mark mk = c.arena.mark();
     ArenaScratch scr(c.arena);
     const bool cheap = is_digit_form(c.precision);   // an impurity-only product of a digit form
-    gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-            cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing,
-            !cheap && c.precision == TRG_PREC_TF32X3);
+    if (!cheap && c.precision == TRG_PREC_TF32X3)
+      gemm_tc(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+              slices_of(c.precision), scr, c.stream, &c.timing, true);
+    else   // BF16 pieces on the persistent tensor-core GEMM (128 x 256 tiles, FP32 sums)
+      gemm_oz(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+              cheap ? 3 : slices_of(c.precision), scr, c.stream, &c.timing, nullptr, nullptr,
+              true);
     c.arena.release(mk);
   } else {
     gemm_f64(ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, c.stream,

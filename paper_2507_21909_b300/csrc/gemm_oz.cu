@@ -465,6 +465,214 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                  : "memory");
 }
 
+// ------------------------------------------------------------- split-BF16 GEMM
+// The split-BF16 products (BF16x3 / x6 / x10: NS BF16 pieces per value, a = a_0 + a_1 +
+// ..., the pairs i + j < NS) on the same persistent design and pre-tiled planes, with
+// 128 x 256 tiles: every pair accumulates in FP32 over the split's K into one of two TMEM
+// accumulators (tiles alternate between columns [0, 256) and [256, 512)), and the 16 drain
+// warps write a finished tile from tensor memory while the next tile's products run.
+constexpr int SBN = 256;
+template <int NS>
+struct SForm {
+  static constexpr uint32_t A_TILE = BM * KS * 2, B_TILE = SBN * KS * 2;
+  static constexpr uint32_t STAGE = NS * (A_TILE + B_TILE);
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(SBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+
+template <int NS>
+__global__ void __launch_bounds__(THREADS, 1)
+split_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                  const __grid_constant__ CUtensorMap tmB, const Params p) {
+  using F = SForm<NS>;
+  constexpr int WC = SBN / 4;   // columns per drain warp
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  const int nst = p.stages;
+  double *epi = reinterpret_cast<double *>(smem + (size_t)nst * F::STAGE);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)nst * F::STAGE + kEpiBytes);
+  // bar[0..nst) stage full, bar[nst..2nst) stage empty, bar[2nst+j] accumulator j holds a
+  // finished tile, bar[2nst+2+j] accumulator j read out (NDRAIN warps), bar[2nst+4] every
+  // product issued by this CTA done
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * MAX_STAGES + 5);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gx = (p.M + BM - 1) / BM, gy = (p.N + SBN - 1) / SBN;
+  const int64_t per_z = gx * gy, ntiles = per_z * p.batch * p.ksplit;
+  const int nks_total = (int)(p.Kp / KS);
+  struct Tile {
+    int64_t m0, n0, b, split;
+    int ks0, nk;
+  };
+  auto tile_of = [&](int64_t t) {
+    Tile o;
+    const int64_t z = t / per_z, lin = t - z * per_z;
+    const int64_t g = lin / ((int64_t)kGroupM * gy), idx = lin % ((int64_t)kGroupM * gy);
+    const int64_t first = g * kGroupM, gsz = min((int64_t)kGroupM, gx - first);
+    o.m0 = (first + idx % gsz) * BM;
+    o.n0 = (idx / gsz) * SBN;
+    o.b = z % p.batch;
+    o.split = z / p.batch;
+    o.ks0 = (int)o.split * p.nks;
+    o.nk = max(min(o.ks0 + p.nks, nks_total) - o.ks0, 0);
+    return o;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < nst; ++st) {
+      mb_init(su32(&bar[st]), 1);
+      mb_init(su32(&bar[nst + st]), 1);
+    }
+    mb_init(su32(&bar[2 * nst]), 1);
+    mb_init(su32(&bar[2 * nst + 1]), 1);
+    mb_init(su32(&bar[2 * nst + 2]), NDRAIN * 32);
+    mb_init(su32(&bar[2 * nst + 3]), NDRAIN * 32);
+    mb_init(su32(&bar[2 * nst + 4]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------------------ TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const Tile tl = tile_of(t);
+        for (int i = 0; i < tl.nk; ++i, ++it) {
+          const int st = it % nst;
+          if (!mb_wait(su32(&bar[nst + st]), ((uint32_t)(it / nst) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t base = su32(smem + (size_t)st * F::STAGE);
+          const uint32_t full = su32(&bar[st]);
+          mb_expect(full, F::STAGE);
+          // [16 groups][NS pieces][256 B] of A, then [32 groups][NS pieces][256 B] of B
+          tma5(base, &tmA, full, tl.ks0 + i, (int)(tl.m0 >> 3), (int)tl.b);
+          tma5(base + NS * F::A_TILE, &tmB, full, tl.ks0 + i, (int)(tl.n0 >> 3), (int)tl.b);
+        }
+      }
+      for (int j = max(it - nst, 0); j < it; ++j)
+        mb_wait(su32(&bar[j % nst]), (uint32_t)(j / nst) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------ MMA issuer
+      constexpr uint64_t kSl = CHUNK_BYTES >> 4;
+      int it = 0, lt = 0;   // stages consumed, tiles issued (this CTA)
+      bool ok = true, issued = false;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+        const Tile tl = tile_of(t);
+        const int j = lt & 1;
+        // accumulator j last held tile lt - 2: the drain warps must have read it out
+        if (lt >= 2) {
+          if (!mb_wait(su32(&bar[2 * nst + 2 + j]), (uint32_t)((lt - 2) >> 1) & 1u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const uint32_t acc = tmem + (uint32_t)(j * SBN);
+        for (int i = 0; i < tl.nk; ++i, ++it) {
+          const int st = it % nst;
+          if (!mb_wait(su32(&bar[st]), (uint32_t)(it / nst) & 1u)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sbase = su32(smem + (size_t)st * F::STAGE);
+          const uint64_t da = sdesc(sbase, NS * CHUNK_BYTES);
+          const uint64_t db = sdesc(sbase + NS * F::A_TILE, NS * CHUNK_BYTES);
+#pragma unroll
+          for (int l = 0; l < NS; ++l)
+#pragma unroll
+            for (int i2 = 0; i2 <= l; ++i2)
+              umma(acc, da + i2 * kSl, db + (l - i2) * kSl, F::IDESC,
+                   (i > 0 || l > 0 || i2 > 0) ? 1u : 0u);
+          umma_commit(su32(&bar[nst + st]));
+          issued = true;
+        }
+        if (!ok) break;
+        umma_commit(su32(&bar[2 * nst + j]));   // this tile's products complete -> write
+      }
+      if (issued) {
+        umma_commit(su32(&bar[2 * nst + 4]));
+        mb_wait(su32(&bar[2 * nst + 4]), 0);
+      }
+    }
+  } else {  // ------------------------------------------ drain warps 2..17
+    const int ew = warp - 2, quad = warp & 3, qc = ew >> 2;   // columns [WC qc, WC qc + WC)
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    double *st = epi + (size_t)ew * 32 * (kEpiCols + 1);
+    constexpr int RPI = 32 / kEpiCols;
+    const int rs = lane / kEpiCols, cs = lane % kEpiCols;
+    int lt = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const Tile tl = tile_of(t);
+      const int j = lt & 1;
+      // warp-uniform (the tensor-memory loads below are warp-collective)
+      if (!__all_sync(0xffffffffu, mb_wait(su32(&bar[2 * nst + j]), (uint32_t)(lt >> 1) & 1u)))
+        break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t row = tl.m0 + quad * 32 + lane;
+      double *Cbase = p.to_ws ? p.C + ((tl.split * p.batch + tl.b) * p.M) * p.N
+                              : p.C + tl.b * p.sC;
+      const int64_t ldc = p.to_ws ? p.N : p.ldc;
+      const bool rd = !p.to_ws && p.beta != 0.0;
+#pragma unroll 1
+      for (int c = 0; c < WC / 16; ++c) {
+        uint32_t r[16];
+        tld16(lane_base + (uint32_t)(j * SBN + qc * WC + c * 16), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c == WC / 16 - 1) {   // the accumulator is read out: the issuer may reuse it
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mb_arrive(su32(&bar[2 * nst + 2 + j]));
+        }
+#pragma unroll
+        for (int q = 0; q < 16 / kEpiCols; ++q) {
+          const int64_t cb = tl.n0 + qc * WC + c * 16 + q * kEpiCols;
+#pragma unroll
+          for (int jj = 0; jj < kEpiCols; ++jj)
+            st[lane * (kEpiCols + 1) + jj] =
+                (row < p.M && cb + jj < p.N) ? (double)__uint_as_float(r[q * kEpiCols + jj])
+                                             : 0.0;
+          __syncwarp();
+          const int64_t col = cb + cs;
+          double old[32 / RPI];
+#pragma unroll
+          for (int u = 0; u < 32 / RPI; ++u) {
+            const int64_t rr = tl.m0 + quad * 32 + u * RPI + rs;
+            old[u] = (rd && rr < p.M && col < p.N) ? Cbase[rr * ldc + col] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 32 / RPI; ++u) {
+            const int lr = u * RPI + rs;
+            const int64_t rr = tl.m0 + quad * 32 + lr;
+            if (rr < p.M && col < p.N) {
+              const double x = st[lr * (kEpiCols + 1) + cs];
+              Cbase[rr * ldc + col] =
+                  p.to_ws ? x : rd ? p.alpha * x + p.beta * old[u] : p.alpha * x;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
 // common exponent of every row r of op(X): e with max_k |op(X)[r][k]| < 2^e, stored as
 // code = e + 4096 (0 for an all-zero row) and combined across blocks with atomicMax.
 // Tiles of 32 rows x 1024 k; the read is coalesced along whichever index is contiguous.
@@ -577,19 +785,53 @@ __device__ __forceinline__ void store_pairs(__nv_bfloat16 *o, const int (&d0)[NS
 // planes are written in units of one 8-row group x one 8-wide K half: 32 lanes, lane =
 // 4 (r % 8) + j, two consecutive k = 8 h + 2 j, 8 h + 2 j + 1, so that each store of a
 // slice is one contiguous 128-byte core matrix
+// BF16 pieces of a value for the split-BF16 products, a_s = bf16(a - a_0 - ... - a_{s-1}):
+// up to three in FP32 (which holds the 24 bits three pieces carry, so the slicing is exact
+// there), four with FP64 remainders
 template <int NS>
+__device__ __forceinline__ void bf_pieces(double v, __nv_bfloat16 (&q)[NS]) {
+  if constexpr (NS <= 3) {
+    float rem = (float)v;
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl) {
+      q[sl] = __float2bfloat16_rn(rem);
+      rem -= __bfloat162float(q[sl]);
+    }
+  } else {
+    double rem = v;
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl) {
+      q[sl] = __double2bfloat16(rem);
+      rem -= (double)__bfloat162float(q[sl]);
+    }
+  }
+}
+
+// FL: BF16 pieces of every value (no common exponent) instead of digits
+template <int NS, bool FL>
 __device__ __forceinline__ void split_pair(double v0, double v1, double scale,
                                            __nv_bfloat16 *chunk, int h, int lane) {
-  int d0[NS], d1[NS];
-  balanced_digits<NS>(__double2ll_rn(v0 * scale), d0);
-  balanced_digits<NS>(__double2ll_rn(v1 * scale), d1);
-  store_pairs<NS>(chunk + h * 64 + (lane >> 2) * 8 + (lane & 3) * 2, d0, d1);
+  __nv_bfloat16 *o = chunk + h * 64 + (lane >> 2) * 8 + (lane & 3) * 2;
+  if constexpr (FL) {
+    __nv_bfloat16 q0[NS], q1[NS];
+    bf_pieces<NS>(v0, q0);
+    bf_pieces<NS>(v1, q1);
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl)
+      *reinterpret_cast<__nv_bfloat162 *>(o + sl * (CHUNK_BYTES / 2)) =
+          __halves2bfloat162(q0[sl], q1[sl]);
+  } else {
+    int d0[NS], d1[NS];
+    balanced_digits<NS>(__double2ll_rn(v0 * scale), d0);
+    balanced_digits<NS>(__double2ll_rn(v1 * scale), d1);
+    store_pairs<NS>(o, d0, d1);
+  }
 }
 
 // Digit planes of op(X) = X (rows contiguous along K): one warp per (8-row group, run of
 // kSplitSeg K), one K half (8 wide) of the group per step, four steps in flight
 constexpr int64_t kSplitSeg = 1024;
-template <int NS>
+template <int NS, bool FL>
 __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
                                      int64_t ld, int64_t sX, const unsigned *__restrict__ e,
                                      __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
@@ -604,7 +846,7 @@ __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows,
     const int64_t r = g * 8 + (lane >> 2);
     const bool live = r < rows;
     const double *x = X + b * sX + (live ? r : 0) * ld;
-    const int ex = live ? decode_exp(e[b * rows + r]) : 0;
+    const int ex = (!FL && live) ? decode_exp(e[b * rows + r]) : 0;
     const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
     const int64_t h0 = seg * (kSplitSeg / 8), h1 = min(Kp, (seg + 1) * kSplitSeg) / 8;
     for (int64_t hb = h0; hb < h1; hb += 4) {   // K halves hb .. hb + 3 (h1 - h0 is even)
@@ -621,7 +863,7 @@ __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows,
         if (hb + u >= h1) break;
         const int64_t kb = (hb + u) >> 1;
         __nv_bfloat16 *chunk = out + ((bg * KB + kb) * NS) * (CHUNK_BYTES / 2);
-        split_pair<NS>(v[2 * u], v[2 * u + 1], scale, chunk, (int)((hb + u) & 1), lane);
+        split_pair<NS, FL>(v[2 * u], v[2 * u + 1], scale, chunk, (int)((hb + u) & 1), lane);
       }
     }
   }
@@ -630,7 +872,7 @@ __global__ void oz_split_rows_kernel(const double *__restrict__ X, int64_t rows,
 // Digit planes of op(X) = X^T (X stored K x rows): 32 rows x 64 k tiles transposed
 // through shared memory (loads coalesced along the rows), then each warp writes whole
 // core matrices as above
-template <int NS>
+template <int NS, bool FL>
 __global__ void oz_split_cols_kernel(const double *__restrict__ X, int64_t rows, int64_t K,
                                      int64_t ld, int64_t sX, const unsigned *__restrict__ e,
                                      __nv_bfloat16 *__restrict__ out, int64_t Kp, int64_t batch) {
@@ -663,29 +905,29 @@ __global__ void oz_split_cols_kernel(const double *__restrict__ X, int64_t rows,
       const int64_t g = (r0 >> 3) + gl;
       if (g >= G) continue;
       const int64_t r = g * 8 + rr;
-      const int ex = r < rows ? decode_exp(e[b * rows + r]) : 0;
+      const int ex = (!FL && r < rows) ? decode_exp(e[b * rows + r]) : 0;
       const double scale = __longlong_as_double((long long)(1023 - ex + 7 * NS) << 52);
       const int kl = hl * 8 + jj * 2;
       const int64_t kb = (k0 >> 4) + (hl >> 1);
       __nv_bfloat16 *chunk = out + (((b * G + g) * KB + kb) * NS) * (CHUNK_BYTES / 2);
-      split_pair<NS>(tile[kl][gl * 8 + rr], tile[kl + 1][gl * 8 + rr], scale, chunk, hl & 1,
-                     tx);
+      split_pair<NS, FL>(tile[kl][gl * 8 + rr], tile[kl + 1][gl * 8 + rr], scale, chunk,
+                         hl & 1, tx);
     }
   }
 }
 
-template <int NS>
+template <int NS, bool FL = false>
 static void launch_split(const double *X, int64_t rows, int64_t K, int64_t ld, int64_t sX,
                          bool trans, const unsigned *e, __nv_bfloat16 *out, int64_t Kp,
                          int64_t batch, cudaStream_t s) {
   const int64_t G = (rows + 7) / 8;
   if (trans) {
     const int64_t t = ((G + 3) / 4) * (Kp / 64) * batch;
-    oz_split_cols_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32),
+    oz_split_cols_kernel<NS, FL><<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 32),
                                dim3(32, 8), 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
   } else {
     const int64_t warps = G * batch * ((Kp + kSplitSeg - 1) / kSplitSeg);
-    oz_split_rows_kernel<NS><<<(unsigned)std::min<int64_t>(std::max<int64_t>((warps + 7) / 8, 1),
+    oz_split_rows_kernel<NS, FL><<<(unsigned)std::min<int64_t>(std::max<int64_t>((warps + 7) / 8, 1),
                                                             148 * 16),
                                256, 0, s>>>(X, rows, K, ld, sX, e, out, Kp, batch);
   }
@@ -781,7 +1023,8 @@ __global__ void oz_rowexp_small_kernel(const double *__restrict__ X, int64_t row
 }
 
 OzOperand oz_prepare(const double *X, int64_t rows, int64_t K, int64_t ld, int64_t sX,
-                     bool trans, int64_t batch, int ns, TcScratch &scr, cudaStream_t s) {
+                     bool trans, int64_t batch, int ns, TcScratch &scr, cudaStream_t s,
+                     bool fl) {
   using namespace oz;
   OzOperand o;
   o.rows = rows;
@@ -789,9 +1032,19 @@ OzOperand oz_prepare(const double *X, int64_t rows, int64_t K, int64_t ld, int64
   o.Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
   o.batch = batch;
   o.ns = ns;
-  unsigned *e = (unsigned *)scr.alloc((size_t)batch * rows * sizeof(unsigned));
+  o.fl = fl;
   __nv_bfloat16 *pl =
       (__nv_bfloat16 *)scr.alloc((size_t)ns * batch * ((rows + 7) / 8 * 8) * o.Kp * 2);
+  if (fl) {   // BF16 pieces of every value: no common exponents
+    switch (ns) {
+      case 2: launch_split<2, true>(X, rows, K, ld, sX, trans, nullptr, pl, o.Kp, batch, s); break;
+      case 3: launch_split<3, true>(X, rows, K, ld, sX, trans, nullptr, pl, o.Kp, batch, s); break;
+      default: launch_split<4, true>(X, rows, K, ld, sX, trans, nullptr, pl, o.Kp, batch, s); break;
+    }
+    o.planes = pl;
+    return o;
+  }
+  unsigned *e = (unsigned *)scr.alloc((size_t)batch * rows * sizeof(unsigned));
   if (!trans && K <= 128) {
     const int64_t t = (rows * batch + 255) / 256;
     oz_rowexp_small_kernel<<<(unsigned)std::min<int64_t>(std::max<int64_t>(t, 1), 148 * 64),
@@ -819,23 +1072,26 @@ OzOperand oz_prepare(const double *X, int64_t rows, int64_t K, int64_t ld, int64
 void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
              int64_t lda, int64_t sA, const double *B, int64_t ldb, int64_t sB, double beta,
              double *C, int64_t ldc, int64_t sC, int64_t batch, int ns, TcScratch &scr,
-             cudaStream_t s, TcTiming *timing, const OzOperand *pa, const OzOperand *pb) {
+             cudaStream_t s, TcTiming *timing, const OzOperand *pa, const OzOperand *pb,
+             bool fl) {
   using namespace oz;
   if (M == 0 || N == 0 || batch == 0) return;
-  if (ns < 3 || ns > 7) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 7");
-  const bool x7 = ns == 7;     // the FP64-equivalent form: its own tile width
-  const int bn = x7 ? Form<7>::TBN : Form<5>::TBN;
+  if (!fl && (ns < 3 || ns > 7)) throw Error(TRG_ERR_ARG, "gemm_oz: 3 <= digits <= 7");
+  if (fl && (ns < 2 || ns > 4)) throw Error(TRG_ERR_ARG, "gemm_oz: 2 <= BF16 pieces <= 4");
+  const bool x7 = !fl && ns == 7;   // the FP64-equivalent form: its own tile width
+  const int bn = fl ? SBN : x7 ? Form<7>::TBN : Form<5>::TBN;
   const size_t stage_bytes = (size_t)ns * (BM + bn) * KS * 2;
   const int64_t Kp = std::max<int64_t>(BK, (K + BK - 1) / BK * BK);
   auto fits = [&](const OzOperand *o, int64_t rows) {
-    return o && o->rows == rows && o->K == K && o->Kp == Kp && o->batch == batch && o->ns == ns;
+    return o && o->rows == rows && o->K == K && o->Kp == Kp && o->batch == batch && o->ns == ns &&
+           o->fl == fl;
   };
   if ((pa && !fits(pa, M)) || (pb && !fits(pb, N)))
     throw Error(TRG_ERR_ARG, "gemm_oz: prepared operand does not match the product");
   // a Gram (op(A) = X^T, op(B) = X, or op(A) = X, op(B) = X^T) has identical digit planes
   const bool gram = A == B && ta != tb && M == N && lda == ldb && sA == sB;
-  OzOperand oa = pa ? *pa : oz_prepare(A, M, K, lda, sA, ta, batch, ns, scr, s);
-  OzOperand ob = pb ? *pb : gram ? oa : oz_prepare(B, N, K, ldb, sB, !tb, batch, ns, scr, s);
+  OzOperand oa = pa ? *pa : oz_prepare(A, M, K, lda, sA, ta, batch, ns, scr, s, fl);
+  OzOperand ob = pb ? *pb : gram ? oa : oz_prepare(B, N, K, ldb, sB, !tb, batch, ns, scr, s, fl);
   Params p{};
   p.M = M;
   p.N = N;
@@ -845,7 +1101,7 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   p.beta = beta;
   p.ea = oa.e;
   p.eb = ob.e;
-  const int npairs = ns * (ns + 1) / 2;    // digit pairs i + j <= ns - 1
+  const int npairs = ns * (ns + 1) / 2;    // digit (piece) pairs i + j <= ns - 1
   const int64_t gx = (M + BM - 1) / BM, gy = (N + bn - 1) / bn;
   const int nks_total = (int)(Kp / KS);
   // thread-safe one-time setup (function-local static initialisation): the shared-memory
@@ -853,7 +1109,8 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   static const int n_sm = [] {
     for (const void *k : {(const void *)oz_gemm_kernel<3>, (const void *)oz_gemm_kernel<4>,
                           (const void *)oz_gemm_kernel<5>, (const void *)oz_gemm_kernel<6>,
-                          (const void *)oz_gemm_kernel<7>})
+                          (const void *)oz_gemm_kernel<7>, (const void *)split_gemm_kernel<2>,
+                          (const void *)split_gemm_kernel<3>, (const void *)split_gemm_kernel<4>})
       TRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kSmemOptin));
     int dev = 0, n = 0;
@@ -885,8 +1142,8 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
     }
   }
   // the fixed-point accumulator holds K 2^41 < 2^63 (K 2^44 in the seven-digit form): at
-  // most 2^21 (2^18) K per split
-  const int64_t kmax = x7 ? kXMaxKSplit : (int64_t(1) << 21);
+  // most 2^21 (2^18) K per split; BF16 pieces accumulate in FP32 (no limit)
+  const int64_t kmax = fl ? (int64_t(1) << 40) : x7 ? kXMaxKSplit : (int64_t(1) << 21);
   ksplit = std::max<int>(ksplit, (int)((Kp + kmax - 1) / kmax));
   int per = (nks_total + ksplit - 1) / ksplit;
   per = (per + CHUNK_KS - 1) / CHUNK_KS * CHUNK_KS;
@@ -911,7 +1168,8 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, n_sm);
   if (debug_opt("attr")) {
     const void *fns[4] = {(const void *)oz_gemm_kernel<5>, (const void *)oz_rowexp_kernel,
-                          (const void *)oz_split_rows_kernel<5>, (const void *)oz_ws_reduce};
+                          (const void *)oz_split_rows_kernel<5, false>,
+                          (const void *)oz_ws_reduce};
     for (int i = 0; i < 4; ++i) {
       cudaFuncAttributes fa;
       cudaFuncGetAttributes(&fa, fns[i]);
@@ -924,16 +1182,25 @@ void gemm_oz(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, co
             p.stages);
   }
   if (timing) timing->before(s);
-  switch (ns) {
-    case 3: oz_gemm_kernel<3><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
-    case 4: oz_gemm_kernel<4><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
-    case 5: oz_gemm_kernel<5><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
-    case 6: oz_gemm_kernel<6><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
-    default: oz_gemm_kernel<7><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+  if (fl) {
+    switch (ns) {
+      case 2: split_gemm_kernel<2><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+      case 3: split_gemm_kernel<3><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+      default: split_gemm_kernel<4><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    }
+  } else {
+    switch (ns) {
+      case 3: oz_gemm_kernel<3><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+      case 4: oz_gemm_kernel<4><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+      case 5: oz_gemm_kernel<5><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+      case 6: oz_gemm_kernel<6><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+      default: oz_gemm_kernel<7><<<grid, THREADS, smem, s>>>(ma, mb, p); break;
+    }
   }
   TRG_LAUNCH_CHECK();
+  // timing kinds: 0 digit GEMM, 1 split-BF16 GEMM, 2 seven-digit GEMM
   if (timing)
-    timing->after(s, x7 ? 2 : 0, 2.0 * (double)M * N * K * batch,
+    timing->after(s, fl ? 1 : x7 ? 2 : 0, 2.0 * (double)M * N * K * batch,
                   2.0 * (double)M * N * K * batch * npairs);
   if (ksplit > 1) {
     const int64_t total = batch * M * N;

@@ -9,8 +9,9 @@ replays those waits and arrivals with mbarrier phase-parity semantics under rand
 interleavings, with tensor-core products that complete in issue order and TMA loads that
 land in any order, and checks that every schedule finishes (no deadlock) and that no
 stage is overwritten before its products ran and no accumulator is read before its
-chunk's products completed or after the next chunk's started.  A planted parity mistake
-makes it fail (last test).
+chunk's products completed or after the next chunk's started.  The split-BF16 kernel's
+protocol (one accumulator per tile, two alternating, released by the drain warps) is
+modelled the same way.  A planted parity mistake makes each model fail.
 """
 import random
 
@@ -159,3 +160,109 @@ def test_planted_parity_mistake_is_caught():
     with pytest.raises(AssertionError):
         for seed in range(12):
             simulate([64] * 4, 4, seed=seed, h_parity_flip=1)
+
+
+def simulate_split(tiles_nk, nst, ndrain=2, seed=0, acc_parity_flip=0):
+    """The split-BF16 kernel: every product of a tile into accumulator lt & 1 over the
+    tile's whole K, one commit per tile, the drain warps read the tile out and release the
+    accumulator for tile lt + 2."""
+    rng = random.Random(seed)
+    full = [Bar(1) for _ in range(nst)]
+    empty = [Bar(1) for _ in range(nst)]
+    acc_full = [Bar(1), Bar(1)]
+    acc_empty = [Bar(ndrain), Bar(ndrain)]
+    all_done = Bar(1)
+    stage_ver = [None] * nst
+    pending_tma, fifo = [], []
+    acc_tile = {0: None, 1: None}    # tile whose products the accumulator holds
+    read_out = set()
+
+    def producer():
+        it = 0
+        for nk in tiles_nk:
+            for i in range(nk):
+                st = it % nst
+                while not empty[st].test(((it // nst) & 1) ^ 1):
+                    yield
+                pending_tma.append((st, it))
+                it += 1
+        for j in range(max(it - nst, 0), it):
+            while not full[j % nst].test((j // nst) & 1):
+                yield
+
+    def issuer():
+        it = 0
+        for lt, nk in enumerate(tiles_nk):
+            j = lt & 1
+            if lt >= 2:
+                while not acc_empty[j].test((((lt - 2) >> 1) & 1) ^ acc_parity_flip):
+                    yield
+            for i in range(nk):
+                st = it % nst
+                while not full[st].test((it // nst) & 1):
+                    yield
+                fifo.append(('mma', j, lt, st, it))
+                fifo.append(('commit', empty[st]))
+                it += 1
+                yield
+            fifo.append(('commit', acc_full[j]))
+        fifo.append(('commit', all_done))
+        while not all_done.test(0):
+            yield
+
+    def drain(w):
+        for lt in range(len(tiles_nk)):
+            j = lt & 1
+            while not acc_full[j].test((lt >> 1) & 1):
+                yield
+            assert acc_tile[j] == lt, ('acc', lt, acc_tile)
+            read_out.add((w, lt))
+            acc_empty[j].arrive()
+            for _ in range(rng.randint(0, 6)):   # the stores of the tile
+                yield
+
+    roles = [producer(), issuer()] + [drain(w) for w in range(ndrain)]
+    alive = list(range(len(roles)))
+    steps = 0
+    while alive or pending_tma or fifo:
+        steps += 1
+        assert steps < 10 ** 7, "no progress"
+        ev = rng.random()
+        if pending_tma and ev < 0.2:
+            st, it = pending_tma.pop(rng.randrange(len(pending_tma)))
+            assert stage_ver[st] is None or stage_ver[st] == it - nst, ('overwrite', st, it)
+            stage_ver[st] = it
+            full[st].arrive()
+            continue
+        if fifo and ev < 0.5:
+            op = fifo.pop(0)
+            if op[0] == 'mma':
+                _, j, lt, st, it = op
+                assert stage_ver[st] == it, ('stage data', st, it)
+                # the accumulator must have been read out before a new tile writes it
+                assert acc_tile[j] in (None, lt) or all((w, acc_tile[j]) in read_out
+                                                         for w in range(ndrain)), ('reuse', j)
+                acc_tile[j] = lt
+            else:
+                op[1].arrive()
+            continue
+        if not alive:
+            continue
+        r = rng.choice(alive)
+        try:
+            next(roles[r])
+        except StopIteration:
+            alive.remove(r)
+    assert len(read_out) == ndrain * len(tiles_nk)
+
+
+@pytest.mark.parametrize("tiles,nst", CFGS)
+def test_split_protocol_finishes_without_hazards(tiles, nst):
+    for seed in range(12):
+        simulate_split(tiles, nst, seed=seed)
+
+
+def test_split_planted_parity_mistake_is_caught():
+    with pytest.raises(AssertionError):
+        for seed in range(12):
+            simulate_split([8] * 6, 4, seed=seed, acc_parity_flip=1)
